@@ -1,0 +1,142 @@
+"""ctypes front end of the C oracle (cplbm_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: only the tests, the smoke check and the benchmark's
+CPU-baseline leg use this module.  It never touches the CUDA library.
+
+Arrays are numpy float64, C-contiguous, row-major [ny][nx]; populations are
+structure-of-arrays [9][ny][nx] in the velocity order of Sec. 2.
+"""
+import ctypes as C
+import math
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+class OrcParams(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32),
+                ("T", C.c_double), ("a", C.c_double), ("b", C.c_double),
+                ("R", C.c_double),
+                ("kappa", C.c_double), ("tau", C.c_double), ("k", C.c_double),
+                ("alpha", C.c_double),
+                ("mu_max", C.c_double), ("mu_cap_steps", C.c_int64)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = C.CDLL(_build.build())
+        dp = C.POINTER(C.c_double)
+        L.orc_cs_p0.restype = C.c_double
+        L.orc_cs_p0.argtypes = [C.c_double] * 5
+        L.orc_cs_mu0.restype = C.c_double
+        L.orc_cs_mu0.argtypes = [C.c_double] * 5
+        L.orc_cfd_line.restype = C.c_int
+        L.orc_cfd_line.argtypes = [dp, C.c_ssize_t, dp, C.c_ssize_t, C.c_int,
+                                   C.c_double, C.c_double]
+        L.orc_forcing_terms.restype = None
+        L.orc_forcing_terms.argtypes = [C.c_double] * 5 + [dp]
+        P = C.POINTER(OrcParams)
+        L.orc_feq_field.restype = None
+        L.orc_feq_field.argtypes = [P, dp, dp, dp, dp]
+        L.orc_force_stage.restype = C.c_int
+        L.orc_force_stage.argtypes = [P, C.c_int64, dp, dp, dp, dp]
+        L.orc_run.restype = C.c_int
+        L.orc_run.argtypes = [P, dp, C.c_int64, C.c_int64]
+        L.orc_macro.restype = C.c_int
+        L.orc_macro.argtypes = [P, dp, C.c_int64, dp, dp, dp, dp, dp, dp]
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def cs_p0(rho, T, a=1.0, b=4.0, R=1.0):
+    """Carnahan-Starling pressure, Eq. 20 (scalar)."""
+    return lib().orc_cs_p0(rho, T, a, b, R)
+
+
+def cs_mu0(rho, T, a=1.0, b=4.0, R=1.0):
+    """Carnahan-Starling chemical potential without the gradient term, Eq. 21."""
+    return lib().orc_cs_mu0(rho, T, a, b, R)
+
+
+def cfd_alpha(order):
+    """alpha of the compact scheme (Eq. 38): 1/4 gives 4th order (b = 0), 1/3 gives
+    the 6th-order scheme of Eq. 39."""
+    if order == 4:
+        return 0.25
+    if order == 6:
+        return 1.0 / 3.0
+    raise ValueError("compact FD order must be 4 or 6")
+
+
+def cfd_line(u, alpha, h=1.0):
+    """Periodic compact first derivative of the 1-D array u (Eqs. 37-38)."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    d = np.empty_like(u)
+    if lib().orc_cfd_line(_ptr(u), 1, _ptr(d), 1, u.size, alpha, h):
+        raise ValueError("line too short")
+    return d
+
+
+def forcing_terms(rho, ux, uy, Fx, Fy):
+    """Exact-difference forcing terms F_i of Eq. 5 at one node."""
+    out = np.empty(9)
+    lib().orc_forcing_terms(rho, ux, uy, Fx, Fy, _ptr(out))
+    return out
+
+
+class OracleSim:
+    """One periodic D2Q9 simulation advanced by the C oracle, FP64."""
+
+    def __init__(self, nx, ny, T, kappa, tau, k, fd_order, mu_max=math.inf,
+                 mu_cap_steps=0, a=1.0, b=4.0, R=1.0):
+        self.p = OrcParams(nx, ny, T, a, b, R, kappa, tau, k, cfd_alpha(fd_order),
+                           mu_max, mu_cap_steps)
+        self.nx, self.ny = nx, ny
+        self.t = 0
+        self.f = np.zeros((9, ny, nx))
+
+    def set_fields(self, rho, ux=None, uy=None):
+        """f = f^eq(rho, u) (u = 0 where not given); time level reset to 0."""
+        rho = np.ascontiguousarray(rho, dtype=np.float64).reshape(self.ny, self.nx)
+        ux = None if ux is None else np.ascontiguousarray(ux, np.float64).reshape(rho.shape)
+        uy = None if uy is None else np.ascontiguousarray(uy, np.float64).reshape(rho.shape)
+        lib().orc_feq_field(C.byref(self.p), _ptr(rho), _ptr(ux), _ptr(uy), _ptr(self.f))
+        self.t = 0
+
+    def set_populations(self, f, t=0):
+        self.f[...] = f
+        self.t = t
+
+    def step(self, n):
+        if lib().orc_run(C.byref(self.p), _ptr(self.f), self.t, n):
+            raise RuntimeError("oracle step failed")
+        self.t += n
+
+    def fields(self):
+        """(rho, vx, vy, mu_hat, Fx, Fy) of the current state."""
+        shape = (self.ny, self.nx)
+        rho, vx, vy, mu, Fx, Fy = (np.empty(shape) for _ in range(6))
+        if lib().orc_macro(C.byref(self.p), _ptr(self.f), self.t, _ptr(rho), _ptr(vx),
+                           _ptr(vy), _ptr(mu), _ptr(Fx), _ptr(Fy)):
+            raise RuntimeError("oracle macro failed")
+        return rho, vx, vy, mu, Fx, Fy
+
+    def force_stage(self, rho, t=None):
+        """(mu_hat, Fx, Fy) computed from a given density field."""
+        rho = np.ascontiguousarray(rho, dtype=np.float64)
+        mu, Fx, Fy = (np.empty_like(rho) for _ in range(3))
+        if lib().orc_force_stage(C.byref(self.p), self.t if t is None else t, _ptr(rho),
+                                 _ptr(mu), _ptr(Fx), _ptr(Fy)):
+            raise RuntimeError("oracle force stage failed")
+        return mu, Fx, Fy

@@ -1,0 +1,63 @@
+"""Seeded synthetic initial fields for the benchmark and the tests.
+
+This module holds no arithmetic of the method itself: it only lays out initial
+density and velocity fields (numpy, FP64, row-major [ny][nx]) from coexistence
+densities that the caller supplies.  Both the CUDA path and the CPU oracle are
+fed from here, so their inputs are bit-identical.
+
+  * drop      the tanh profile of Eq. 41 around the domain centre
+  * flat      two planar interfaces normal to y, liquid in the middle (Sec. 5.1)
+  * noise     multiplicative uniform noise rho <- rho (1 + eps), eps in [-A, A],
+              drawn from splitmix64 of (seed, node index): a counter-based
+              generator, so any node's value can be recomputed on its own.
+"""
+import numpy as np
+
+_M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+def splitmix64(x):
+    """splitmix64 finaliser (Steele, Lea and Flood, 2014) on a uint64 array."""
+    with np.errstate(over="ignore"):
+        z = (x + np.uint64(0x9E3779B97F4A7C15)) & _M64
+        z = ((z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)) & _M64
+        z = ((z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)) & _M64
+        return z ^ (z >> np.uint64(31))
+
+
+def uniform_noise(shape, seed, amplitude):
+    """eps in [-amplitude, amplitude) for every node, node index = y*nx + x."""
+    n = int(np.prod(shape))
+    idx = np.arange(n, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        key = splitmix64(np.uint64(seed) * np.uint64(0x100000001B3) + idx)
+    u = (key >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)  # [0,1)
+    return (amplitude * (2.0 * u - 1.0)).reshape(shape)
+
+
+def drop(nx, ny, rho_g, rho_l, radius, width, center=None):
+    """Eq. 41: rho = (rho_g+rho_l)/2 + (rho_g-rho_l)/2 tanh(2(r - r0)/W), centre
+    (nx/2, ny/2) in node indices unless given."""
+    x0, y0 = (nx / 2.0, ny / 2.0) if center is None else center
+    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    r = np.sqrt((x - x0) ** 2 + (y - y0) ** 2)
+    return 0.5 * (rho_g + rho_l) + 0.5 * (rho_g - rho_l) * np.tanh(2.0 * (r - radius) / width)
+
+
+def flat(nx, ny, rho_g, rho_l, thickness, width):
+    """Liquid slab |y - ny/2| < thickness/2 in gas, tanh edges of width W."""
+    y = np.arange(ny, dtype=np.float64)[:, None] * np.ones((1, nx))
+    d = np.abs(y - ny / 2.0) - thickness / 2.0
+    return 0.5 * (rho_g + rho_l) + 0.5 * (rho_g - rho_l) * np.tanh(2.0 * d / width)
+
+
+def with_noise(rho, seed, amplitude):
+    """Multiplicative noise, rho (1 + eps): keeps low gas densities positive."""
+    return rho * (1.0 + uniform_noise(rho.shape, seed, amplitude))
+
+
+def shear_wave(nx, ny, rho0, amplitude):
+    """Uniform density with u_x = A sin(2 pi y / ny), u_y = 0."""
+    y = np.arange(ny, dtype=np.float64)[:, None] * np.ones((1, nx))
+    return (np.full((ny, nx), rho0), amplitude * np.sin(2 * np.pi * y / ny),
+            np.zeros((ny, nx)))
