@@ -1,0 +1,321 @@
+#!/usr/bin/env python3
+"""Benchmark of the chemical-potential multiphase LBM time step on GB300.
+
+Workload (default): a 1024 x 1024 periodic static drop of radius 200 in its
+Maxwell gas, Carnahan-Starling EOS (a=1, b=4, R=1) at T_r = 0.5, mesh
+coefficient k = 0.5, 6th-order compact FD, tau = 1, kappa-hat = 0.1, tanh width
+8; populations in FP32, density / derivatives / chemical potential / force in
+FP64 ("mixed").  Synthetic, seeded inputs.
+
+One "step" is one time step: the five device passes (collide-stream, x- and
+y-line compact FD of rho with the chemical potential, x- and y-line compact FD
+of mu with the force).  Timing: W warm-up steps, then K steps, each bracketed by
+CUDA events recorded by the library on its stream around every pass; between
+steps a 512 MB buffer is written to flush the L2 (not timed).  value = nodes x K
+/ sum of step times.  e2e = the same metric through the public host API
+(lbm_set_fields from pinned host memory, K steps, lbm_fields back to host),
+wall clock.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun every rank runs its own replica (weak scaling, no collective
+on the data path); rank 0 prints the JSON line.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(nx=1024, ny=1024, T_r=0.5, k=0.5, kappa=0.1, tau=1.0, order=6, radius=200.0,
+                width=8.0)
+METRIC = "MLUPS (million lattice-node updates per second) of the full time step"
+# algorithmic bytes per node of each pass: [collide-stream, x rho, y rho + mu, x mu + F_x,
+# y mu + F_y]; populations 4 B (mixed) or 8 B (fp64), fields 8 B
+PASS_NAMES = ["collide_stream", "cfd_x_rho", "cfd_y_rho_mu", "cfd_x_force", "cfd_y_force"]
+
+
+def pass_bytes(precision):
+    fb = 4 if precision == "mixed" else 8
+    return [9 * fb + 16 + 9 * fb + 8, 24, 32, 32, 32]
+
+
+def workload_name(w, precision):
+    return (f"cs-drop-{w['nx']}x{w['ny']}-r{int(w['radius'])}-Tr{w['T_r']}-k{w['k']}"
+            f"-cfd{w['order']}-{precision}")
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id=None):
+        self.bus = bus_id
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 10:
+                continue
+            if self.bus and self.bus.lower()[-12:] not in parts[1].lower():
+                continue
+            rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[6 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def bus_id(dev):
+    import torch
+    p = torch.cuda.get_device_properties(dev)
+    try:
+        return f"{p.pci_domain_id:08x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}"
+    except Exception:
+        return None
+
+
+def cpu_baseline(w, target_s=12.0):
+    """The FP64 C oracle, single thread, on a bounded sample of the same workload:
+    as many full-grid time steps as fit in about target_s seconds."""
+    from oracle import OracleSim, thermo
+    from paper_1906_09530_gb300 import workloads as W
+    Tc, _ = thermo.critical_point()
+    rg, rl = thermo.maxwell(w["T_r"])
+    rho = W.drop(w["nx"], w["ny"], rg, rl, w["radius"], w["width"])
+    o = OracleSim(w["nx"], w["ny"], w["T_r"] * Tc, w["kappa"], w["tau"], w["k"], w["order"])
+    o.set_fields(rho)
+    t0 = time.perf_counter()
+    o.step(1)
+    dt1 = time.perf_counter() - t0
+    n = max(1, min(200, int(target_s / max(dt1, 1e-6)) - 1))
+    t0 = time.perf_counter()
+    o.step(n)
+    dt = time.perf_counter() - t0
+    mlups = w["nx"] * w["ny"] * n / dt / 1e6
+    return {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{n} full {w['nx']}x{w['ny']} FP64 time steps of the same drop "
+                      f"(after 1 untimed), plain C oracle, 1 thread, {dt:.1f} s"}
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from oracle import OracleSim, thermo
+    from paper_1906_09530_gb300 import workloads as W
+    Tc, _ = thermo.critical_point()
+    rg, rl = thermo.maxwell(w["T_r"])
+    rho = W.drop(w["nx"], w["ny"], rg, rl, w["radius"], w["width"])
+    o = OracleSim(w["nx"], w["ny"], w["T_r"] * Tc, w["kappa"], w["tau"], w["k"], w["order"])
+    o.set_fields(rho)
+    # each reference step is one full-grid oracle step; the count is bounded so
+    # that the run ends within about three minutes
+    t0 = time.perf_counter()
+    o.step(1)
+    per = time.perf_counter() - t0
+    warm = min(args.warmup, 1)
+    budget = 150.0
+    k = max(1, min(args.steps, int(budget / max(per, 1e-6))))
+    if warm > 1:
+        o.step(warm - 1)
+    t0 = time.perf_counter()
+    o.step(k)
+    dt = time.perf_counter() - t0
+    N = w["nx"] * w["ny"]
+    val = N * k / dt / 1e6
+    line = {"metric": METRIC, "value": val, "unit": "MLUPS", "impl": "reference",
+            "n_gpus": args.gpus, "steps": k, "warmup": warm, "ms_per_step": dt / k * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(w, "fp64")},
+            "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": f"{k} full-grid FP64 oracle steps (of {args.steps} "
+                                       "asked; bounded to ~150 s), 1 thread"},
+            "e2e": {"value": val, "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=100)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--size", type=int, default=1024)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    w = dict(WORKLOAD)
+    if args.size != 1024:
+        s = args.size / 1024
+        w.update(nx=args.size, ny=args.size, radius=w["radius"] * s)
+    if args.impl == "reference":
+        return run_reference(args, w)
+    if args.warmup < 3:
+        raise SystemExit("at least 3 warm-up steps")
+
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import paper_1906_09530_gb300 as P
+    from paper_1906_09530_gb300 import workloads as W
+    rg, rl = P.lbm_maxwell(w["T_r"])
+    rho0 = W.drop(w["nx"], w["ny"], rg, rl, w["radius"], w["width"])
+    N = w["nx"] * w["ny"]
+    sim = P.Simulation(w["nx"], w["ny"], w["T_r"], w["kappa"], w["tau"], w["k"],
+                       fd_order=w["order"], precision=args.precision)
+    sim.set_fields(rho0)
+    sim.step(args.warmup)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(bus_id(local))
+    barrier()
+    pass_ms = np.zeros((args.steps, 5))
+    for i in range(args.steps):
+        flush.zero_()
+        pass_ms[i] = sim.step_timed()
+    barrier()
+    clk = clocks.stop()
+    step_ms = pass_ms.sum(axis=1)
+    total_s = step_ms.sum() / 1e3
+    if dist is not None:
+        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = world * N * args.steps / total_s / 1e6
+
+    # back-to-back CUDA-graph steps without flushing (context only)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kb = max(2, args.steps // 2 * 2)
+    torch.cuda.synchronize()
+    ev0.record()
+    sim.step_async(kb)
+    ev1.record()
+    sim.check()
+    graph_mlups = N * kb / (ev0.elapsed_time(ev1) / 1e3) / 1e6
+
+    # e2e through the public host API, pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        h_rho = torch.from_numpy(rho0).pin_memory().numpy()
+        outs = [torch.empty((w["ny"], w["nx"]), dtype=torch.float64).pin_memory().numpy()
+                for _ in range(4)]
+        from paper_1906_09530_gb300._binding import _check, _hptr, lib
+        barrier()
+        t0 = time.perf_counter()
+        _check(lib().lbm_set_fields(sim.ctx, _hptr(h_rho), None, None), "lbm_set_fields")
+        _check(lib().lbm_step(sim.ctx, args.steps), "lbm_step")
+        _check(lib().lbm_fields(sim.ctx, *[_hptr(a) for a in outs]), "lbm_fields")
+        dt = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": world * N * args.steps / dt / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": N * 8 / args.steps,
+               "d2h_bytes_per_step": 4 * N * 8 / args.steps,
+               "what": "lbm_set_fields(host rho) + lbm_step(K) + lbm_fields(rho, vx, vy, "
+                       "mu to host), wall clock; bytes per step = run totals / K"}
+
+    mean_pass = pass_ms.mean(axis=0)
+    pb = pass_bytes(args.precision)
+    peak, peak_kind = load_peaks()
+    dom = int(np.argmax(mean_pass))
+    passes = {}
+    for i, nm in enumerate(PASS_NAMES):
+        gbs = pb[i] * N / (mean_pass[i] / 1e3) / 1e9
+        passes[nm] = {"ms": round(float(mean_pass[i]), 5), "alg_bytes_per_node": pb[i],
+                      "GB/s": round(gbs, 1), "frac_hbm": round(gbs / peak, 4)}
+    ach = pb[dom] * N / (mean_pass[dom] / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": PASS_NAMES[dom], "achieved": ach, "peak": peak,
+                "unit": "GB/s", "frac": ach / peak, "traffic": None,
+                "peak_kind": f"{peak_kind} copy bandwidth",
+                "alg_bytes_per_launch": pb[dom] * N}
+    step_gbs = sum(pb) * N / (float(step_ms.mean()) / 1e3) / 1e9
+    line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": float(step_ms.mean()), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+            "data": "synthetic",
+            "config": {"workload": workload_name(w, args.precision), "nodes": N,
+                       "l2": "512 MB write between timed steps (L2 flushed)",
+                       "parallelism": f"replicas{world}" if world > 1 else "single"},
+            "roofline": roofline,
+            "step_roofline": {"alg_bytes_per_node": sum(pb), "achieved_GB/s": step_gbs,
+                              "frac": step_gbs / peak},
+            "passes": passes,
+            "graph_back_to_back_mlups": graph_mlups,
+            "e2e": e2e, "gpu_launches": 5 * args.steps, "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

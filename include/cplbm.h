@@ -1,0 +1,190 @@
+/*
+ * cplbm.h -- C ABI of the GB300 (sm_103a) chemical-potential multiphase
+ * lattice Boltzmann library.
+ *
+ * The method is that of Wen, Zhao, Qiu, Ye and Shan, "Chemical-potential
+ * multiphase lattice Boltzmann method with superlarge density ratios"
+ * (arXiv:1906.09530).  One time step, in the paper's notation (mesh space,
+ * Sec. 4.1: grid step 1, time step 1, lattice c_s^2 = 1/3):
+ *
+ *   rho = sum_i f_i,  rho u = sum_i e_i f_i                           Eq. 3
+ *   d_x rho, d_y rho by the compact scheme, periodic lines           Eqs. 37-39
+ *   d_xx rho = D_x(D_x rho), d_yy rho = D_y(D_y rho)                 Sec. 4.3
+ *   mu-hat = k^2 mu0(rho; T) - kappa-hat (d_xx rho + d_yy rho)       Eqs. 21, 33
+ *   mu-hat <- min(mu-hat, k^2 mu_max) for the first mu_cap_steps     Sec. 5.6
+ *   F = -rho grad(mu-hat) + c_s^2 grad(rho)                          Eq. 12
+ *   F_i = f_i^eq(rho, u + F/rho) - f_i^eq(rho, u)                    Eq. 5
+ *   f_i(x + e_i, t + 1) = f_i - (f_i - f_i^eq(rho, u))/tau + F_i     Eqs. 1-2
+ *
+ * Conventions for every call:
+ *   - Fields are row-major [ny][nx] (x fastest); populations are
+ *     structure-of-arrays [9][ny][nx] in the velocity order of Sec. 2:
+ *     (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1).
+ *   - "h_" pointers are host memory, "d_" pointers device memory of the
+ *     current CUDA device.  The caller owns every pointer it passes.
+ *   - Every call that can fail returns an lbm_status; LBM_OK is 0.
+ *   - All device work runs on the CUDA stream given to lbm_init.
+ *   - There is no CPU fallback: without a usable CUDA device every call that
+ *     needs one returns LBM_ECUDA.
+ */
+#ifndef CPLBM_H
+#define CPLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx; /* opaque, owned by the library */
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_EINVAL = 1,    /* an argument is out of range, or a call came out of order */
+    LBM_ENOMEM = 2,    /* workspace too small, or host allocation failed */
+    LBM_ECUDA = 3,     /* a CUDA runtime call failed */
+    LBM_EUNSTABLE = 4, /* the device flagged rho <= 0, a non-finite value or the
+                          EOS pole (b rho / 4 >= 1); see lbm_failed_step() */
+    LBM_ETIMEOUT = 5,  /* device work did not finish within the wait limit */
+    LBM_ENOTIMPL = 6   /* option recognised but not built (e.g. non-periodic) */
+} lbm_status;
+
+/* Equation of state.  Only Carnahan-Starling is on the hot path. */
+enum { LBM_EOS_CS = 0 };
+
+/* Precision of the populations.  FP64: everything in double.  MIXED: the
+ * populations and the collide-stream pass in float; density, its compact-FD
+ * derivatives, the chemical potential, the force and all reductions in double. */
+enum { LBM_PREC_FP64 = 0, LBM_PREC_MIXED = 1 };
+
+typedef struct {
+    int32_t nx, ny;                 /* lattice size, each >= 8 */
+    int32_t periodic_x, periodic_y; /* must both be 1 (walls: LBM_ENOTIMPL) */
+} lbm_grid;
+
+typedef struct {
+    int32_t kind;          /* LBM_EOS_CS */
+    double a, b, R, omega; /* Eq. 20: the paper's CS values are a=1, b=4, R=1;
+                              omega (acentric factor) is unused by CS */
+} lbm_eos;
+
+typedef struct {
+    int32_t prec;         /* LBM_PREC_FP64 or LBM_PREC_MIXED */
+    int32_t fd_order;     /* 4 (alpha = 1/4) or 6 (alpha = 1/3, Eq. 39) */
+    double mu_max;        /* chemical-potential upper limit in momentum-space
+                             units (Sec. 5.6); +INFINITY switches it off */
+    int64_t mu_cap_steps; /* the limit acts while the time level t < mu_cap_steps */
+} lbm_opts;
+
+/* Bytes of device workspace lbm_init needs for this grid and options, or 0
+ * if the arguments are invalid.  Layout: two population buffers, seven FP64
+ * fields (rho, d_x rho, d_y rho, d_xx rho, mu-hat, F_x, F_y), reduction
+ * partials and a small device state block, each 256-byte aligned. */
+size_t lbm_workspace_bytes(const lbm_grid *grid, const lbm_opts *opts);
+
+/* Create a simulation context.
+ *   grid, eos, opts   see above (copied; the caller keeps ownership)
+ *   T_r               reduced temperature T/T_c in (0, 1) (Sec. 3.2); T_c is
+ *                     solved from the EOS on the host
+ *   kappa             the mesh-space kappa-hat of Eq. 33, > 0
+ *   tau               BGK relaxation time of Eq. 1, > 0.5
+ *   mesh_coeff        the proportional coefficient k of Eq. 25, in (0, 1]
+ *   d_workspace       device memory of lbm_workspace_bytes() bytes, 256-byte
+ *                     aligned, owned by the caller, which must keep it alive
+ *                     until lbm_free
+ *   cuda_stream       a cudaStream_t (NULL = the legacy default stream); the
+ *                     caller keeps ownership
+ * Nothing runs on the device until lbm_set_fields.  On error *out is NULL. */
+lbm_status lbm_init(lbm_ctx **out, const lbm_grid *grid, const lbm_eos *eos, double T_r,
+                    double kappa, double tau, double mesh_coeff, const lbm_opts *opts,
+                    void *d_workspace, size_t ws_bytes, void *cuda_stream);
+
+/* Initial state from host FP64 fields: f_i = f_i^eq(rho, u) (Eq. 2), time
+ * level 0, then the force of Eq. 12 is computed from rho.  h_ux / h_uy may be
+ * NULL (zero velocity).  Returns when the device work is done. */
+lbm_status lbm_set_fields(lbm_ctx *ctx, const double *h_rho, const double *h_ux,
+                          const double *h_uy);
+
+/* The same from device FP64 fields (enqueued on the stream; returns at once). */
+lbm_status lbm_set_fields_device(lbm_ctx *ctx, const double *d_rho, const double *d_ux,
+                                 const double *d_uy);
+
+/* Advance n >= 0 time steps.  Steps are enqueued (in CUDA graphs of two
+ * steps); the call then waits for the stream and checks the device error
+ * flag.  LBM_EUNSTABLE: some step produced a bad value, lbm_failed_step()
+ * names the first time level flagged, and the state is undefined until the
+ * next lbm_set_fields. */
+lbm_status lbm_step(lbm_ctx *ctx, int64_t n);
+
+/* Like lbm_step but returns right after enqueuing; lbm_check() later waits
+ * for the stream and reads the error flag. */
+lbm_status lbm_step_async(lbm_ctx *ctx, int64_t n);
+lbm_status lbm_check(lbm_ctx *ctx);
+
+/* Profiling: run one time step as direct launches (no graph) with a CUDA event
+ * recorded on the stream before and after each of its five passes, wait for
+ * it, and return the passes' durations in milliseconds:
+ *   pass_ms[0] collide-stream, [1] x-lines of rho, [2] y-lines of rho + mu-hat,
+ *   [3] x-lines of mu-hat + F_x, [4] y-lines of mu-hat + F_y. */
+lbm_status lbm_step_timed(lbm_ctx *ctx, float *pass_ms);
+
+/* Outputs of the current state to host FP64 [ny][nx] arrays, any may be NULL:
+ * rho (Eq. 3), the velocity v = u + F/(2 rho) (Sec. 2, after Eq. 5) and the
+ * mesh-space chemical potential mu-hat (Eq. 33).  Returns when copied. */
+lbm_status lbm_fields(lbm_ctx *ctx, double *h_rho, double *h_vx, double *h_vy,
+                      double *h_mu);
+
+/* The same into device FP64 arrays (enqueued; returns at once). */
+lbm_status lbm_fields_device(lbm_ctx *ctx, double *d_rho, double *d_vx, double *d_vy,
+                             double *d_mu);
+
+/* Checkpoint / resume: the populations as host FP64 [9][ny][nx] and the time
+ * level.  A resume on the same build and precision is bit-exact. */
+lbm_status lbm_get_populations(lbm_ctx *ctx, double *h_f, int64_t *t);
+lbm_status lbm_set_populations(lbm_ctx *ctx, const double *h_f, int64_t t);
+
+/* Diagnostics of the current state, FP64 reductions on the device: total mass
+ * sum(rho), max |v|, min rho, max rho.  Any output may be NULL. */
+lbm_status lbm_diag(lbm_ctx *ctx, double *mass, double *max_v, double *rho_min,
+                    double *rho_max);
+
+/* Critical point (T_c, rho_c) of the EOS: the point where dp0/drho and
+ * d2p0/drho2 both vanish (Sec. 3.2).  Host only. */
+lbm_status lbm_critical(const lbm_eos *eos, double *Tc, double *rhoc);
+
+/* Maxwell equal-area coexistence densities at reduced temperature T_r: equal
+ * pressure and equal chemical potential on the two stable branches (Sec. 5.1).
+ * Host only. */
+lbm_status lbm_maxwell(const lbm_eos *eos, double T_r, double *rho_g, double *rho_l);
+
+/* Stand-alone compact-FD derivative of a device FP64 field [ny][nx] along
+ * axis 0 (x) or 1 (y), periodic, Eqs. 37-38 with alpha = 1/4 (fd_order 4) or
+ * 1/3 (fd_order 6, Eq. 39).  d_d1 receives D u; d_d2, if not NULL, receives
+ * D(D u) ("applying CFM twice", Sec. 4.3).  The outputs must not overlap the
+ * input.  Enqueued on cuda_stream; returns at once. */
+lbm_status lbm_cfd(const double *d_u, double *d_d1, double *d_d2, int32_t nx, int32_t ny,
+                   int32_t axis, int32_t fd_order, void *cuda_stream);
+
+/* Time level of the current state, and the first flagged time level after
+ * LBM_EUNSTABLE (-1 if none). */
+int64_t lbm_time(const lbm_ctx *ctx);
+int64_t lbm_failed_step(const lbm_ctx *ctx);
+
+/* Host wait limit, in seconds, for lbm_step / lbm_check / copies (default 600). */
+lbm_status lbm_set_timeout(lbm_ctx *ctx, double seconds);
+
+/* Segment lengths of the compact-FD line sweeps along x and y (0 = automatic).
+ * A tuning knob: results do not depend on it beyond rounding. */
+lbm_status lbm_set_line_segments(lbm_ctx *ctx, int32_t seg_x, int32_t seg_y);
+
+const char *lbm_strerror(lbm_status s);
+
+/* Release the context (not the workspace or the stream, which the caller owns). */
+void lbm_free(lbm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CPLBM_H */

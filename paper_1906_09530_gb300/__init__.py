@@ -1,2 +1,9 @@
 """GB300 (sm_103a) chemical-potential multiphase lattice Boltzmann method
-(Wen, Zhao, Qiu, Ye and Shan, arXiv:1906.09530)."""
+(Wen, Zhao, Qiu, Ye and Shan, arXiv:1906.09530).
+
+The compute path is the CUDA library libcplbm.so (C ABI in include/cplbm.h);
+this package is its ctypes binding plus the seeded synthetic workloads.
+"""
+from ._binding import (LBM_PREC_FP64, LBM_PREC_MIXED, LbmError, Simulation,  # noqa: F401
+                       cs_eos, lbm_cfd, lbm_critical, lbm_maxwell, lbm_strerror,
+                       lbm_workspace_bytes, lib)

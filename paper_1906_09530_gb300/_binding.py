@@ -1,0 +1,267 @@
+"""ctypes binding of libcplbm.so (include/cplbm.h): argument marshalling only.
+
+Every function named lbm_* here calls the C function of the same name.  Device
+memory and streams come from PyTorch (torch tensors' data_ptr() and
+torch.cuda streams); host arrays are numpy float64.  There is no fallback: if
+the library is not built, or the call fails, an exception is raised.
+"""
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+from . import _build
+
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ENOTIMPL = range(7)
+LBM_EOS_CS = 0
+LBM_PREC_FP64, LBM_PREC_MIXED = 0, 1
+
+
+class LbmGrid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("periodic_x", C.c_int32),
+                ("periodic_y", C.c_int32)]
+
+
+class LbmEos(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("a", C.c_double), ("b", C.c_double),
+                ("R", C.c_double), ("omega", C.c_double)]
+
+
+class LbmOpts(C.Structure):
+    _fields_ = [("prec", C.c_int32), ("fd_order", C.c_int32), ("mu_max", C.c_double),
+                ("mu_cap_steps", C.c_int64)]
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        super().__init__(f"{what}: {lbm_strerror(status)} (status {status})")
+
+
+_lib = None
+_vp, _dp, _i32, _i64 = C.c_void_p, C.POINTER(C.c_double), C.c_int32, C.c_int64
+
+
+def lib():
+    """The loaded library; raises ImportError if it has not been built."""
+    global _lib
+    if _lib is None:
+        path = _build.lib_path()
+        if not os.path.exists(path):
+            raise ImportError(
+                f"{path} is missing: build it with `python -m paper_1906_09530_gb300._build` "
+                "(there is no CPU fallback)")
+        L = C.CDLL(path)
+        sigs = {
+            "lbm_workspace_bytes": (C.c_size_t, [C.POINTER(LbmGrid), C.POINTER(LbmOpts)]),
+            "lbm_init": (C.c_int, [C.POINTER(_vp), C.POINTER(LbmGrid), C.POINTER(LbmEos),
+                                   C.c_double, C.c_double, C.c_double, C.c_double,
+                                   C.POINTER(LbmOpts), _vp, C.c_size_t, _vp]),
+            "lbm_set_fields": (C.c_int, [_vp, _vp, _vp, _vp]),
+            "lbm_set_fields_device": (C.c_int, [_vp, _vp, _vp, _vp]),
+            "lbm_step": (C.c_int, [_vp, _i64]),
+            "lbm_step_async": (C.c_int, [_vp, _i64]),
+            "lbm_check": (C.c_int, [_vp]),
+            "lbm_step_timed": (C.c_int, [_vp, C.POINTER(C.c_float)]),
+            "lbm_fields": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
+            "lbm_fields_device": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
+            "lbm_get_populations": (C.c_int, [_vp, _vp, C.POINTER(C.c_int64)]),
+            "lbm_set_populations": (C.c_int, [_vp, _vp, _i64]),
+            "lbm_diag": (C.c_int, [_vp, _dp, _dp, _dp, _dp]),
+            "lbm_critical": (C.c_int, [C.POINTER(LbmEos), _dp, _dp]),
+            "lbm_maxwell": (C.c_int, [C.POINTER(LbmEos), C.c_double, _dp, _dp]),
+            "lbm_cfd": (C.c_int, [_vp, _vp, _vp, _i32, _i32, _i32, _i32, _vp]),
+            "lbm_time": (C.c_int64, [_vp]),
+            "lbm_failed_step": (C.c_int64, [_vp]),
+            "lbm_set_timeout": (C.c_int, [_vp, C.c_double]),
+            "lbm_set_line_segments": (C.c_int, [_vp, _i32, _i32]),
+            "lbm_strerror": (C.c_char_p, [C.c_int]),
+            "lbm_free": (None, [_vp]),
+        }
+        for name, (res, args) in sigs.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def lbm_strerror(status):
+    return lib().lbm_strerror(status).decode()
+
+
+def _check(status, what):
+    if status != LBM_OK:
+        raise LbmError(status, what)
+
+
+def cs_eos(a=1.0, b=4.0, R=1.0):
+    """Carnahan-Starling EOS parameters (Eq. 20; the paper's values by default)."""
+    return LbmEos(LBM_EOS_CS, a, b, R, 0.0)
+
+
+def lbm_critical(eos=None):
+    """(T_c, rho_c) of the EOS, solved on the host by the library."""
+    tc, rc = C.c_double(), C.c_double()
+    _check(lib().lbm_critical(C.byref(eos or cs_eos()), C.byref(tc), C.byref(rc)),
+           "lbm_critical")
+    return tc.value, rc.value
+
+
+def lbm_maxwell(T_r, eos=None):
+    """Maxwell coexistence densities (rho_g, rho_l) at T_r, solved by the library."""
+    g, l = C.c_double(), C.c_double()
+    _check(lib().lbm_maxwell(C.byref(eos or cs_eos()), T_r, C.byref(g), C.byref(l)),
+           "lbm_maxwell")
+    return g.value, l.value
+
+
+def lbm_workspace_bytes(nx, ny, precision=LBM_PREC_FP64, fd_order=6):
+    g = LbmGrid(nx, ny, 1, 1)
+    o = LbmOpts(precision, fd_order, math.inf, 0)
+    return lib().lbm_workspace_bytes(C.byref(g), C.byref(o))
+
+
+def _dptr(t):
+    """Device pointer of a torch tensor (must be CUDA, float64, contiguous)."""
+    if t is None:
+        return None
+    import torch
+    assert t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+    return t.data_ptr()
+
+
+def _hptr(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data
+
+
+def lbm_cfd(u, axis, fd_order, second=False, stream=None):
+    """Compact-FD derivative(s) of a CUDA float64 tensor [ny][nx] along axis 0 (x)
+    or 1 (y): returns D u, and D(D u) if `second` (Eqs. 37-39)."""
+    import torch
+    ny, nx = u.shape
+    d1 = torch.empty_like(u)
+    d2 = torch.empty_like(u) if second else None
+    s = stream if stream is not None else torch.cuda.current_stream(u.device)
+    _check(lib().lbm_cfd(_dptr(u), _dptr(d1), _dptr(d2), nx, ny, axis, fd_order,
+                         s.cuda_stream), "lbm_cfd")
+    return (d1, d2) if second else d1
+
+
+class Simulation:
+    """One periodic D2Q9 run of the method on the current CUDA device.
+
+    Owns a torch uint8 workspace and the library context.  Host inputs/outputs are
+    numpy float64 [ny][nx]; device variants take/return torch float64 tensors.
+    """
+
+    def __init__(self, nx, ny, T_r, kappa, tau, mesh_coeff, fd_order=6,
+                 precision="fp64", mu_max=math.inf, mu_cap_steps=0, eos=None,
+                 device=None, stream=None):
+        import torch
+        self.nx, self.ny = nx, ny
+        self.device = torch.device(device if device is not None else "cuda")
+        prec = {"fp64": LBM_PREC_FP64, "mixed": LBM_PREC_MIXED}[precision]
+        self.grid = LbmGrid(nx, ny, 1, 1)
+        self.opts = LbmOpts(prec, fd_order, mu_max, mu_cap_steps)
+        self.eos = eos or cs_eos()
+        nbytes = lib().lbm_workspace_bytes(C.byref(self.grid), C.byref(self.opts))
+        if nbytes == 0:
+            raise LbmError(LBM_EINVAL, "lbm_workspace_bytes")
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream()
+            self.ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            self.ctx = C.c_void_p()
+            _check(lib().lbm_init(C.byref(self.ctx), C.byref(self.grid), C.byref(self.eos),
+                                  T_r, kappa, tau, mesh_coeff, C.byref(self.opts),
+                                  self.ws.data_ptr(), nbytes, self.stream.cuda_stream),
+                   "lbm_init")
+
+    # -- state ------------------------------------------------------------
+    def set_fields(self, rho, ux=None, uy=None):
+        """Initial state from host numpy arrays (f = f^eq, Eq. 2)."""
+        arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+                for a in (rho, ux, uy)]
+        for a in arrs:
+            if a is not None and a.size != self.nx * self.ny:
+                raise ValueError("field size does not match the grid")
+        _check(lib().lbm_set_fields(self.ctx, *[_hptr(a) for a in arrs]), "lbm_set_fields")
+
+    def set_fields_device(self, rho, ux=None, uy=None):
+        _check(lib().lbm_set_fields_device(self.ctx, _dptr(rho), _dptr(ux), _dptr(uy)),
+               "lbm_set_fields_device")
+
+    def step(self, n=1):
+        _check(lib().lbm_step(self.ctx, n), "lbm_step")
+
+    def step_async(self, n=1):
+        _check(lib().lbm_step_async(self.ctx, n), "lbm_step_async")
+
+    def step_timed(self):
+        """One step with per-pass CUDA-event timing; returns 5 durations in ms."""
+        ms = (C.c_float * 5)()
+        _check(lib().lbm_step_timed(self.ctx, ms), "lbm_step_timed")
+        return list(ms)
+
+    def check(self):
+        _check(lib().lbm_check(self.ctx), "lbm_check")
+
+    @property
+    def t(self):
+        return lib().lbm_time(self.ctx)
+
+    @property
+    def failed_step(self):
+        return lib().lbm_failed_step(self.ctx)
+
+    def fields(self):
+        """(rho, vx, vy, mu_hat) as host numpy arrays; v = u + F/(2 rho)."""
+        out = [np.empty((self.ny, self.nx)) for _ in range(4)]
+        _check(lib().lbm_fields(self.ctx, *[_hptr(a) for a in out]), "lbm_fields")
+        return tuple(out)
+
+    def fields_device(self):
+        import torch
+        out = [torch.empty((self.ny, self.nx), dtype=torch.float64, device=self.device)
+               for _ in range(4)]
+        _check(lib().lbm_fields_device(self.ctx, *[_dptr(a) for a in out]),
+               "lbm_fields_device")
+        return tuple(out)
+
+    def get_populations(self):
+        f = np.empty((9, self.ny, self.nx))
+        t = C.c_int64()
+        _check(lib().lbm_get_populations(self.ctx, _hptr(f), C.byref(t)),
+               "lbm_get_populations")
+        return f, t.value
+
+    def set_populations(self, f, t=0):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        _check(lib().lbm_set_populations(self.ctx, _hptr(f), t), "lbm_set_populations")
+
+    def diag(self):
+        """(mass, max|v|, rho_min, rho_max), FP64 device reductions."""
+        v = [C.c_double() for _ in range(4)]
+        _check(lib().lbm_diag(self.ctx, *[C.byref(x) for x in v]), "lbm_diag")
+        return tuple(x.value for x in v)
+
+    def set_timeout(self, seconds):
+        _check(lib().lbm_set_timeout(self.ctx, seconds), "lbm_set_timeout")
+
+    def set_line_segments(self, seg_x, seg_y):
+        _check(lib().lbm_set_line_segments(self.ctx, seg_x, seg_y), "lbm_set_line_segments")
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lib().lbm_free(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

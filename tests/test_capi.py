@@ -1,0 +1,117 @@
+"""The C-ABI library without a GPU: it loads, exports every symbol the header
+declares, validates arguments before touching CUDA, and its host
+thermodynamics agree with the oracle's (two independent solvers)."""
+import ctypes as C
+import math
+import os
+import re
+
+import pytest
+
+import paper_1906_09530_gb300 as P
+from paper_1906_09530_gb300 import _binding as B
+from oracle import thermo
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "cplbm.h")
+
+
+def declared_symbols():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = P.lib()
+    names = declared_symbols()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_critical_point_agrees_with_oracle():
+    tc, rc = P.lbm_critical()
+    otc, orc = thermo.critical_point()
+    assert tc == pytest.approx(otc, rel=1e-12)
+    assert rc == pytest.approx(orc, rel=1e-10)
+    # other a, b, R
+    eos = P.cs_eos(2.0, 3.0, 1.5)
+    tc2, rc2 = P.lbm_critical(eos)
+    otc2, orc2 = thermo.critical_point(2.0, 3.0, 1.5)
+    assert tc2 == pytest.approx(otc2, rel=1e-12) and rc2 == pytest.approx(orc2, rel=1e-10)
+
+
+@pytest.mark.parametrize("T_r", [0.95, 0.7, 0.6, 0.5, 0.45, 0.35, 0.3, 0.2, 0.16])
+def test_maxwell_agrees_with_oracle(T_r):
+    g, l = P.lbm_maxwell(T_r)
+    og, ol = thermo.maxwell(T_r)
+    assert l == pytest.approx(ol, rel=1e-12)
+    assert g == pytest.approx(og, rel=1e-9)
+
+
+def test_workspace_bytes_validation():
+    assert P.lbm_workspace_bytes(1024, 1024, P.LBM_PREC_MIXED, 6) > 9 * 1024 * 1024 * 4 * 2
+    assert P.lbm_workspace_bytes(1024, 1024, P.LBM_PREC_FP64, 6) > 9 * 1024 * 1024 * 8 * 2
+    assert P.lbm_workspace_bytes(4, 1024, P.LBM_PREC_FP64, 6) == 0     # nx < 8
+    assert P.lbm_workspace_bytes(64, 64, P.LBM_PREC_FP64, 5) == 0      # bad order
+    assert P.lbm_workspace_bytes(64, 64, 7, 6) == 0                    # bad precision
+
+
+def _init(**kw):
+    args = dict(nx=64, ny=64, T_r=0.6, kappa=0.1, tau=1.0, k=0.5, order=6, ws=256, wsb=1 << 40)
+    args.update(kw)
+    ctx = C.c_void_p()
+    g = B.LbmGrid(args["nx"], args["ny"], args.get("px", 1), args.get("py", 1))
+    o = B.LbmOpts(B.LBM_PREC_FP64, args["order"], math.inf, 0)
+    st = P.lib().lbm_init(C.byref(ctx), C.byref(g), C.byref(P.cs_eos()), args["T_r"],
+                          args["kappa"], args["tau"], args["k"], C.byref(o), args["ws"],
+                          args["wsb"], None)
+    return st, ctx
+
+
+@pytest.mark.parametrize("bad", [dict(tau=0.5), dict(kappa=0.0), dict(k=0.0), dict(k=1.5),
+                                 dict(T_r=1.0), dict(T_r=0.0), dict(nx=7), dict(order=8),
+                                 dict(ws=0), dict(ws=100)])
+def test_init_rejects_bad_arguments(bad):
+    st, ctx = _init(**bad)
+    assert st == B.LBM_EINVAL and not ctx.value
+
+
+def test_init_small_workspace_and_walls():
+    st, _ = _init(wsb=16)
+    assert st == B.LBM_ENOMEM
+    st, _ = _init(px=0)
+    assert st == B.LBM_ENOTIMPL
+
+
+def test_cfd_rejects_bad_arguments():
+    lib = P.lib()
+    assert lib.lbm_cfd(None, 256, None, 8, 8, 0, 6, None) == B.LBM_EINVAL
+    assert lib.lbm_cfd(256, 512, None, 8, 8, 2, 6, None) == B.LBM_EINVAL
+    assert lib.lbm_cfd(256, 512, None, 8, 8, 0, 5, None) == B.LBM_EINVAL
+    assert lib.lbm_cfd(256, 256, None, 8, 8, 0, 6, None) == B.LBM_EINVAL  # aliasing
+
+
+def test_strerror_and_null_ctx():
+    assert "unstable" in P.lbm_strerror(B.LBM_EUNSTABLE)
+    lib = P.lib()
+    assert lib.lbm_step(None, 1) == B.LBM_EINVAL
+    assert lib.lbm_time(None) == -1
+    lib.lbm_free(None)
+
+
+def test_oracle_and_library_share_nothing():
+    """The CUDA library and its binding never import, include or load the oracle,
+    and the oracle never imports the library."""
+    root = os.path.dirname(os.path.dirname(__file__))
+    pkg = os.path.join(root, "paper_1906_09530_gb300")
+    bad_pkg = re.compile(r"^\s*(import|from)\s+oracle\b|#include\s*[<\"].*oracle|liboracle",
+                         re.M)
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".cpp", ".h")):
+                assert not bad_pkg.search(open(os.path.join(dirpath, f)).read()), f
+    bad_orc = re.compile(r"paper_1906_09530_gb300|cplbm\.h|libcplbm")
+    for f in os.listdir(os.path.join(root, "oracle")):
+        if f.endswith((".py", ".c")):
+            assert not bad_orc.search(open(os.path.join(root, "oracle", f)).read()), f

@@ -1,0 +1,268 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle on
+the same seeded inputs.
+
+Tolerances (written here, justified by the arithmetic):
+  * compact-FD solves: |d_gpu - d_oracle| <= 1e-13 max|d_oracle|.  Both are FP64;
+    the factorised sweep truncates recursions whose tail weight is < 1e-18, so
+    only rounding-order differences remain.
+  * force stage at t = 0: mu-hat and v = F/(2 rho) within 1e-12 (relative to max).
+  * full FP64 steps: pointwise rho relative error <= 1e-10 after 1000 steps
+    (the FP64 path's stated tolerance), v and mu-hat within 1e-8 of their max.
+  * mixed path: populations in FP32 (unit rounding 6e-8); after 200 steps rho
+    stays within 1e-5 relative of the FP64 oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from tests import cases
+
+pytestmark = pytest.mark.gpu
+
+
+def rel_point(a, b):
+    return float(np.max(np.abs(a - b) / np.abs(b)))
+
+
+@pytest.mark.parametrize("order", [4, 6])
+@pytest.mark.parametrize("shape", [(8, 8), (37, 50), (128, 96), (1024, 64), (5, 300)])
+@pytest.mark.parametrize("axis", [0, 1])
+def test_cfd_parity(cuda, order, shape, axis):
+    from oracle import cfd_alpha, cfd_line
+    from paper_1906_09530_gb300 import lbm_cfd
+    torch = cuda
+    ny, nx = shape
+    rng = np.random.default_rng(nx * 1000 + ny + order)
+    u = rng.standard_normal((ny, nx)) + 3.0
+    d1, d2 = lbm_cfd(torch.from_numpy(u).cuda(), axis, order, second=True)
+    torch.cuda.synchronize()
+    d1, d2 = d1.cpu().numpy(), d2.cpu().numpy()
+    alpha = cfd_alpha(order)
+    if axis == 0:
+        r1 = np.stack([cfd_line(u[j], alpha) for j in range(ny)])
+    else:
+        r1 = np.stack([cfd_line(u[:, i], alpha) for i in range(nx)], axis=1)
+    if axis == 0:
+        r2 = np.stack([cfd_line(r1[j], alpha) for j in range(ny)])
+    else:
+        r2 = np.stack([cfd_line(r1[:, i], alpha) for i in range(nx)], axis=1)
+    assert np.abs(d1 - r1).max() <= 1e-13 * np.abs(r1).max()
+    assert np.abs(d2 - r2).max() <= 1e-13 * np.abs(r2).max()
+    # first derivative alone (the single-recursion kernel)
+    d1b = lbm_cfd(torch.from_numpy(u).cuda(), axis, order, second=False).cpu().numpy()
+    assert np.abs(d1b - r1).max() <= 1e-13 * np.abs(r1).max()
+
+
+@pytest.mark.parametrize("case", ["config1", "ragged4", "ragged6"])
+def test_force_stage_parity_t0(cuda, case):
+    c = {"config1": cases.config1(), "ragged4": cases.ragged(order=4),
+         "ragged6": cases.ragged(order=6)}[case]
+    g = cases.gpu_sim(c)
+    g.set_fields(c["rho"])
+    rho, vx, vy, mu = g.fields()
+    o = cases.oracle_sim(c)
+    o.set_fields(c["rho"])
+    orho, ovx, ovy, omu, _, _ = o.fields()
+    assert rel_point(rho, orho) <= 1e-14
+    assert cases.rel_err(mu, omu) <= 1e-12
+    assert np.abs(vx - ovx).max() <= 1e-12 * np.abs(ovx).max()
+    assert np.abs(vy - ovy).max() <= 1e-12 * np.abs(ovy).max()
+
+
+def test_config1_1000_steps_fp64(cuda):
+    """128^2 drop, CS T_r = 0.7, k = 1, 4th order: rho within 1e-10 after 1000 steps."""
+    c = cases.config1()
+    g = cases.gpu_sim(c)
+    g.set_fields(c["rho"])
+    g.step(1000)
+    rho, vx, vy, mu = g.fields()
+    o = cases.oracle_sim(c)
+    o.set_fields(c["rho"])
+    o.step(1000)
+    orho, ovx, ovy, omu, _, _ = o.fields()
+    assert g.t == 1000
+    assert rel_point(rho, orho) <= 1e-10
+    assert np.abs(vx - ovx).max() <= 1e-8 * np.abs(ovx).max()
+    assert np.abs(mu - omu).max() <= 1e-8 * np.abs(omu).max()
+
+
+@pytest.mark.parametrize("order", [4, 6])
+def test_ragged_grid_steps(cuda, order):
+    """37 x 29: every tile and line segment is ragged; odd step count exercises
+    the single-step path after the two-step graphs."""
+    c = cases.ragged(order=order)
+    g = cases.gpu_sim(c)
+    g.set_fields(c["rho"])
+    g.step(201)
+    o = cases.oracle_sim(c)
+    o.set_fields(c["rho"])
+    o.step(201)
+    assert rel_point(g.fields()[0], o.fields()[0]) <= 1e-11
+
+
+def test_velocity_init_parity(cuda):
+    """Initial velocity (a drop translated at u_x = 0.05, the Galilean variant)."""
+    c = cases.ragged(nx=48, ny=40, order=6)
+    ux = np.full((40, 48), 0.05)
+    uy = np.full((40, 48), -0.02)
+    g = cases.gpu_sim(c)
+    g.set_fields(c["rho"], ux, uy)
+    g.step(100)
+    o = cases.oracle_sim(c)
+    o.set_fields(c["rho"], ux, uy)
+    o.step(100)
+    rho, vx, vy, _ = g.fields()
+    orho, ovx, ovy, _, _, _ = o.fields()
+    assert rel_point(rho, orho) <= 1e-11
+    assert np.abs(vx - ovx).max() <= 1e-10
+
+
+def test_mu_cap_parity(cuda):
+    """Sec. 5.6 upper limit active for the first 7 steps."""
+    c = cases.ragged(nx=40, ny=40, order=6)
+    kw = dict(mu_max=-0.55, mu_cap_steps=7)
+    g = cases.gpu_sim(c, **kw)
+    g.set_fields(c["rho"])
+    o = cases.oracle_sim(c, **kw)
+    o.set_fields(c["rho"])
+    mu0 = g.fields()[3]
+    assert mu0.max() <= 0.25 * -0.55 + 1e-15
+    g.step(20)
+    o.step(20)
+    assert rel_point(g.fields()[0], o.fields()[0]) <= 1e-11
+
+
+def test_config2_full_size_steps(cuda):
+    """1024^2, T_r = 0.5, k = 0.5, 6th order, the launch configuration the benchmark
+    times: every node after 4 steps against the oracle."""
+    c = cases.config2(0.5)
+    g = cases.gpu_sim(c)
+    g.set_fields(c["rho"])
+    g.step(4)
+    o = cases.oracle_sim(c)
+    o.set_fields(c["rho"])
+    o.step(4)
+    assert rel_point(g.fields()[0], o.fields()[0]) <= 1e-12
+
+
+def test_config2_mixed_full_size_steps(cuda):
+    c = cases.config2(0.45)
+    g = cases.gpu_sim(c, precision="mixed")
+    g.set_fields(c["rho"])
+    g.step(4)
+    o = cases.oracle_sim(c)
+    o.set_fields(c["rho"])
+    o.step(4)
+    assert rel_point(g.fields()[0], o.fields()[0]) <= 2e-6
+
+
+def test_mixed_close_to_oracle(cuda):
+    c = cases.config1()
+    g = cases.gpu_sim(c, precision="mixed")
+    g.set_fields(c["rho"])
+    g.step(200)
+    o = cases.oracle_sim(c)
+    o.set_fields(c["rho"])
+    o.step(200)
+    assert rel_point(g.fields()[0], o.fields()[0]) <= 1e-5
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
+def test_mass_conservation_large(cuda, precision, tol):
+    c = cases.config2(0.5, n=2048)
+    g = cases.gpu_sim(c, precision=precision)
+    g.set_fields(c["rho"])
+    m0 = g.diag()[0]
+    assert m0 == pytest.approx(c["rho"].sum(), rel=1e-7 if precision == "mixed" else 1e-13)
+    g.step(100)
+    assert abs(g.diag()[0] - m0) / m0 <= tol
+
+
+def test_uniform_rest_fixed_point(cuda):
+    from paper_1906_09530_gb300 import Simulation
+    g = Simulation(64, 48, 0.6, 0.1, 0.8, 0.5, fd_order=6)
+    g.set_fields(np.full((48, 64), 0.25))
+    g.step(20)
+    rho, vx, vy, mu = g.fields()
+    assert np.allclose(rho, 0.25, rtol=1e-14, atol=0)
+    assert np.abs(vx).max() < 1e-15 and np.abs(vy).max() < 1e-15
+
+
+def test_diag_matches_fields(cuda):
+    c = cases.ragged(nx=64, ny=64)
+    g = cases.gpu_sim(c)
+    g.set_fields(c["rho"])
+    g.step(10)
+    rho, vx, vy, _ = g.fields()
+    mass, vmax, rmin, rmax = g.diag()
+    assert mass == pytest.approx(rho.sum(), rel=1e-13)
+    assert vmax == pytest.approx(np.hypot(vx, vy).max(), rel=1e-12)
+    assert (rmin, rmax) == (rho.min(), rho.max())
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_checkpoint_resume_bitexact(cuda, precision):
+    c = cases.ragged(nx=64, ny=40)
+    g = cases.gpu_sim(c, precision=precision)
+    g.set_fields(c["rho"])
+    g.step(15)
+    f, t = g.get_populations()
+    assert t == 15
+    g.step(11)
+    a = g.fields()
+    g.set_populations(f, t)
+    assert g.t == 15
+    g.step(11)
+    b = g.fields()
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def test_unstable_is_reported_not_trapped(cuda):
+    """A host-written bad density (negative at one node) makes the device raise
+    its error flag; the call returns LBM_EUNSTABLE and the context stays usable."""
+    from paper_1906_09530_gb300 import LbmError
+    from paper_1906_09530_gb300._binding import LBM_EUNSTABLE
+    c = cases.ragged(nx=32, ny=32)
+    rho = c["rho"].copy()
+    rho[5, 7] = -1e-3
+    g = cases.gpu_sim(c)
+    with pytest.raises(LbmError) as ei:
+        g.set_fields(rho)
+        g.step(3)
+    assert ei.value.status == LBM_EUNSTABLE
+    assert 0 <= g.failed_step <= 3
+    g.set_fields(c["rho"])  # recovers
+    g.step(2)
+
+
+def test_bounded_wait_reports_timeout(cuda):
+    """The host wait has a limit: a tiny limit on a long queue returns
+    LBM_ETIMEOUT (the work itself finishes normally afterwards)."""
+    from paper_1906_09530_gb300 import LbmError
+    from paper_1906_09530_gb300._binding import LBM_ETIMEOUT
+    c = cases.config2(0.5, n=1024)
+    g = cases.gpu_sim(c)
+    g.set_fields(c["rho"])
+    g.set_timeout(1e-7)
+    with pytest.raises(LbmError) as ei:
+        g.step(200)
+    assert ei.value.status == LBM_ETIMEOUT
+    g.set_timeout(600)
+    g.check()
+    assert g.t == 200
+
+
+def test_set_fields_device_matches_host(cuda):
+    torch = cuda
+    c = cases.ragged(nx=64, ny=64)
+    a = cases.gpu_sim(c)
+    a.set_fields(c["rho"])
+    a.step(10)
+    b = cases.gpu_sim(c)
+    b.set_fields_device(torch.from_numpy(c["rho"]).cuda())
+    b.step(10)
+    ra = a.fields()[0]
+    rb = b.fields_device()[0].cpu().numpy()
+    assert np.array_equal(ra, rb)
