@@ -53,9 +53,11 @@ typedef enum {
 /* Equation of state.  Only Carnahan-Starling is on the hot path. */
 enum { LBM_EOS_CS = 0 };
 
-/* Precision of the populations.  FP64: everything in double.  MIXED: the
- * populations and the collide-stream pass in float; density, its compact-FD
- * derivatives, the chemical potential, the force and all reductions in double. */
+/* Precision.  FP64: everything in double.  MIXED: populations and the
+ * collide-stream pass in float; the density kept exactly as a double-float pair
+ * (hi + lo floats) and its first compact-FD derivatives computed in double-float
+ * arithmetic; second derivatives, chemical potential and force in float; all
+ * reductions and outputs in double. */
 enum { LBM_PREC_FP64 = 0, LBM_PREC_MIXED = 1 };
 
 typedef struct {
@@ -78,9 +80,10 @@ typedef struct {
 } lbm_opts;
 
 /* Bytes of device workspace lbm_init needs for this grid and options, or 0
- * if the arguments are invalid.  Layout: two population buffers, seven FP64
- * fields (rho, d_x rho, d_y rho, d_xx rho, mu-hat, F_x, F_y), reduction
- * partials and a small device state block, each 256-byte aligned. */
+ * if the arguments are invalid.  Layout: two population buffers, the fields
+ * (FP64: rho, d_x rho, d_y rho, d_xx rho, mu-hat, F_x, F_y; MIXED: rho hi, rho lo
+ * and the same six as FP32), reduction partials and a small device state
+ * block, each 256-byte aligned. */
 size_t lbm_workspace_bytes(const lbm_grid *grid, const lbm_opts *opts);
 
 /* Create a simulation context.
@@ -166,6 +169,16 @@ lbm_status lbm_maxwell(const lbm_eos *eos, double T_r, double *rho_g, double *rh
 lbm_status lbm_cfd(const double *d_u, double *d_d1, double *d_d2, int32_t nx, int32_t ny,
                    int32_t axis, int32_t fd_order, void *cuda_stream);
 
+/* The mixed path's line solve, stand-alone: derivative along axis 0 (x) or 1 (y)
+ * of a periodic field given as an unevaluated double-float sum hi + lo of two
+ * device FP32 arrays [ny][nx] (the form the mixed path keeps the density in).
+ * d_d1 receives D u computed in double-float arithmetic and rounded to FP32;
+ * d_d2, if not NULL, receives D(D u) computed in FP32 (Eqs. 37-39, Sec. 4.3).
+ * Outputs must not overlap the inputs.  Enqueued on cuda_stream. */
+lbm_status lbm_cfd_df(const float *d_hi, const float *d_lo, float *d_d1, float *d_d2,
+                      int32_t nx, int32_t ny, int32_t axis, int32_t fd_order,
+                      void *cuda_stream);
+
 /* Time level of the current state, and the first flagged time level after
  * LBM_EUNSTABLE (-1 if none). */
 int64_t lbm_time(const lbm_ctx *ctx);
@@ -173,10 +186,6 @@ int64_t lbm_failed_step(const lbm_ctx *ctx);
 
 /* Host wait limit, in seconds, for lbm_step / lbm_check / copies (default 600). */
 lbm_status lbm_set_timeout(lbm_ctx *ctx, double seconds);
-
-/* Segment lengths of the compact-FD line sweeps along x and y (0 = automatic).
- * A tuning knob: results do not depend on it beyond rounding. */
-lbm_status lbm_set_line_segments(lbm_ctx *ctx, int32_t seg_x, int32_t seg_y);
 
 const char *lbm_strerror(lbm_status s);
 

@@ -72,10 +72,10 @@ def lib():
             "lbm_critical": (C.c_int, [C.POINTER(LbmEos), _dp, _dp]),
             "lbm_maxwell": (C.c_int, [C.POINTER(LbmEos), C.c_double, _dp, _dp]),
             "lbm_cfd": (C.c_int, [_vp, _vp, _vp, _i32, _i32, _i32, _i32, _vp]),
+            "lbm_cfd_df": (C.c_int, [_vp, _vp, _vp, _vp, _i32, _i32, _i32, _i32, _vp]),
             "lbm_time": (C.c_int64, [_vp]),
             "lbm_failed_step": (C.c_int64, [_vp]),
             "lbm_set_timeout": (C.c_int, [_vp, C.c_double]),
-            "lbm_set_line_segments": (C.c_int, [_vp, _i32, _i32]),
             "lbm_strerror": (C.c_char_p, [C.c_int]),
             "lbm_free": (None, [_vp]),
         }
@@ -149,6 +149,23 @@ def lbm_cfd(u, axis, fd_order, second=False, stream=None):
     s = stream if stream is not None else torch.cuda.current_stream(u.device)
     _check(lib().lbm_cfd(_dptr(u), _dptr(d1), _dptr(d2), nx, ny, axis, fd_order,
                          s.cuda_stream), "lbm_cfd")
+    return (d1, d2) if second else d1
+
+
+def lbm_cfd_df(u_hi, u_lo, axis, fd_order, second=False, stream=None):
+    """The mixed path's line solve on a double-float field given as two CUDA
+    float32 tensors (hi, lo): D u in double-float rounded to float32, and D(D u)
+    in float32 if `second`."""
+    import torch
+    ny, nx = u_hi.shape
+    for t in (u_hi, u_lo):
+        assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+    d1 = torch.empty_like(u_hi)
+    d2 = torch.empty_like(u_hi) if second else None
+    s = stream if stream is not None else torch.cuda.current_stream(u_hi.device)
+    _check(lib().lbm_cfd_df(u_hi.data_ptr(), u_lo.data_ptr(), d1.data_ptr(),
+                            None if d2 is None else d2.data_ptr(), nx, ny, axis, fd_order,
+                            s.cuda_stream), "lbm_cfd_df")
     return (d1, d2) if second else d1
 
 
@@ -251,9 +268,6 @@ class Simulation:
 
     def set_timeout(self, seconds):
         _check(lib().lbm_set_timeout(self.ctx, seconds), "lbm_set_timeout")
-
-    def set_line_segments(self, seg_x, seg_y):
-        _check(lib().lbm_set_line_segments(self.ctx, seg_x, seg_y), "lbm_set_line_segments")
 
     def close(self):
         if getattr(self, "ctx", None):

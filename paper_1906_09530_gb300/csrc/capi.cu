@@ -31,9 +31,7 @@ struct lbm_ctx {
     double T, Tc, rhoc, kappa, tau, k;
     double mu_max;
     int64_t mu_cap_steps;
-    CfdCoef cfd;
     PhysParams phys;
-    int seg_x, seg_y;
     cudaStream_t stream;      // caller's stream
     cudaStream_t cap_stream;  // private, for graph capture only
     cudaEvent_t ev;
@@ -42,7 +40,9 @@ struct lbm_ctx {
     size_t ws_bytes;
     void* f[2];
     int cur;
-    double *rho, *dxr, *dyr, *dxx, *mu, *Fx, *Fy;
+    double *rho, *dxr, *dyr, *dxx, *mu, *Fx, *Fy;  // FP64 path
+    // mixed path: density as hi/lo floats, the rest FP32
+    float *m_rh, *m_rl, *m_dxr, *m_dyr, *m_dxx, *m_mu, *m_Fx, *m_Fy;
     double* partials;
     int nparts;
     DevState* dst;   // device
@@ -72,17 +72,20 @@ bool opts_ok(const lbm_opts* o) {
            (o->fd_order == 4 || o->fd_order == 6) && !std::isnan(o->mu_max);
 }
 
+// Workspace: two population buffers, then the fields (FP64 path: seven FP64
+// planes; mixed path: eight FP32 planes), reduction partials, device state.
 Layout layout(int nx, int ny, int prec) {
     Layout L;
     const size_t N = (size_t)nx * ny;
     L.plane = align_up(N, 64);
-    const size_t tf = prec == LBM_PREC_FP64 ? sizeof(double) : sizeof(float);
+    const bool f64 = prec == LBM_PREC_FP64;
+    const size_t tf = f64 ? sizeof(double) : sizeof(float);
     L.f_bytes = align_up(9 * L.plane * tf, kAlign);
-    L.field_bytes = align_up(L.plane * sizeof(double), kAlign);
+    L.field_bytes = align_up(L.plane * tf, kAlign);
     L.off_f0 = 0;
     L.off_f1 = L.off_f0 + L.f_bytes;
     L.off_fields = L.off_f1 + L.f_bytes;
-    L.off_parts = L.off_fields + 7 * L.field_bytes;
+    L.off_parts = L.off_fields + (f64 ? 7 : 8) * L.field_bytes;
     L.off_state = L.off_parts + align_up(4 * kParts * sizeof(double), kAlign);
     L.total = L.off_state + align_up(sizeof(DevState), kAlign);
     return L;
@@ -101,27 +104,50 @@ lbm_status use_dev(lbm_ctx* c) {
     return LBM_OK;
 }
 
-// Passes 2-5 on the current density.
-lbm_status enqueue_force(lbm_ctx* c, cudaStream_t s, int bump) {
-    CK(launch_cfd_x_rho(c->rho, c->dxr, c->dxx, c->nx, c->ny, c->seg_x, c->cfd, c->dst, bump, s));
-    CK(launch_cfd_y_rho_mu(c->rho, c->dxx, c->dyr, c->mu, c->nx, c->ny, c->seg_y, c->cfd,
-                           c->phys, c->dst, s));
-    CK(launch_cfd_x_force(c->mu, c->rho, c->dxr, c->Fx, c->nx, c->ny, c->seg_x, c->cfd, s));
-    CK(launch_cfd_y_force(c->mu, c->rho, c->dyr, c->Fy, c->nx, c->ny, c->seg_y, c->cfd, s));
+// Passes 2-5 on the current density.  `timed` records an event after each.
+lbm_status enqueue_force(lbm_ctx* c, cudaStream_t s, int bump, cudaEvent_t* ev = nullptr) {
+    const int nx = c->nx, ny = c->ny, o = c->fd_order;
+    auto mark = [&](int i) { return ev ? cudaEventRecord(ev[i], s) : cudaSuccess; };
+    if (!is_fp64(c)) {
+        CK(lines_mixed_rho_x(c->m_rh, c->m_rl, c->m_dxr, c->m_dxx, nx, ny, o, c->dst, bump, s));
+        CK(mark(0));
+        CK(lines_mixed_rho_y_mu(c->m_rh, c->m_rl, c->m_dxx, c->m_dyr, c->m_mu, nx, ny, o, c->phys,
+                                c->dst, s));
+        CK(mark(1));
+        CK(lines_mixed_force(c->m_mu, c->m_rh, c->m_dxr, c->m_Fx, nx, ny, 0, o, s));
+        CK(mark(2));
+        CK(lines_mixed_force(c->m_mu, c->m_rh, c->m_dyr, c->m_Fy, nx, ny, 1, o, s));
+        CK(mark(3));
+        return LBM_OK;
+    }
+    CK(lines_fp64_rho_x(c->rho, c->dxr, c->dxx, nx, ny, o, c->dst, bump, s));
+    CK(mark(0));
+    CK(lines_fp64_rho_y_mu(c->rho, c->dxx, c->dyr, c->mu, nx, ny, o, c->phys, c->dst, s));
+    CK(mark(1));
+    CK(lines_fp64_force(c->mu, c->rho, c->dxr, c->Fx, nx, ny, 0, o, s));
+    CK(mark(2));
+    CK(lines_fp64_force(c->mu, c->rho, c->dyr, c->Fy, nx, ny, 1, o, s));
+    CK(mark(3));
     return LBM_OK;
 }
 
-// One full time step starting from f[from]; leaves the state in f[1-from].
-lbm_status enqueue_step(lbm_ctx* c, cudaStream_t s, int from) {
+// Pass 1 from f[from] into f[1-from].
+lbm_status enqueue_collide(lbm_ctx* c, cudaStream_t s, int from) {
     const int to = 1 - from;
     if (is_fp64(c))
         CK(launch_collide_stream<double>((const double*)c->f[from], (double*)c->f[to], c->Fx,
                                          c->Fy, c->rho, c->nx, c->ny, c->plane,
                                          c->phys.omega, c->dst, s));
     else
-        CK(launch_collide_stream<float>((const float*)c->f[from], (float*)c->f[to], c->Fx,
-                                        c->Fy, c->rho, c->nx, c->ny, c->plane, c->phys.omega,
-                                        c->dst, s));
+        CK(launch_cs_mixed((const float*)c->f[from], (float*)c->f[to], c->m_Fx, c->m_Fy,
+                           c->m_rh, c->m_rl, c->nx, c->ny, c->plane, c->phys.omega, c->dst, s));
+    return LBM_OK;
+}
+
+// One full time step starting from f[from]; leaves the state in f[1-from].
+lbm_status enqueue_step(lbm_ctx* c, cudaStream_t s, int from) {
+    lbm_status st = enqueue_collide(c, s, from);
+    if (st) return st;
     return enqueue_force(c, s, 1);
 }
 
@@ -267,7 +293,6 @@ lbm_status lbm_init(lbm_ctx** out, const lbm_grid* grid, const lbm_eos* eos, dou
     c->k = mesh_coeff;
     c->mu_max = opts->mu_max;
     c->mu_cap_steps = opts->mu_cap_steps;
-    c->cfd = make_cfd_coef(opts->fd_order);
     c->phys.T = c->T;
     c->phys.a = eos->a;
     c->phys.b = eos->b;
@@ -277,8 +302,6 @@ lbm_status lbm_init(lbm_ctx** out, const lbm_grid* grid, const lbm_eos* eos, dou
     c->phys.omega = 1.0 / tau;
     c->phys.mu_cap = std::isinf(opts->mu_max) ? HUGE_VAL : c->phys.k2 * opts->mu_max;
     c->phys.cap_steps = opts->mu_cap_steps;
-    c->seg_x = 0;
-    c->seg_y = 0;
     c->stream = (cudaStream_t)cuda_stream;
     c->ws = (char*)d_workspace;
     c->ws_bytes = ws_bytes;
@@ -286,13 +309,21 @@ lbm_status lbm_init(lbm_ctx** out, const lbm_grid* grid, const lbm_eos* eos, dou
     c->f[1] = c->ws + L.off_f1;
     double* fields = (double*)(c->ws + L.off_fields);
     const size_t fs = L.field_bytes / sizeof(double);
-    c->rho = fields;
-    c->dxr = fields + fs;
-    c->dyr = fields + 2 * fs;
-    c->dxx = fields + 3 * fs;
-    c->mu = fields + 4 * fs;
-    c->Fx = fields + 5 * fs;
-    c->Fy = fields + 6 * fs;
+    if (opts->prec == LBM_PREC_FP64) {
+        c->rho = fields;
+        c->dxr = fields + fs;
+        c->dyr = fields + 2 * fs;
+        c->dxx = fields + 3 * fs;
+        c->mu = fields + 4 * fs;
+        c->Fx = fields + 5 * fs;
+        c->Fy = fields + 6 * fs;
+    } else {
+        float* ff = (float*)fields;
+        const size_t ffs = L.field_bytes / sizeof(float);
+        float** slots[8] = {&c->m_rh, &c->m_rl, &c->m_dxr, &c->m_dyr,
+                            &c->m_dxx, &c->m_mu, &c->m_Fx, &c->m_Fy};
+        for (int i = 0; i < 8; ++i) *slots[i] = ff + i * ffs;
+    }
     c->partials = (double*)(c->ws + L.off_parts);
     c->nparts = kParts;
     c->dst = (DevState*)(c->ws + L.off_state);
@@ -333,14 +364,6 @@ lbm_status lbm_set_timeout(lbm_ctx* c, double seconds) {
     return LBM_OK;
 }
 
-lbm_status lbm_set_line_segments(lbm_ctx* c, int32_t seg_x, int32_t seg_y) {
-    if (!c || seg_x < 0 || seg_y < 0) return LBM_EINVAL;
-    c->seg_x = seg_x;
-    c->seg_y = seg_y;
-    drop_graphs(c);
-    return LBM_OK;
-}
-
 int64_t lbm_time(const lbm_ctx* c) { return c ? c->t : -1; }
 int64_t lbm_failed_step(const lbm_ctx* c) { return c ? c->failed : -1; }
 
@@ -353,8 +376,8 @@ static lbm_status init_from_device_fields(lbm_ctx* c, const double* rho, const d
         CK(launch_init_feq<double>(rho, ux, uy, (double*)c->f[0], c->rho, c->nx, c->ny,
                                    c->plane, c->stream));
     else
-        CK(launch_init_feq<float>(rho, ux, uy, (float*)c->f[0], c->rho, c->nx, c->ny,
-                                  c->plane, c->stream));
+        CK(launch_init_mixed(rho, ux, uy, (float*)c->f[0], c->m_rh, c->m_rl, c->nx, c->ny,
+                             c->plane, c->stream));
     st = enqueue_force(c, c->stream, 0);
     if (st) return st;
     c->ready = true;
@@ -429,24 +452,11 @@ lbm_status lbm_step_timed(lbm_ctx* c, float* pass_ms) {
     cudaStream_t s = c->stream;
     const int from = c->cur, to = 1 - from;
     CK(cudaEventRecord(c->tev[0], s));
-    if (is_fp64(c))
-        CK(launch_collide_stream<double>((const double*)c->f[from], (double*)c->f[to], c->Fx,
-                                         c->Fy, c->rho, c->nx, c->ny, c->plane,
-                                         c->phys.omega, c->dst, s));
-    else
-        CK(launch_collide_stream<float>((const float*)c->f[from], (float*)c->f[to], c->Fx,
-                                        c->Fy, c->rho, c->nx, c->ny, c->plane, c->phys.omega,
-                                        c->dst, s));
+    st = enqueue_collide(c, s, from);
+    if (st) return st;
     CK(cudaEventRecord(c->tev[1], s));
-    CK(launch_cfd_x_rho(c->rho, c->dxr, c->dxx, c->nx, c->ny, c->seg_x, c->cfd, c->dst, 1, s));
-    CK(cudaEventRecord(c->tev[2], s));
-    CK(launch_cfd_y_rho_mu(c->rho, c->dxx, c->dyr, c->mu, c->nx, c->ny, c->seg_y, c->cfd,
-                           c->phys, c->dst, s));
-    CK(cudaEventRecord(c->tev[3], s));
-    CK(launch_cfd_x_force(c->mu, c->rho, c->dxr, c->Fx, c->nx, c->ny, c->seg_x, c->cfd, s));
-    CK(cudaEventRecord(c->tev[4], s));
-    CK(launch_cfd_y_force(c->mu, c->rho, c->dyr, c->Fy, c->nx, c->ny, c->seg_y, c->cfd, s));
-    CK(cudaEventRecord(c->tev[5], s));
+    st = enqueue_force(c, s, 1, c->tev + 2);
+    if (st) return st;
     c->cur = to;
     c->t += 1;
     st = read_state(c);
@@ -458,13 +468,14 @@ lbm_status lbm_step_timed(lbm_ctx* c, float* pass_ms) {
 static lbm_status fields_to_device(lbm_ctx* c, double* rho, double* vx, double* vy,
                                    double* mu) {
     const size_t B = c->N * sizeof(double);
+    if (!is_fp64(c)) {
+        CK(launch_macro_mixed((const float*)c->f[c->cur], c->m_rh, c->m_rl, c->m_Fx, c->m_Fy,
+                              c->m_mu, rho, vx, vy, mu, c->nx, c->ny, c->plane, c->stream));
+        return LBM_OK;
+    }
     if (vx || vy) {
-        if (is_fp64(c))
-            CK(launch_macro<double>((const double*)c->f[c->cur], c->Fx, c->Fy, vx, vy, c->nx,
-                                    c->ny, c->plane, c->stream));
-        else
-            CK(launch_macro<float>((const float*)c->f[c->cur], c->Fx, c->Fy, vx, vy, c->nx,
-                                   c->ny, c->plane, c->stream));
+        CK(launch_macro<double>((const double*)c->f[c->cur], c->Fx, c->Fy, vx, vy, c->nx,
+                                c->ny, c->plane, c->stream));
     }
     if (rho) CK(cudaMemcpyAsync(rho, c->rho, B, cudaMemcpyDeviceToDevice, c->stream));
     if (mu) CK(cudaMemcpyAsync(mu, c->mu, B, cudaMemcpyDeviceToDevice, c->stream));
@@ -485,16 +496,19 @@ lbm_status lbm_fields(lbm_ctx* c, double* h_rho, double* h_vx, double* h_vy, dou
     if (!c->ready) return LBM_EINVAL;
     lbm_status st = use_dev(c);
     if (st) return st;
-    double* sg = staging(c);  // the idle population buffer holds >= 3 N doubles
-    st = fields_to_device(c, nullptr, h_vx ? sg : nullptr, h_vy ? sg + c->N : nullptr, nullptr);
+    // the idle population buffer holds >= 4 N doubles in both precisions
+    double* sg = staging(c);
+    const size_t N = c->N;
+    st = fields_to_device(c, h_rho ? sg : nullptr, h_vx ? sg + N : nullptr,
+                          h_vy ? sg + 2 * N : nullptr, h_mu ? sg + 3 * N : nullptr);
     if (st) return st;
     st = wait_stream(c);
     if (st) return st;
-    const size_t B = c->N * sizeof(double);
-    if (h_rho) CK(cudaMemcpyAsync(h_rho, c->rho, B, cudaMemcpyDeviceToHost, c->stream));
-    if (h_vx) CK(cudaMemcpyAsync(h_vx, sg, B, cudaMemcpyDeviceToHost, c->stream));
-    if (h_vy) CK(cudaMemcpyAsync(h_vy, sg + c->N, B, cudaMemcpyDeviceToHost, c->stream));
-    if (h_mu) CK(cudaMemcpyAsync(h_mu, c->mu, B, cudaMemcpyDeviceToHost, c->stream));
+    const size_t B = N * sizeof(double);
+    if (h_rho) CK(cudaMemcpyAsync(h_rho, sg, B, cudaMemcpyDeviceToHost, c->stream));
+    if (h_vx) CK(cudaMemcpyAsync(h_vx, sg + N, B, cudaMemcpyDeviceToHost, c->stream));
+    if (h_vy) CK(cudaMemcpyAsync(h_vy, sg + 2 * N, B, cudaMemcpyDeviceToHost, c->stream));
+    if (h_mu) CK(cudaMemcpyAsync(h_mu, sg + 3 * N, B, cudaMemcpyDeviceToHost, c->stream));
     return wait_stream(c);
 }
 
@@ -547,8 +561,8 @@ lbm_status lbm_set_populations(lbm_ctx* c, const double* h_f, int64_t t) {
         CK(launch_rho_from_f<double>((const double*)c->f[0], c->rho, c->nx, c->ny, c->plane,
                                      c->stream));
     else
-        CK(launch_rho_from_f<float>((const float*)c->f[0], c->rho, c->nx, c->ny, c->plane,
-                                    c->stream));
+        CK(launch_rho_from_f_mixed((const float*)c->f[0], c->m_rh, c->m_rl, c->nx, c->ny,
+                                   c->plane, c->stream));
     st = enqueue_force(c, c->stream, 0);
     if (st) return st;
     c->ready = true;
@@ -564,8 +578,9 @@ lbm_status lbm_diag(lbm_ctx* c, double* mass, double* max_v, double* rho_min, do
         CK(launch_diag<double>((const double*)c->f[c->cur], c->rho, c->Fx, c->Fy, c->nx, c->ny,
                                c->plane, c->partials, c->nparts, c->dst, c->stream));
     else
-        CK(launch_diag<float>((const float*)c->f[c->cur], c->rho, c->Fx, c->Fy, c->nx, c->ny,
-                              c->plane, c->partials, c->nparts, c->dst, c->stream));
+        CK(launch_diag_mixed((const float*)c->f[c->cur], c->m_rh, c->m_rl, c->m_Fx, c->m_Fy,
+                             c->nx, c->ny, c->plane, c->partials, c->nparts, c->dst,
+                             c->stream));
     st = read_state(c);
     if (st) return st;
     if (mass) *mass = c->hst->diag[0];
@@ -581,8 +596,22 @@ lbm_status lbm_cfd(const double* d_u, double* d_d1, double* d_d2, int32_t nx, in
         (fd_order != 4 && fd_order != 6))
         return LBM_EINVAL;
     if (d_d1 == d_u || d_d2 == d_u || (d_d2 && d_d2 == d_d1)) return LBM_EINVAL;
-    const CfdCoef c = make_cfd_coef(fd_order);
-    CK(launch_cfd_plain(d_u, d_d1, d_d2, nx, ny, axis, 0, c, (cudaStream_t)cuda_stream));
+    CK(lines_fp64_plain(d_u, d_d1, d_d2, nx, ny, axis, fd_order, (cudaStream_t)cuda_stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_cfd_df(const float* d_hi, const float* d_lo, float* d_d1, float* d_d2,
+                      int32_t nx, int32_t ny, int32_t axis, int32_t fd_order,
+                      void* cuda_stream) {
+    if (!d_hi || !d_lo || !d_d1 || nx < 1 || ny < 1 || (axis != 0 && axis != 1) ||
+        (fd_order != 4 && fd_order != 6))
+        return LBM_EINVAL;
+    const void* outs[2] = {d_d1, d_d2};
+    for (const void* o : outs)
+        if (o && (o == (const void*)d_hi || o == (const void*)d_lo)) return LBM_EINVAL;
+    if (d_d2 == d_d1) return LBM_EINVAL;
+    CK(lines_mixed_plain(d_hi, d_lo, d_d1, d_d2, nx, ny, axis, fd_order,
+                         (cudaStream_t)cuda_stream));
     return LBM_OK;
 }
 

@@ -24,21 +24,6 @@ enum : unsigned int {
     FLAG_EOS = 2u,   // EOS pass: b rho / 4 >= 1 (the CS pole) or mu not finite
 };
 
-// Compact-FD coefficients in the factorised form used by the line sweeps.
-// The periodic system alpha d[i-1] + d[i] + alpha d[i+1] = (B u)[i] is split as
-// A = (alpha/lam)(1 + lam S^-1)(1 + lam S), lam = (1 - sqrt(1 - 4 alpha^2))/(2 alpha),
-// so d = (lam/alpha) (1 + lam S)^-1 (1 + lam S^-1)^-1 B u.  The factor lam/alpha
-// is folded into the right-hand-side weights c1 = (lam/alpha) a/2 and
-// c2 = (lam/alpha) b/4 (a, b from Eq. 38).  Each first-order recursion is cut
-// after `warm` terms, where its weight has fallen below FP64 rounding.
-struct CfdCoef {
-    double c1, c2, lam;
-    int warm;
-    int sixth;  // 1 when b != 0 (the +-2 neighbours enter)
-};
-
-CfdCoef make_cfd_coef(int fd_order);
-
 // Physical parameters the kernels need.
 struct PhysParams {
     double T, a, b, R;   // EOS (Eq. 20), T absolute
@@ -78,24 +63,46 @@ cudaError_t launch_f_to_double(const TF* f, double* out, size_t n, cudaStream_t 
 template <typename TF>
 cudaError_t launch_f_from_double(const double* in, TF* f, size_t n, cudaStream_t s);
 
-// Force stage (passes 2-5).
-cudaError_t launch_cfd_x_rho(const double* rho, double* dxr, double* dxx, int nx, int ny,
-                             int seg, const CfdCoef& c, DevState* st, int bump,
-                             cudaStream_t s);
-cudaError_t launch_cfd_y_rho_mu(const double* rho, const double* dxx, double* dyr, double* mu,
-                                int nx, int ny, int seg, const CfdCoef& c,
-                                const PhysParams& p, DevState* st, cudaStream_t s);
-cudaError_t launch_cfd_x_force(const double* mu, const double* rho, const double* dxr,
-                               double* Fx, int nx, int ny, int seg, const CfdCoef& c,
-                               cudaStream_t s);
-cudaError_t launch_cfd_y_force(const double* mu, const double* rho, const double* dyr,
-                               double* Fy, int nx, int ny, int seg, const CfdCoef& c,
-                               cudaStream_t s);
-// Plain derivative(s) along an axis (stand-alone entry point).
-cudaError_t launch_cfd_plain(const double* u, double* d1, double* d2, int nx, int ny, int axis,
-                             int seg, const CfdCoef& c, cudaStream_t s);
+cudaError_t launch_diag_final(const double* partials, int nparts, DevState* st, cudaStream_t s);
 
-int default_segment(int line_len, int n_lines);
+// ---- mixed precision path (kernels_mixed.cu) ------------------------------
+cudaError_t launch_cs_mixed(const float* fin, float* fout, const float* Fx, const float* Fy,
+                            float* rh, float* rl, int nx, int ny, size_t plane, double omega,
+                            DevState* st, cudaStream_t s);
+cudaError_t launch_init_mixed(const double* rho, const double* ux, const double* uy, float* f,
+                              float* rh, float* rl, int nx, int ny, size_t plane,
+                              cudaStream_t s);
+cudaError_t launch_rho_from_f_mixed(const float* f, float* rh, float* rl, int nx, int ny,
+                                    size_t plane, cudaStream_t s);
+cudaError_t launch_macro_mixed(const float* f, const float* rh, const float* rl,
+                               const float* Fx, const float* Fy, const float* mu, double* rho,
+                               double* vx, double* vy, double* mu_o, int nx, int ny,
+                               size_t plane, cudaStream_t s);
+cudaError_t launch_diag_mixed(const float* f, const float* rh, const float* rl, const float* Fx,
+                              const float* Fy, int nx, int ny, size_t plane, double* partials,
+                              int nparts, DevState* st, cudaStream_t s);
+
+// Warp-cooperative compact-FD line solves (kernels_lines.cu).  axis 0: lines
+// along x, 1: along y.  Passes 2-5 of the FP64 path and of the mixed path, and
+// the stand-alone derivatives.
+cudaError_t lines_fp64_rho_x(const double* rho, double* dxr, double* dxx, int nx, int ny,
+                             int order, DevState* st, int bump, cudaStream_t s);
+cudaError_t lines_fp64_rho_y_mu(const double* rho, const double* dxx, double* dyr, double* mu,
+                                int nx, int ny, int order, const PhysParams& p, DevState* st,
+                                cudaStream_t s);
+cudaError_t lines_fp64_force(const double* mu, const double* rho, const double* dr, double* F,
+                             int nx, int ny, int axis, int order, cudaStream_t s);
+cudaError_t lines_fp64_plain(const double* u, double* d1, double* d2, int nx, int ny, int axis,
+                             int order, cudaStream_t s);
+cudaError_t lines_mixed_rho_x(const float* rh, const float* rl, float* dxr, float* dxx, int nx,
+                              int ny, int order, DevState* st, int bump, cudaStream_t s);
+cudaError_t lines_mixed_rho_y_mu(const float* rh, const float* rl, const float* dxx, float* dyr,
+                                 float* mu, int nx, int ny, int order, const PhysParams& p,
+                                 DevState* st, cudaStream_t s);
+cudaError_t lines_mixed_force(const float* mu, const float* rh, const float* dr, float* F, int nx,
+                              int ny, int axis, int order, cudaStream_t s);
+cudaError_t lines_mixed_plain(const float* uh, const float* ul, float* d1, float* d2, int nx,
+                              int ny, int axis, int order, cudaStream_t s);
 
 // Host thermodynamics of the product library (independent of the oracle).
 int cs_critical(double a, double b, double R, double* Tc, double* rhoc);

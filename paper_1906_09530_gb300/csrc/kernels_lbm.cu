@@ -314,6 +314,11 @@ cudaError_t launch_diag(const TF* f, const double* rho, const double* Fx, const 
     return cudaGetLastError();
 }
 
+cudaError_t launch_diag_final(const double* partials, int nparts, DevState* st, cudaStream_t s) {
+    k_diag_final<<<1, kDiagThreads, 0, s>>>(partials, nparts, st);
+    return cudaGetLastError();
+}
+
 template <typename TF>
 cudaError_t launch_f_to_double(const TF* f, double* out, size_t n, cudaStream_t s) {
     k_f_to_double<TF><<<grid_for(n, 256), 256, 0, s>>>(f, out, n);

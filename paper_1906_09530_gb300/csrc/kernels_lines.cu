@@ -1,0 +1,576 @@
+// kernels_lines.cu -- warp-cooperative compact-FD line solves (Eqs. 37-39) with
+// the fused chemical-potential (Eqs. 21, 33, Sec. 5.6) and force (Eq. 12)
+// epilogues, for both the FP64 and the mixed path.
+//
+// The periodic compact scheme is the circulant system A d = B u with
+//   (A d)_i = alpha d_{i-1} + d_i + alpha d_{i+1},
+//   (B u)_i = a/2 (u_{i+1} - u_{i-1}) + b/4 (u_{i+2} - u_{i-2})   (a, b: Eq. 38).
+// A = (alpha/lam)(1 + lam S^-1)(1 + lam S), lam = (1 - sqrt(1 - 4 alpha^2))/(2 alpha),
+// so d follows from two first-order recursions on r = (lam/alpha) B u:
+//   forward  w_i = r_i - lam w_{i-1},    backward  z_i = w_i - lam z_{i+1},   d = z.
+// |lam| < 1 (0.382 at alpha = 1/3, 0.268 at alpha = 1/4), so a value's influence
+// decays as lam^distance and each recursion is exact to rounding once started a
+// few dozen positions away; positions are taken mod n, so any line length works.
+//
+// Parallel form.  A block stages a window of W = 32 C consecutive positions of
+// NL lines in shared memory (loads and stores coalesced whichever axis the lines
+// run along).  Warp w owns line w; lane l owns positions [l C, l C + C).  Each
+// lane runs both recursions over its chunk from a zero state, then the chunk
+// boundary states are joined by a two-level shuffle scan: the state entering
+// chunk l is T_{l-1} with T_l = E_l + m T_{l-1}, m = (-lam)^C (|m| = 3.7e-6 for
+// C = 13), and each position adds (-lam)^{j+1} times that carry.  The window
+// starts H positions before the first owned position and ends H after the last,
+// H chosen so that lam^H (or (H+1) lam^H for the double recursion) is below the
+// arithmetic's rounding.  The second derivative D(D u) ("applying CFM twice",
+// Sec. 4.3) uses that the circulant operators commute: D D u = F_b F_b F_f F_f B B u,
+// a double recursion in each direction whose chunk-joining map is
+// (v, w) -> (m v, m (C v + w)).
+//
+// Arithmetic policies: PolD (FP64), PolF (FP32), PolDF (double-float pairs).
+// The mixed path uses PolDF for the first derivative of the density and PolF for
+// everything else (see kernels_mixed.cu for why).
+#include <cfloat>
+#include <cmath>
+
+#include "cplbm_internal.cuh"
+#include "df.cuh"
+
+namespace cplbm {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+struct PolD {
+    using V = double;
+    using K = double;
+    using O = double;  // stored result
+    static __device__ __forceinline__ V zero() { return 0.0; }
+    static __device__ __forceinline__ V sub(V a, V b) { return a - b; }
+    static __device__ __forceinline__ V mulc(V a, K c) { return a * c; }
+    static __device__ __forceinline__ V fmac(V a, K c, V b) { return fma(a, c, b); }
+    static __device__ __forceinline__ V up(V a, int o) { return __shfl_up_sync(kFull, a, o); }
+    static __device__ __forceinline__ V down(V a, int o) { return __shfl_down_sync(kFull, a, o); }
+    static __device__ __forceinline__ O out(V a) { return a; }
+    static K konst(double v) { return v; }
+};
+
+struct PolF {
+    using V = float;
+    using K = float;
+    using O = float;
+    static __device__ __forceinline__ V zero() { return 0.0f; }
+    static __device__ __forceinline__ V sub(V a, V b) { return a - b; }
+    static __device__ __forceinline__ V mulc(V a, K c) { return a * c; }
+    static __device__ __forceinline__ V fmac(V a, K c, V b) { return fmaf(a, c, b); }
+    static __device__ __forceinline__ V up(V a, int o) { return __shfl_up_sync(kFull, a, o); }
+    static __device__ __forceinline__ V down(V a, int o) { return __shfl_down_sync(kFull, a, o); }
+    static __device__ __forceinline__ O out(V a) { return a; }
+    static K konst(double v) { return (float)v; }
+};
+
+struct PolDF {
+    using V = df;
+    using K = df;
+    using O = float;  // the derivative is rounded once, relative to itself
+    static __device__ __forceinline__ V zero() { return df{0.0f, 0.0f}; }
+    static __device__ __forceinline__ V sub(V a, V b) { return df_sub(a, b); }
+    static __device__ __forceinline__ V mulc(V a, K c) { return df_mul(a, c.hi, c.lo); }
+    static __device__ __forceinline__ V fmac(V a, K c, V b) { return df_add(df_mul(a, c.hi, c.lo), b); }
+    static __device__ __forceinline__ V up(V a, int o) {
+        return df{__shfl_up_sync(kFull, a.hi, o), __shfl_up_sync(kFull, a.lo, o)};
+    }
+    static __device__ __forceinline__ V down(V a, int o) {
+        return df{__shfl_down_sync(kFull, a.hi, o), __shfl_down_sync(kFull, a.lo, o)};
+    }
+    static __device__ __forceinline__ O out(V a) { return df_round(a); }
+    static K konst(double v) {
+        df r;
+        r.hi = (float)v;
+        r.lo = (float)(v - (double)r.hi);
+        return r;
+    }
+};
+
+// value of the second-derivative arithmetic from the first's right-hand side
+template <class P2>
+__device__ __forceinline__ typename P2::V to2(double v) { return (typename P2::V)v; }
+template <class P2>
+__device__ __forceinline__ typename P2::V to2(float v) { return (typename P2::V)v; }
+template <class P2>
+__device__ __forceinline__ typename P2::V to2(df v) { return (typename P2::V)v.hi; }
+
+constexpr int kC = 13;         // positions per lane
+constexpr int kW = 32 * kC;    // window length
+constexpr int kNL = 8;         // lines (warps) per block
+constexpr int kLW = kW + 9;    // shared-memory stride of one staged line (margin 4 + 4, odd)
+
+template <class P>
+struct LineConst {
+    typename P::K c1, c2, nlam;  // (lam/alpha) a/2, (lam/alpha) b/4, -lam
+    typename P::K pw[kC];        // (-lam)^(j+1)
+    typename P::K m1, m2;        // (-lam)^C, (-lam)^(2C)
+    typename P::K Cm1, Cm2;      // C (-lam)^C, 2C (-lam)^(2C)  (double-recursion joins)
+};
+
+struct LineGeo {
+    int n;          // line length
+    int nlines;
+    long long ps;   // stride along a line
+    long long ls;   // stride between lines
+    int H;          // window positions before the first owned one
+    int own;        // owned positions per window
+    int nwin;       // windows per line
+    int ngroups;    // line groups of kNL
+};
+
+// Input readers.  In<P>: a field in P's storage.
+struct InD {
+    const double* p;
+    __device__ __forceinline__ double get(size_t o) const { return __ldg(p + o); }
+};
+struct InF {
+    const float* p;
+    __device__ __forceinline__ float get(size_t o) const { return __ldg(p + o); }
+};
+struct InDF {
+    const float* h;
+    const float* l;
+    __device__ __forceinline__ df get(size_t o) const { return df{__ldg(h + o), __ldg(l + o)}; }
+};
+
+__device__ __forceinline__ int wrapi(long long v, int n) {
+    long long r = v % n;
+    return (int)(r < 0 ? r + n : r);
+}
+
+__device__ __forceinline__ void raise_flag(DevState* st, unsigned bits, int64_t t) {
+    atomicOr(&st->flag, bits);
+    atomicMin(&st->failed_t, (unsigned long long)t);
+}
+
+// ---------------------------------------------------------------------------
+// The kernel.  AXIS 0: lines along x (rows, stride 1); AXIS 1: lines along y.
+// ---------------------------------------------------------------------------
+template <int AXIS, class P1, class P2, bool SIXTH, bool SECOND, class In, class Epi>
+__global__ void __launch_bounds__(kNL * 32)
+    k_lines(In in, LineGeo g, LineConst<P1> k1, LineConst<P2> k2, Epi epi, DevState* st,
+            int bump) {
+    using V1 = typename P1::V;
+    using V2 = typename P2::V;
+    using O1 = typename P1::O;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V1* tin = reinterpret_cast<V1*>(smem_raw);                      // [kNL][kLW]
+    O1* tout1 = reinterpret_cast<O1*>(tin + kNL * kLW);             // [kNL][kW]
+    V2* tout2 = reinterpret_cast<V2*>(tout1 + kNL * kW);            // [kNL][kW]
+
+    if (bump && blockIdx.x == 0 && threadIdx.x == 0) st->t += 1;
+    epi.init(st);
+
+    const int grp = blockIdx.x % g.ngroups;
+    const int win = blockIdx.x / g.ngroups;
+    const int line0 = grp * kNL;
+    const int s = win * g.own;                      // first owned position
+    const int e = min(s + g.own, g.n);              // one past the last
+    const long long s0 = (long long)s - g.H;         // window position 0
+    const int tid = threadIdx.x;
+
+    // ---- stage the window: positions s0-4 .. s0+kW+3 of kNL lines ----
+    constexpr int LWIN = kW + 8;
+    for (int idx = tid; idx < kNL * LWIN; idx += kNL * 32) {
+        int l, q;
+        if (AXIS == 0) {
+            l = idx / LWIN;
+            q = idx - l * LWIN;
+        } else {
+            q = idx / kNL;
+            l = idx - q * kNL;
+        }
+        const int line = line0 + l;
+        V1 v = P1::zero();
+        if (line < g.nlines) {
+            const int p = wrapi(s0 - 4 + q, g.n);
+            v = in.get((size_t)line * g.ls + (size_t)p * g.ps);
+        }
+        tin[l * kLW + q] = v;
+    }
+    __syncthreads();
+
+    // ---- per-warp solve of one line ----
+    const int w = tid >> 5, lane = tid & 31;
+    const V1* tl = tin + w * kLW + 4;  // tl[q] = window position q, q in [-4, kW+4)
+    const int q0 = lane * kC;
+
+    V1 r[kC];  // right-hand side, then forward states, then the result
+    {
+        V1 u[kC + 4];
+#pragma unroll
+        for (int k = 0; k < kC + 4; ++k) u[k] = tl[q0 - 2 + k];
+#pragma unroll
+        for (int j = 0; j < kC; ++j) {
+            V1 b = P1::mulc(P1::sub(u[j + 3], u[j + 1]), k1.c1);
+            if (SIXTH) b = P1::fmac(P1::sub(u[j + 4], u[j]), k1.c2, b);
+            r[j] = b;
+        }
+    }
+    V2 r2[kC];
+    if (SECOND) {
+        // b1 at positions q0-2 .. q0+kC+1 in the second arithmetic; the two
+        // extra on each side are recomputed from the staged field
+        V2 bx[kC + 4];
+#pragma unroll
+        for (int k = 0; k < kC + 4; ++k) {
+            if (k >= 2 && k < kC + 2) {
+                bx[k] = to2<P2>(r[k - 2]);
+            } else {
+                const int qc = q0 - 2 + k;  // in [-2, kW+2)
+                V2 t = (to2<P2>(tl[qc + 1]) - to2<P2>(tl[qc - 1])) * k2.c1;
+                if (SIXTH) t = P2::fmac(to2<P2>(tl[qc + 2]) - to2<P2>(tl[qc - 2]), k2.c2, t);
+                bx[k] = t;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kC; ++j) {
+            V2 t = (bx[j + 3] - bx[j + 1]) * k2.c1;
+            if (SIXTH) t = P2::fmac(bx[j + 4] - bx[j], k2.c2, t);
+            r2[j] = t;
+        }
+    }
+
+    // forward recursions over the chunk from a zero state
+    V1 wv = P1::zero();
+#pragma unroll
+    for (int j = 0; j < kC; ++j) {
+        wv = P1::fmac(wv, k1.nlam, r[j]);
+        r[j] = wv;
+    }
+    V2 vv = 0, ww = 0;
+    if (SECOND) {
+#pragma unroll
+        for (int j = 0; j < kC; ++j) {
+            vv = P2::fmac(vv, k2.nlam, r2[j]);
+            ww = P2::fmac(ww, k2.nlam, vv);
+            r2[j] = ww;
+        }
+    }
+    // join the chunks (forward): state entering this lane's chunk
+    {
+        V1 T = wv;
+        V1 t = P1::up(T, 1);
+        if (lane >= 1) T = P1::fmac(t, k1.m1, T);
+        t = P1::up(T, 2);
+        if (lane >= 2) T = P1::fmac(t, k1.m2, T);
+        V1 c = P1::up(T, 1);
+        if (lane == 0) c = P1::zero();
+#pragma unroll
+        for (int j = 0; j < kC; ++j) r[j] = P1::fmac(c, k1.pw[j], r[j]);
+    }
+    if (SECOND) {
+        V2 TV = vv, TW = ww;
+        V2 tv = P2::up(TV, 1), tw = P2::up(TW, 1);
+        if (lane >= 1) {
+            TW = TW + k2.m1 * tw + k2.Cm1 * tv;
+            TV = TV + k2.m1 * tv;
+        }
+        tv = P2::up(TV, 2);
+        tw = P2::up(TW, 2);
+        if (lane >= 2) {
+            TW = TW + k2.m2 * tw + k2.Cm2 * tv;
+            TV = TV + k2.m2 * tv;
+        }
+        V2 cv = P2::up(TV, 1), cw = P2::up(TW, 1);
+        if (lane == 0) cv = cw = 0;
+#pragma unroll
+        for (int j = 0; j < kC; ++j) r2[j] = r2[j] + k2.pw[j] * ((V2)(j + 1) * cv + cw);
+    }
+
+    // backward recursions over the chunk from a zero state
+    V1 zv = P1::zero();
+#pragma unroll
+    for (int j = kC - 1; j >= 0; --j) {
+        zv = P1::fmac(zv, k1.nlam, r[j]);
+        r[j] = zv;
+    }
+    V2 yv = 0, zz = 0;
+    if (SECOND) {
+#pragma unroll
+        for (int j = kC - 1; j >= 0; --j) {
+            yv = P2::fmac(yv, k2.nlam, r2[j]);
+            zz = P2::fmac(zz, k2.nlam, yv);
+            r2[j] = zz;
+        }
+    }
+    {
+        V1 T = zv;
+        V1 t = P1::down(T, 1);
+        if (lane <= 30) T = P1::fmac(t, k1.m1, T);
+        t = P1::down(T, 2);
+        if (lane <= 29) T = P1::fmac(t, k1.m2, T);
+        V1 c = P1::down(T, 1);
+        if (lane == 31) c = P1::zero();
+#pragma unroll
+        for (int j = 0; j < kC; ++j) r[j] = P1::fmac(c, k1.pw[kC - 1 - j], r[j]);
+    }
+    if (SECOND) {
+        V2 TY = yv, TZ = zz;
+        V2 ty = P2::down(TY, 1), tz = P2::down(TZ, 1);
+        if (lane <= 30) {
+            TZ = TZ + k2.m1 * tz + k2.Cm1 * ty;
+            TY = TY + k2.m1 * ty;
+        }
+        ty = P2::down(TY, 2);
+        tz = P2::down(TZ, 2);
+        if (lane <= 29) {
+            TZ = TZ + k2.m2 * tz + k2.Cm2 * ty;
+            TY = TY + k2.m2 * ty;
+        }
+        V2 cy = P2::down(TY, 1), cz = P2::down(TZ, 1);
+        if (lane == 31) cy = cz = 0;
+#pragma unroll
+        for (int j = 0; j < kC; ++j)
+            r2[j] = r2[j] + k2.pw[kC - 1 - j] * ((V2)(kC - j) * cy + cz);
+    }
+#pragma unroll
+    for (int j = 0; j < kC; ++j) {
+        tout1[w * kW + q0 + j] = P1::out(r[j]);
+        if (SECOND) tout2[w * kW + q0 + j] = r2[j];
+    }
+    __syncthreads();
+
+    // ---- epilogue over the owned positions, coalesced ----
+    const int nown = e - s;
+    bool bad = false;
+    for (int idx = tid; idx < kNL * nown; idx += kNL * 32) {
+        int l, q;
+        if (AXIS == 0) {
+            l = idx / nown;
+            q = idx - l * nown;
+        } else {
+            q = idx / kNL;
+            l = idx - q * kNL;
+        }
+        const int line = line0 + l;
+        if (line >= g.nlines) continue;
+        const size_t o = (size_t)line * g.ls + (size_t)(s + q) * g.ps;
+        const int wq = g.H + q;
+        bad |= epi(o, tout1[l * kW + wq], SECOND ? tout2[l * kW + wq] : (V2)0);
+    }
+    if (bad) raise_flag(st, FLAG_EOS, st->t);
+}
+
+// ---- epilogues: return true when a value is bad (flags the run) ----
+template <class O, class V2>
+struct EpiStore {
+    O* d1;
+    V2* d2;
+    __device__ __forceinline__ void init(const DevState*) {}
+    __device__ __forceinline__ bool operator()(size_t o, O a, V2 b) {
+        d1[o] = a;
+        if (d2) d2[o] = b;
+        return false;
+    }
+};
+
+// mu-hat = k^2 mu0(rho) - kappa (d_xx + d_yy) rho, Eqs. 21 and 33, limited from
+// above while t < cap_steps (Sec. 5.6).  R is the arithmetic of the EOS.
+template <class R, class O, class RhoT>
+struct EpiMu {
+    O* dyr;
+    O* mu;
+    const RhoT* __restrict__ rho;
+    const O* __restrict__ dxx;
+    R T, a, b, Rg, k2, kappa, cap;
+    int64_t cap_steps;
+    bool capped;
+    // the time level is read on the device: graph replays reuse the arguments
+    __device__ __forceinline__ void init(const DevState* st) { capped = st->t < cap_steps; }
+    __device__ __forceinline__ bool operator()(size_t o, O d1, O d2) {
+        dyr[o] = d1;
+        const R r = (R)rho[o];
+        const R eta = R(0.25) * b * r;
+        const R om = R(1) - eta;
+        const R mu0 = Rg * T * ((R(3) - eta) / (om * om * om) + log(r) + R(1)) - R(2) * a * r;
+        R m = k2 * mu0 - kappa * ((R)dxx[o] + (R)d2);
+        if (capped) m = m < cap ? m : cap;
+        mu[o] = (O)m;
+        return !(r > R(0) && eta < R(1) && m > -R(1e30) && m < R(1e30));
+    }
+};
+
+// F = -rho d(mu-hat) + c_s^2 d(rho), Eq. 12.
+template <class O, class RhoT>
+struct EpiForce {
+    O* F;
+    const RhoT* __restrict__ rho;
+    const O* __restrict__ dr;
+    __device__ __forceinline__ void init(const DevState*) {}
+    __device__ __forceinline__ bool operator()(size_t o, O dmu, O) {
+        F[o] = -(O)rho[o] * dmu + dr[o] * (O)(1.0 / 3.0);
+        return false;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Host side: constants, geometry, launch
+// ---------------------------------------------------------------------------
+struct Scheme {
+    double alpha, a, b, lam, c1, c2;
+};
+Scheme scheme(int order) {
+    Scheme s;
+    s.alpha = order == 6 ? 1.0 / 3.0 : 0.25;
+    s.a = 2.0 / 3.0 * (s.alpha + 2.0);  // Eq. 38
+    s.b = (4.0 * s.alpha - 1.0) / 3.0;  // Eq. 38
+    s.lam = (1.0 - std::sqrt(1.0 - 4.0 * s.alpha * s.alpha)) / (2.0 * s.alpha);
+    s.c1 = s.lam / s.alpha * s.a / 2.0;
+    s.c2 = s.lam / s.alpha * s.b / 4.0;
+    return s;
+}
+
+template <class P>
+LineConst<P> make_const(int order) {
+    const Scheme sc = scheme(order);
+    LineConst<P> k;
+    k.c1 = P::konst(sc.c1);
+    k.c2 = P::konst(sc.c2);
+    k.nlam = P::konst(-sc.lam);
+    double p = 1.0;
+    for (int j = 0; j < kC; ++j) {
+        p *= -sc.lam;
+        k.pw[j] = P::konst(p);
+    }
+    const double m = std::pow(-sc.lam, kC);
+    k.m1 = P::konst(m);
+    k.m2 = P::konst(m * m);
+    k.Cm1 = P::konst(kC * m);
+    k.Cm2 = P::konst(2.0 * kC * m * m);
+    return k;
+}
+
+// Halo: lam^H (single recursion) or (H+1) lam^H (double) below eps.
+int halo(int order, double eps1, bool second, double eps2) {
+    const double lam = scheme(order).lam;
+    int h1 = 1;
+    while (std::pow(lam, h1) >= eps1) ++h1;
+    int h2 = 0;
+    if (second) {
+        h2 = 1;
+        while ((h2 + 1) * std::pow(lam, h2) >= eps2) ++h2;
+    }
+    return (h1 > h2 ? h1 : h2) + 1;
+}
+
+LineGeo make_geo(int nx, int ny, int axis, int H) {
+    LineGeo g;
+    if (axis == 0) {
+        g.n = nx; g.nlines = ny; g.ps = 1; g.ls = nx;
+    } else {
+        g.n = ny; g.nlines = nx; g.ps = nx; g.ls = 1;
+    }
+    g.H = H;
+    g.own = kW - 2 * H;
+    if (g.own > g.n) g.own = g.n;
+    g.nwin = (g.n + g.own - 1) / g.own;
+    g.ngroups = (g.nlines + kNL - 1) / kNL;
+    return g;
+}
+
+template <class P1, class P2, bool SECOND>
+size_t smem_bytes() {
+    return (size_t)kNL * kLW * sizeof(typename P1::V) + (size_t)kNL * kW * sizeof(typename P1::O) +
+           (SECOND ? (size_t)kNL * kW * sizeof(typename P2::V) : 0);
+}
+
+template <int AXIS, class P1, class P2, bool SIXTH, bool SECOND, class In, class Epi>
+cudaError_t launch_lines_t(In in, const LineGeo& g, int order, Epi epi, DevState* st, int bump,
+                           cudaStream_t s) {
+    auto kern = k_lines<AXIS, P1, P2, SIXTH, SECOND, In, Epi>;
+    const size_t smem = smem_bytes<P1, P2, SECOND>();
+    static bool attr = false;  // one flag per kernel instantiation
+    if (!attr) {
+        cudaError_t e =
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const unsigned blocks = (unsigned)((long long)g.ngroups * g.nwin);
+    kern<<<blocks, kNL * 32, smem, s>>>(in, g, make_const<P1>(order), make_const<P2>(order), epi,
+                                        st, bump);
+    return cudaGetLastError();
+}
+
+// dispatch on axis and scheme order
+template <class P1, class P2, bool SECOND, class In, class Epi>
+cudaError_t launch_lines(In in, int nx, int ny, int axis, int order, double eps1, double eps2,
+                         Epi epi, DevState* st, int bump, cudaStream_t s) {
+    const LineGeo g = make_geo(nx, ny, axis, halo(order, eps1, SECOND, eps2));
+    if (axis == 0) {
+        if (order == 6)
+            return launch_lines_t<0, P1, P2, true, SECOND>(in, g, order, epi, st, bump, s);
+        return launch_lines_t<0, P1, P2, false, SECOND>(in, g, order, epi, st, bump, s);
+    }
+    if (order == 6) return launch_lines_t<1, P1, P2, true, SECOND>(in, g, order, epi, st, bump, s);
+    return launch_lines_t<1, P1, P2, false, SECOND>(in, g, order, epi, st, bump, s);
+}
+
+// rounding levels the recursions are cut at
+constexpr double kEpsD = 1e-17, kEpsDF = 1e-15, kEpsF = 1e-8;
+
+}  // namespace
+
+// ---- FP64 path ----
+cudaError_t lines_fp64_rho_x(const double* rho, double* dxr, double* dxx, int nx, int ny,
+                             int order, DevState* st, int bump, cudaStream_t s) {
+    return launch_lines<PolD, PolD, true>(InD{rho}, nx, ny, 0, order, kEpsD, kEpsD,
+                                          EpiStore<double, double>{dxr, dxx}, st, bump, s);
+}
+cudaError_t lines_fp64_rho_y_mu(const double* rho, const double* dxx, double* dyr, double* mu,
+                                int nx, int ny, int order, const PhysParams& p, DevState* st,
+                                cudaStream_t s) {
+    EpiMu<double, double, double> epi{dyr, mu, rho, dxx, p.T, p.a, p.b, p.R, p.k2, p.kappa,
+                                      p.mu_cap, p.cap_steps, false};
+    return launch_lines<PolD, PolD, true>(InD{rho}, nx, ny, 1, order, kEpsD, kEpsD, epi, st, 0, s);
+}
+cudaError_t lines_fp64_force(const double* mu, const double* rho, const double* dr, double* F,
+                             int nx, int ny, int axis, int order, cudaStream_t s) {
+    return launch_lines<PolD, PolD, false>(InD{mu}, nx, ny, axis, order, kEpsD, kEpsD,
+                                           EpiForce<double, double>{F, rho, dr}, nullptr, 0, s);
+}
+cudaError_t lines_fp64_plain(const double* u, double* d1, double* d2, int nx, int ny, int axis,
+                             int order, cudaStream_t s) {
+    if (d2)
+        return launch_lines<PolD, PolD, true>(InD{u}, nx, ny, axis, order, kEpsD, kEpsD,
+                                              EpiStore<double, double>{d1, d2}, nullptr, 0, s);
+    return launch_lines<PolD, PolD, false>(InD{u}, nx, ny, axis, order, kEpsD, kEpsD,
+                                           EpiStore<double, double>{d1, nullptr}, nullptr, 0, s);
+}
+
+// ---- mixed path ----
+cudaError_t lines_mixed_rho_x(const float* rh, const float* rl, float* dxr, float* dxx, int nx,
+                              int ny, int order, DevState* st, int bump, cudaStream_t s) {
+    return launch_lines<PolDF, PolF, true>(InDF{rh, rl}, nx, ny, 0, order, kEpsDF, kEpsF,
+                                           EpiStore<float, float>{dxr, dxx}, st, bump, s);
+}
+cudaError_t lines_mixed_rho_y_mu(const float* rh, const float* rl, const float* dxx, float* dyr,
+                                 float* mu, int nx, int ny, int order, const PhysParams& p,
+                                 DevState* st, cudaStream_t s) {
+    EpiMu<float, float, float> epi{dyr, mu, rh, dxx, (float)p.T, (float)p.a, (float)p.b,
+                                   (float)p.R, (float)p.k2, (float)p.kappa,
+                                   (float)fmin(p.mu_cap, (double)FLT_MAX), p.cap_steps, false};
+    return launch_lines<PolDF, PolF, true>(InDF{rh, rl}, nx, ny, 1, order, kEpsDF, kEpsF, epi, st,
+                                           0, s);
+}
+cudaError_t lines_mixed_force(const float* mu, const float* rh, const float* dr, float* F, int nx,
+                              int ny, int axis, int order, cudaStream_t s) {
+    return launch_lines<PolF, PolF, false>(InF{mu}, nx, ny, axis, order, kEpsF, kEpsF,
+                                           EpiForce<float, float>{F, rh, dr}, nullptr, 0, s);
+}
+cudaError_t lines_mixed_plain(const float* uh, const float* ul, float* d1, float* d2, int nx,
+                              int ny, int axis, int order, cudaStream_t s) {
+    if (d2)
+        return launch_lines<PolDF, PolF, true>(InDF{uh, ul}, nx, ny, axis, order, kEpsDF, kEpsF,
+                                               EpiStore<float, float>{d1, d2}, nullptr, 0, s);
+    return launch_lines<PolDF, PolF, false>(InDF{uh, ul}, nx, ny, axis, order, kEpsDF, kEpsF,
+                                            EpiStore<float, float>{d1, nullptr}, nullptr, 0, s);
+}
+
+}  // namespace cplbm

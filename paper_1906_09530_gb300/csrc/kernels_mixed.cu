@@ -1,0 +1,275 @@
+// kernels_mixed.cu -- lattice kernels of the mixed-precision path: FP32
+// populations and collision, the density kept as a double-float pair; its line
+// solves are in kernels_lines.cu (double-float first derivatives of the density,
+// FP32 second derivatives, chemical potential and force).
+//
+// Why this split (GB300 runs FP64 at 1/64 of the FP32 rate, so FP64 arithmetic
+// in the line solves would bound the whole step):
+//   * The density is the sum of nine FP32 populations; it is kept exactly, as an
+//     unevaluated sum hi + lo of two floats ("double-float", DF).
+//   * d rho enters the force (Eq. 12).  Near an interface a compact-FD line
+//     solve mixes liquid-scale values into gas-side derivatives with weight
+//     lam^d; FP32 rounding there (6e-8 of rho_l) would be an error of relative
+//     size ~6e-8 rho_l / rho_g in the gas gradient, i.e. an inconsistent force
+//     that shifts the coexistence density.  The solve is therefore carried in DF
+//     (about 2^-44 relative to the line's values) and only the result is rounded
+//     to FP32, which is relative to the derivative's own magnitude.
+//   * d_xx rho, d_yy rho enter mu-hat multiplied by kappa; mu0 and mu-hat are
+//     O(T ln rho); the force is rounded relative to itself.  FP32 errors in these
+//     move mu by ~1e-7 of its size, i.e. relative density shifts ~1e-6, far below
+//     the 1e-3 coexistence tolerance.
+// FP32 rounding of all DF operations is forced with __fadd_rn/__fmul_rn so the
+// compiler cannot contract them into fused multiply-adds.
+#include <cfloat>
+#include <cmath>
+
+#include "cplbm_internal.cuh"
+#include "df.cuh"
+
+namespace cplbm {
+
+namespace {
+
+__device__ __forceinline__ int wrapi(int v, int n) {
+    v %= n;
+    return v < 0 ? v + n : v;
+}
+__device__ __forceinline__ int nexti(int v, int n) { return v + 1 == n ? 0 : v + 1; }
+
+// D2Q9 (Sec. 2)
+__host__ __device__ __forceinline__ constexpr int ex(int i) {
+    return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+__host__ __device__ __forceinline__ constexpr int ey(int i) {
+    return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+__host__ __device__ __forceinline__ constexpr float wqf(int i) {
+    return i == 0 ? 4.0f / 9.0f : (i < 5 ? 1.0f / 9.0f : 1.0f / 36.0f);
+}
+
+__device__ __forceinline__ df sum9_df(const float g[9]) {
+    df s{g[0], 0.0f};
+#pragma unroll
+    for (int i = 1; i < 9; ++i) s = df_add_f(s, g[i]);
+    return s;
+}
+
+__device__ __forceinline__ void raise_flag(DevState* st, unsigned bits, int64_t t) {
+    atomicOr(&st->flag, bits);
+    atomicMin(&st->failed_t, (unsigned long long)t);
+}
+
+// ---------------------------------------------------------------------------
+// Pass 1, mixed: fused collide-stream in FP32 (same tile scheme as the FP64
+// kernel), the new density written as the exact DF sum of the nine streamed
+// populations.
+// ---------------------------------------------------------------------------
+template <int BX, int BY>
+__global__ void __launch_bounds__(BX* BY)
+    k_cs_mixed(const float* __restrict__ fin, float* __restrict__ fout,
+               const float* __restrict__ Fx, const float* __restrict__ Fy,
+               float* __restrict__ rho_hi, float* __restrict__ rho_lo, int nx, int ny,
+               size_t plane, float omega, DevState* __restrict__ st) {
+    constexpr int HX = BX + 2, HY = BY + 2, HN = HX * HY;
+    __shared__ float sf[9][HN];
+    const int tid = threadIdx.x + BX * threadIdx.y;
+    const int gx0 = blockIdx.x * BX - 1, gy0 = blockIdx.y * BY - 1;
+    bool ok = true;
+    const float keep = 1.0f - omega;
+    for (int k = tid; k < HN; k += BX * BY) {
+        const int ly = k / HX, lx = k - ly * HX;
+        const int gx = wrapi(gx0 + lx, nx), gy = wrapi(gy0 + ly, ny);
+        const size_t n = (size_t)gy * nx + gx;
+        float f[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i] = fin[i * plane + n];
+        // moments (Eq. 3), forcing (Eq. 5), BGK (Eq. 1)
+        const float rho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+        const float jx = (f[1] + f[5] + f[8]) - (f[3] + f[6] + f[7]);
+        const float jy = (f[2] + f[5] + f[6]) - (f[4] + f[7] + f[8]);
+        const float inv = 1.0f / rho;
+        const float ux = jx * inv, uy = jy * inv;
+        const float vx = ux + Fx[n] * inv, vy = uy + Fy[n] * inv;
+        const float uu = ux * ux + uy * uy, vv = vx * vx + vy * vy;
+        ok &= rho > 0.0f && rho < FLT_MAX;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const float eu = (float)ex(i) * ux + (float)ey(i) * uy;
+            const float ev = (float)ex(i) * vx + (float)ey(i) * vy;
+            const float fu = wqf(i) * rho * (1.0f + 3.0f * eu + 4.5f * eu * eu - 1.5f * uu);
+            const float fv = wqf(i) * rho * (1.0f + 3.0f * ev + 4.5f * ev * ev - 1.5f * vv);
+            sf[i][k] = fv + keep * (f[i] - fu);
+        }
+    }
+    __syncthreads();
+    const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y;
+    if (x < nx && y < ny) {
+        const int lx = threadIdx.x + 1, ly = threadIdx.y + 1;
+        const size_t n = (size_t)y * nx + x;
+        float g[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            g[i] = sf[i][(ly - ey(i)) * HX + (lx - ex(i))];
+            fout[i * plane + n] = g[i];
+        }
+        const df r = sum9_df(g);
+        rho_hi[n] = r.hi;
+        rho_lo[n] = r.lo;
+    }
+    if (!ok) raise_flag(st, FLAG_RHO, st->t);
+}
+
+// f = f^eq(rho, u) in FP64, stored as FP32; rho = DF sum of the stored floats.
+__global__ void k_init_mixed(const double* __restrict__ rho, const double* __restrict__ ux,
+                             const double* __restrict__ uy, float* __restrict__ f,
+                             float* __restrict__ rh, float* __restrict__ rl, size_t N,
+                             size_t plane) {
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
+         n += (size_t)gridDim.x * blockDim.x) {
+        const double r = rho[n];
+        const double u = ux ? ux[n] : 0.0, v = uy ? uy[n] : 0.0;
+        const double uu = u * u + v * v;
+        float g[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const double eu = ex(i) * u + ey(i) * v;
+            const double w = i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+            g[i] = (float)(w * r * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu));
+            f[i * plane + n] = g[i];
+        }
+        const df s = sum9_df(g);
+        rh[n] = s.hi;
+        rl[n] = s.lo;
+    }
+}
+
+__global__ void k_rho_from_f_mixed(const float* __restrict__ f, float* __restrict__ rh,
+                                   float* __restrict__ rl, size_t N, size_t plane) {
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
+         n += (size_t)gridDim.x * blockDim.x) {
+        float g[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) g[i] = f[i * plane + n];
+        const df s = sum9_df(g);
+        rh[n] = s.hi;
+        rl[n] = s.lo;
+    }
+}
+
+// FP64 outputs of the mixed state: rho = hi + lo, v = u + F/(2 rho), mu-hat.
+__global__ void k_macro_mixed(const float* __restrict__ f, const float* __restrict__ rh,
+                              const float* __restrict__ rl, const float* __restrict__ Fx,
+                              const float* __restrict__ Fy, const float* __restrict__ mu,
+                              double* rho_o, double* vx, double* vy, double* mu_o, size_t N,
+                              size_t plane) {
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
+         n += (size_t)gridDim.x * blockDim.x) {
+        double g[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) g[i] = (double)f[i * plane + n];
+        const double r = (double)rh[n] + (double)rl[n];
+        const double jx = (g[1] + g[5] + g[8]) - (g[3] + g[6] + g[7]);
+        const double jy = (g[2] + g[5] + g[6]) - (g[4] + g[7] + g[8]);
+        if (rho_o) rho_o[n] = r;
+        if (vx) vx[n] = (jx + 0.5 * (double)Fx[n]) / r;
+        if (vy) vy[n] = (jy + 0.5 * (double)Fy[n]) / r;
+        if (mu_o) mu_o[n] = (double)mu[n];
+    }
+}
+
+constexpr int kDiagT = 256;
+
+__global__ void __launch_bounds__(kDiagT)
+    k_diag_mixed(const float* __restrict__ f, const float* __restrict__ rh,
+                 const float* __restrict__ rl, const float* __restrict__ Fx,
+                 const float* __restrict__ Fy, size_t N, size_t plane,
+                 double* __restrict__ partials) {
+    double s = 0.0, vmax = 0.0, rmin = DBL_MAX, rmax = -DBL_MAX;
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
+         n += (size_t)gridDim.x * blockDim.x) {
+        double g[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) g[i] = (double)f[i * plane + n];
+        const double r = (double)rh[n] + (double)rl[n];
+        const double jx = (g[1] + g[5] + g[8]) - (g[3] + g[6] + g[7]);
+        const double jy = (g[2] + g[5] + g[6]) - (g[4] + g[7] + g[8]);
+        const double u = (jx + 0.5 * (double)Fx[n]) / r, v = (jy + 0.5 * (double)Fy[n]) / r;
+        s += r;
+        vmax = fmax(vmax, sqrt(u * u + v * v));
+        rmin = fmin(rmin, r);
+        rmax = fmax(rmax, r);
+    }
+    __shared__ double sh[4][kDiagT];
+    sh[0][threadIdx.x] = s;
+    sh[1][threadIdx.x] = vmax;
+    sh[2][threadIdx.x] = rmin;
+    sh[3][threadIdx.x] = rmax;
+    __syncthreads();
+    for (int w = kDiagT / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
+            sh[1][threadIdx.x] = fmax(sh[1][threadIdx.x], sh[1][threadIdx.x + w]);
+            sh[2][threadIdx.x] = fmin(sh[2][threadIdx.x], sh[2][threadIdx.x + w]);
+            sh[3][threadIdx.x] = fmax(sh[3][threadIdx.x], sh[3][threadIdx.x + w]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 4; ++q) partials[4 * blockIdx.x + q] = sh[q][0];
+}
+
+inline unsigned grid_for(size_t n, int threads) {
+    size_t b = (n + threads - 1) / threads;
+    return (unsigned)(b < 65535 * 16 ? (b ? b : 1) : 65535 * 16);
+}
+
+}  // namespace
+
+constexpr int kCsMBX = 32, kCsMBY = 8;
+
+cudaError_t launch_cs_mixed(const float* fin, float* fout, const float* Fx, const float* Fy,
+                            float* rh, float* rl, int nx, int ny, size_t plane, double omega,
+                            DevState* st, cudaStream_t s) {
+    dim3 block(kCsMBX, kCsMBY);
+    dim3 grid((nx + kCsMBX - 1) / kCsMBX, (ny + kCsMBY - 1) / kCsMBY);
+    k_cs_mixed<kCsMBX, kCsMBY><<<grid, block, 0, s>>>(fin, fout, Fx, Fy, rh, rl, nx, ny, plane,
+                                                      (float)omega, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_mixed(const double* rho, const double* ux, const double* uy, float* f,
+                              float* rh, float* rl, int nx, int ny, size_t plane,
+                              cudaStream_t s) {
+    const size_t N = (size_t)nx * ny;
+    k_init_mixed<<<grid_for(N, 256), 256, 0, s>>>(rho, ux, uy, f, rh, rl, N, plane);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rho_from_f_mixed(const float* f, float* rh, float* rl, int nx, int ny,
+                                    size_t plane, cudaStream_t s) {
+    const size_t N = (size_t)nx * ny;
+    k_rho_from_f_mixed<<<grid_for(N, 256), 256, 0, s>>>(f, rh, rl, N, plane);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_macro_mixed(const float* f, const float* rh, const float* rl,
+                               const float* Fx, const float* Fy, const float* mu, double* rho,
+                               double* vx, double* vy, double* mu_o, int nx, int ny,
+                               size_t plane, cudaStream_t s) {
+    const size_t N = (size_t)nx * ny;
+    k_macro_mixed<<<grid_for(N, 256), 256, 0, s>>>(f, rh, rl, Fx, Fy, mu, rho, vx, vy, mu_o, N,
+                                                   plane);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_diag_mixed(const float* f, const float* rh, const float* rl, const float* Fx,
+                              const float* Fy, int nx, int ny, size_t plane, double* partials,
+                              int nparts, DevState* st, cudaStream_t s) {
+    const size_t N = (size_t)nx * ny;
+    k_diag_mixed<<<nparts, kDiagT, 0, s>>>(f, rh, rl, Fx, Fy, N, plane, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_diag_final(partials, nparts, st, s);
+}
+
+}  // namespace cplbm
