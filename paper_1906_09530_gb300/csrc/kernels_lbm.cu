@@ -9,6 +9,7 @@
 #include <climits>
 
 #include "cplbm_internal.cuh"
+#include "lattice.cuh"
 
 namespace cplbm {
 namespace {
@@ -26,10 +27,6 @@ __host__ __device__ __forceinline__ constexpr T wq(int i) {
     return i == 0 ? T(4.0 / 9.0) : (i < 5 ? T(1.0 / 9.0) : T(1.0 / 36.0));
 }
 
-__device__ __forceinline__ int wrap(int v, int n) {
-    v %= n;
-    return v < 0 ? v + n : v;
-}
 
 template <typename T>
 __device__ __forceinline__ T sum9(const T f[9]) {
@@ -44,33 +41,13 @@ __device__ __forceinline__ T feq(int i, T rho, T ux, T uy, T uu) {
     return wq<T>(i) * rho * (T(1) + T(3) * eu + T(4.5) * eu * eu - T(1.5) * uu);
 }
 
-// BGK collision with exact-difference forcing, in place on f[9]:
-//   f_i* = f_i - (f_i - f_i^eq(rho,u))/tau + [f_i^eq(rho,u+F/rho) - f_i^eq(rho,u)]
-//        = f_i^eq(rho, u + F/rho) + (1 - 1/tau)(f_i - f_i^eq(rho, u))      (Eqs. 1, 5)
-// Returns false when rho is not a finite positive number.
-template <typename T>
-__device__ __forceinline__ bool collide(T f[9], T Fx, T Fy, T omega) {
-    const T rho = sum9(f);
-    const T jx = (f[1] + f[5] + f[8]) - (f[3] + f[6] + f[7]);
-    const T jy = (f[2] + f[5] + f[6]) - (f[4] + f[7] + f[8]);
-    const T inv = T(1) / rho;
-    const T ux = jx * inv, uy = jy * inv;
-    const T vx = ux + Fx * inv, vy = uy + Fy * inv;
-    const T uu = ux * ux + uy * uy, vv = vx * vx + vy * vy;
-    const T keep = T(1) - omega;
-#pragma unroll
-    for (int i = 0; i < 9; ++i)
-        f[i] = feq<T>(i, rho, vx, vy, vv) + keep * (f[i] - feq<T>(i, rho, ux, uy, uu));
-    return rho > T(0) && rho < T(FLT_MAX);
-}
-
 __device__ __forceinline__ void raise_flag(DevState* st, unsigned bits, int64_t t) {
     atomicOr(&st->flag, bits);
     atomicMin(&st->failed_t, (unsigned long long)t);
 }
 
 // ---------------------------------------------------------------------------
-// Pass 1: fused collide + stream (pull from a shared-memory tile).
+// Pass 1, FP64: fused collide + stream (pull from a shared-memory tile).
 // A block owns a BX x BY tile of destination nodes.  It first collides the
 // tile plus a one-node periodic halo (post-collision values to shared memory),
 // then every destination node gathers f_i*(x - e_i) from shared memory, writes
@@ -89,12 +66,12 @@ __global__ void __launch_bounds__(BX* BY)
     bool ok = true;
     for (int k = tid; k < HN; k += BX * BY) {
         const int ly = k / HX, lx = k - ly * HX;
-        const int gx = wrap(gx0 + lx, nx), gy = wrap(gy0 + ly, ny);
+        const int gx = wrap_near(gx0 + lx, nx), gy = wrap_near(gy0 + ly, ny);
         const size_t n = (size_t)gy * nx + gx;
         TF f[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i] = fin[i * plane + n];
-        ok &= collide<TF>(f, (TF)Fx[n], (TF)Fy[n], omega);
+        ok &= collide_pairs<TF>(f, (TF)Fx[n], (TF)Fy[n], omega, (TF)FLT_MAX);
 #pragma unroll
         for (int i = 0; i < 9; ++i) sf[i][k] = f[i];
     }
@@ -106,7 +83,7 @@ __global__ void __launch_bounds__(BX* BY)
         TF g[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            g[i] = sf[i][(ly - ey(i)) * HX + (lx - ex(i))];
+            g[i] = sf[i][(ly - q_ey(i)) * HX + (lx - q_ex(i))];
             fout[i * plane + n] = g[i];
         }
         rho_out[n] = (double)sum9(g);
@@ -265,7 +242,7 @@ inline unsigned grid_for(size_t n, int threads) {
 }  // namespace
 
 // Tile of the collide-stream pass: 32 x 8 destination nodes per block.
-constexpr int kCsBX = 32, kCsBY = 8;
+constexpr int kCsBX = 32, kCsBY = 16;
 
 template <typename TF>
 cudaError_t launch_collide_stream(const TF* fin, TF* fout, const double* Fx, const double* Fy,

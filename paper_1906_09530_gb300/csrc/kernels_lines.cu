@@ -52,6 +52,11 @@ struct PolD {
     static __device__ __forceinline__ V down(V a, int o) { return __shfl_down_sync(kFull, a, o); }
     static __device__ __forceinline__ O out(V a) { return a; }
     static K konst(double v) { return v; }
+    // shared-memory staging: one plane of S
+    using S = double;
+    static constexpr int kPlanes = 1;
+    static __device__ __forceinline__ V sget(const S* t, int i, int) { return t[i]; }
+    static __device__ __forceinline__ void sput(S* t, int i, int, V v) { t[i] = v; }
 };
 
 struct PolF {
@@ -66,6 +71,10 @@ struct PolF {
     static __device__ __forceinline__ V down(V a, int o) { return __shfl_down_sync(kFull, a, o); }
     static __device__ __forceinline__ O out(V a) { return a; }
     static K konst(double v) { return (float)v; }
+    using S = float;
+    static constexpr int kPlanes = 1;
+    static __device__ __forceinline__ V sget(const S* t, int i, int) { return t[i]; }
+    static __device__ __forceinline__ void sput(S* t, int i, int, V v) { t[i] = v; }
 };
 
 struct PolDF {
@@ -89,6 +98,16 @@ struct PolDF {
         r.lo = (float)(v - (double)r.hi);
         return r;
     }
+    // hi and lo in two planes, `ps` floats apart (no bank conflicts for 4-byte words)
+    using S = float;
+    static constexpr int kPlanes = 2;
+    static __device__ __forceinline__ V sget(const S* t, int i, int ps) {
+        return df{t[i], t[i + ps]};
+    }
+    static __device__ __forceinline__ void sput(S* t, int i, int ps, V v) {
+        t[i] = v.hi;
+        t[i + ps] = v.lo;
+    }
 };
 
 // value of the second-derivative arithmetic from the first's right-hand side
@@ -102,7 +121,13 @@ __device__ __forceinline__ typename P2::V to2(df v) { return (typename P2::V)v.h
 constexpr int kC = 13;         // positions per lane
 constexpr int kW = 32 * kC;    // window length
 constexpr int kNL = 8;         // lines (warps) per block
-constexpr int kLW = kW + 9;    // shared-memory stride of one staged line (margin 4 + 4, odd)
+// Shared-memory strides of one line in the staged input (window + margin 4 on
+// each side) and in the outputs.  Both are 4 mod 32: lanes reading chunk starts
+// (stride 13) and the y-line staging/epilogue (8 lines x 4 positions per warp)
+// then touch 32 distinct banks.
+constexpr int kLW = 452;
+constexpr int kSO = 420;
+static_assert(kLW >= kW + 8 && kLW % 32 == 4 && kSO >= kW && kSO % 32 == 4, "strides");
 
 template <class P>
 struct LineConst {
@@ -158,10 +183,12 @@ __global__ void __launch_bounds__(kNL * 32)
     using V1 = typename P1::V;
     using V2 = typename P2::V;
     using O1 = typename P1::O;
+    using S1 = typename P1::S;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    V1* tin = reinterpret_cast<V1*>(smem_raw);                      // [kNL][kLW]
-    O1* tout1 = reinterpret_cast<O1*>(tin + kNL * kLW);             // [kNL][kW]
-    V2* tout2 = reinterpret_cast<V2*>(tout1 + kNL * kW);            // [kNL][kW]
+    constexpr int kPS = kNL * kLW;                                   // plane stride
+    S1* tin = reinterpret_cast<S1*>(smem_raw);                      // [planes][kNL][kLW]
+    O1* tout1 = reinterpret_cast<O1*>(tin + P1::kPlanes * kPS);     // [kNL][kSO]
+    V2* tout2 = reinterpret_cast<V2*>(tout1 + kNL * kSO);           // [kNL][kSO]
 
     if (bump && blockIdx.x == 0 && threadIdx.x == 0) st->t += 1;
     epi.init(st);
@@ -171,11 +198,13 @@ __global__ void __launch_bounds__(kNL * 32)
     const int line0 = grp * kNL;
     const int s = win * g.own;                      // first owned position
     const int e = min(s + g.own, g.n);              // one past the last
-    const long long s0 = (long long)s - g.H;         // window position 0
     const int tid = threadIdx.x;
 
-    // ---- stage the window: positions s0-4 .. s0+kW+3 of kNL lines ----
+    // ---- stage the window: positions s-H-4 .. s-H+kW+3 of kNL lines ----
     constexpr int LWIN = kW + 8;
+    const int p0 = wrapi((long long)s - g.H - 4, g.n);  // line position of window slot 0
+    const bool short_line = g.n < LWIN;
+#pragma unroll 4
     for (int idx = tid; idx < kNL * LWIN; idx += kNL * 32) {
         int l, q;
         if (AXIS == 0) {
@@ -188,23 +217,26 @@ __global__ void __launch_bounds__(kNL * 32)
         const int line = line0 + l;
         V1 v = P1::zero();
         if (line < g.nlines) {
-            const int p = wrapi(s0 - 4 + q, g.n);
+            int p = p0 + q;
+            if (short_line) p %= g.n;
+            else if (p >= g.n) p -= g.n;
             v = in.get((size_t)line * g.ls + (size_t)p * g.ps);
         }
-        tin[l * kLW + q] = v;
+        P1::sput(tin, l * kLW + q, kPS, v);
     }
     __syncthreads();
 
     // ---- per-warp solve of one line ----
     const int w = tid >> 5, lane = tid & 31;
-    const V1* tl = tin + w * kLW + 4;  // tl[q] = window position q, q in [-4, kW+4)
+    const int tb = w * kLW + 4;  // slot of window position 0 of this warp's line
+    auto tl = [&](int q) { return P1::sget(tin, tb + q, kPS); };  // q in [-4, kW+4)
     const int q0 = lane * kC;
 
     V1 r[kC];  // right-hand side, then forward states, then the result
     {
         V1 u[kC + 4];
 #pragma unroll
-        for (int k = 0; k < kC + 4; ++k) u[k] = tl[q0 - 2 + k];
+        for (int k = 0; k < kC + 4; ++k) u[k] = tl(q0 - 2 + k);
 #pragma unroll
         for (int j = 0; j < kC; ++j) {
             V1 b = P1::mulc(P1::sub(u[j + 3], u[j + 1]), k1.c1);
@@ -223,8 +255,8 @@ __global__ void __launch_bounds__(kNL * 32)
                 bx[k] = to2<P2>(r[k - 2]);
             } else {
                 const int qc = q0 - 2 + k;  // in [-2, kW+2)
-                V2 t = (to2<P2>(tl[qc + 1]) - to2<P2>(tl[qc - 1])) * k2.c1;
-                if (SIXTH) t = P2::fmac(to2<P2>(tl[qc + 2]) - to2<P2>(tl[qc - 2]), k2.c2, t);
+                V2 t = (to2<P2>(tl(qc + 1)) - to2<P2>(tl(qc - 1))) * k2.c1;
+                if (SIXTH) t = P2::fmac(to2<P2>(tl(qc + 2)) - to2<P2>(tl(qc - 2)), k2.c2, t);
                 bx[k] = t;
             }
         }
@@ -331,28 +363,35 @@ __global__ void __launch_bounds__(kNL * 32)
     }
 #pragma unroll
     for (int j = 0; j < kC; ++j) {
-        tout1[w * kW + q0 + j] = P1::out(r[j]);
-        if (SECOND) tout2[w * kW + q0 + j] = r2[j];
+        tout1[w * kSO + q0 + j] = P1::out(r[j]);
+        if (SECOND) tout2[w * kSO + q0 + j] = r2[j];
     }
     __syncthreads();
 
     // ---- epilogue over the owned positions, coalesced ----
     const int nown = e - s;
     bool bad = false;
-    for (int idx = tid; idx < kNL * nown; idx += kNL * 32) {
-        int l, q;
-        if (AXIS == 0) {
-            l = idx / nown;
-            q = idx - l * nown;
-        } else {
-            q = idx / kNL;
-            l = idx - q * kNL;
+    if (AXIS == 0) {
+        for (int l = 0; l < kNL; ++l) {
+            const int line = line0 + l;
+            if (line >= g.nlines) break;
+            const size_t ob = (size_t)line * g.ls + (size_t)s;
+#pragma unroll 2
+            for (int q = tid; q < nown; q += kNL * 32) {
+                const int wq = g.H + q;
+                bad |= epi(ob + q, tout1[l * kSO + wq], SECOND ? tout2[l * kSO + wq] : (V2)0);
+            }
         }
-        const int line = line0 + l;
-        if (line >= g.nlines) continue;
-        const size_t o = (size_t)line * g.ls + (size_t)(s + q) * g.ps;
-        const int wq = g.H + q;
-        bad |= epi(o, tout1[l * kW + wq], SECOND ? tout2[l * kW + wq] : (V2)0);
+    } else {
+        const int lmax = min(kNL, g.nlines - line0);
+#pragma unroll 4
+        for (int idx = tid; idx < kNL * nown; idx += kNL * 32) {
+            const int q = idx / kNL, l = idx - q * kNL;
+            if (l >= lmax) continue;
+            const size_t o = (size_t)(line0 + l) + (size_t)(s + q) * g.ps;
+            const int wq = g.H + q;
+            bad |= epi(o, tout1[l * kSO + wq], SECOND ? tout2[l * kSO + wq] : (V2)0);
+        }
     }
     if (bad) raise_flag(st, FLAG_EOS, st->t);
 }
@@ -476,8 +515,9 @@ LineGeo make_geo(int nx, int ny, int axis, int H) {
 
 template <class P1, class P2, bool SECOND>
 size_t smem_bytes() {
-    return (size_t)kNL * kLW * sizeof(typename P1::V) + (size_t)kNL * kW * sizeof(typename P1::O) +
-           (SECOND ? (size_t)kNL * kW * sizeof(typename P2::V) : 0);
+    return (size_t)P1::kPlanes * kNL * kLW * sizeof(typename P1::S) +
+           (size_t)kNL * kSO * sizeof(typename P1::O) +
+           (SECOND ? (size_t)kNL * kSO * sizeof(typename P2::V) : 0);
 }
 
 template <int AXIS, class P1, class P2, bool SIXTH, bool SECOND, class In, class Epi>

@@ -25,16 +25,12 @@
 
 #include "cplbm_internal.cuh"
 #include "df.cuh"
+#include "lattice.cuh"
 
 namespace cplbm {
 
 namespace {
 
-__device__ __forceinline__ int wrapi(int v, int n) {
-    v %= n;
-    return v < 0 ? v + n : v;
-}
-__device__ __forceinline__ int nexti(int v, int n) { return v + 1 == n ? 0 : v + 1; }
 
 // D2Q9 (Sec. 2)
 __host__ __device__ __forceinline__ constexpr int ex(int i) {
@@ -42,9 +38,6 @@ __host__ __device__ __forceinline__ constexpr int ex(int i) {
 }
 __host__ __device__ __forceinline__ constexpr int ey(int i) {
     return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
-}
-__host__ __device__ __forceinline__ constexpr float wqf(int i) {
-    return i == 0 ? 4.0f / 9.0f : (i < 5 ? 1.0f / 9.0f : 1.0f / 36.0f);
 }
 
 __device__ __forceinline__ df sum9_df(const float g[9]) {
@@ -75,31 +68,17 @@ __global__ void __launch_bounds__(BX* BY)
     const int tid = threadIdx.x + BX * threadIdx.y;
     const int gx0 = blockIdx.x * BX - 1, gy0 = blockIdx.y * BY - 1;
     bool ok = true;
-    const float keep = 1.0f - omega;
     for (int k = tid; k < HN; k += BX * BY) {
         const int ly = k / HX, lx = k - ly * HX;
-        const int gx = wrapi(gx0 + lx, nx), gy = wrapi(gy0 + ly, ny);
+        const int gx = wrap_near(gx0 + lx, nx), gy = wrap_near(gy0 + ly, ny);
         const size_t n = (size_t)gy * nx + gx;
         float f[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i] = fin[i * plane + n];
-        // moments (Eq. 3), forcing (Eq. 5), BGK (Eq. 1)
-        const float rho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
-        const float jx = (f[1] + f[5] + f[8]) - (f[3] + f[6] + f[7]);
-        const float jy = (f[2] + f[5] + f[6]) - (f[4] + f[7] + f[8]);
-        const float inv = 1.0f / rho;
-        const float ux = jx * inv, uy = jy * inv;
-        const float vx = ux + Fx[n] * inv, vy = uy + Fy[n] * inv;
-        const float uu = ux * ux + uy * uy, vv = vx * vx + vy * vy;
-        ok &= rho > 0.0f && rho < FLT_MAX;
+        // moments (Eq. 3), exact-difference forcing (Eq. 5), BGK (Eq. 1)
+        ok &= collide_pairs<float>(f, Fx[n], Fy[n], omega, FLT_MAX);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const float eu = (float)ex(i) * ux + (float)ey(i) * uy;
-            const float ev = (float)ex(i) * vx + (float)ey(i) * vy;
-            const float fu = wqf(i) * rho * (1.0f + 3.0f * eu + 4.5f * eu * eu - 1.5f * uu);
-            const float fv = wqf(i) * rho * (1.0f + 3.0f * ev + 4.5f * ev * ev - 1.5f * vv);
-            sf[i][k] = fv + keep * (f[i] - fu);
-        }
+        for (int i = 0; i < 9; ++i) sf[i][k] = f[i];
     }
     __syncthreads();
     const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y;
@@ -109,7 +88,7 @@ __global__ void __launch_bounds__(BX* BY)
         float g[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            g[i] = sf[i][(ly - ey(i)) * HX + (lx - ex(i))];
+            g[i] = sf[i][(ly - q_ey(i)) * HX + (lx - q_ex(i))];
             fout[i * plane + n] = g[i];
         }
         const df r = sum9_df(g);
@@ -225,7 +204,7 @@ inline unsigned grid_for(size_t n, int threads) {
 
 }  // namespace
 
-constexpr int kCsMBX = 32, kCsMBY = 8;
+constexpr int kCsMBX = 32, kCsMBY = 16;
 
 cudaError_t launch_cs_mixed(const float* fin, float* fout, const float* Fx, const float* Fy,
                             float* rh, float* rl, int nx, int ny, size_t plane, double omega,
