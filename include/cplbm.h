@@ -152,6 +152,19 @@ lbm_status lbm_set_populations(lbm_ctx *ctx, const double *h_f, int64_t t);
 lbm_status lbm_diag(lbm_ctx *ctx, double *mass, double *max_v, double *rho_min,
                     double *rho_max);
 
+/* lbm_diag without any device allocation, for callers that cannot call
+ * cudaMalloc (e.g. code whose device memory is all owned by another allocator,
+ * or that may not allocate after start-up).  Same outputs as lbm_diag (FP64
+ * reductions; they agree with lbm_diag to rounding of the summation order).
+ * The reduction's partial sums live in a fixed 512 KB device array inside the
+ * library (one 4-double record per 2048 nodes): grids above 33,554,432 nodes
+ * return LBM_EINVAL.  The paper has no counterpart; this is library plumbing.
+ * The first call on a device looks up that array's device address; make it
+ * before any stream capture.  Calls share the array, so calls that overlap on
+ * the GPU race on it. */
+lbm_status lbm_diag_noalloc(lbm_ctx *ctx, double *mass, double *max_v, double *rho_min,
+                            double *rho_max);
+
 /* Critical point (T_c, rho_c) of the EOS: the point where dp0/drho and
  * d2p0/drho2 both vanish (Sec. 3.2).  Host only. */
 lbm_status lbm_critical(const lbm_eos *eos, double *Tc, double *rhoc);

@@ -69,6 +69,7 @@ def lib():
             "lbm_get_populations": (C.c_int, [_vp, _vp, C.POINTER(C.c_int64)]),
             "lbm_set_populations": (C.c_int, [_vp, _vp, _i64]),
             "lbm_diag": (C.c_int, [_vp, _dp, _dp, _dp, _dp]),
+            "lbm_diag_noalloc": (C.c_int, [_vp, _dp, _dp, _dp, _dp]),
             "lbm_critical": (C.c_int, [C.POINTER(LbmEos), _dp, _dp]),
             "lbm_maxwell": (C.c_int, [C.POINTER(LbmEos), C.c_double, _dp, _dp]),
             "lbm_cfd": (C.c_int, [_vp, _vp, _vp, _i32, _i32, _i32, _i32, _vp]),

@@ -569,18 +569,21 @@ lbm_status lbm_set_populations(lbm_ctx* c, const double* h_f, int64_t t) {
     return read_state(c);
 }
 
-lbm_status lbm_diag(lbm_ctx* c, double* mass, double* max_v, double* rho_min, double* rho_max) {
-    if (!c) return LBM_EINVAL;
+}  // extern "C"
+
+// Body of lbm_diag with the partials buffer and its record count chosen by the
+// caller (lbm_diag: the workspace's; lbm_diag_noalloc: the library's fixed array).
+lbm_status cplbm_diag_with_partials(lbm_ctx* c, double* partials, int nparts, double* mass,
+                                    double* max_v, double* rho_min, double* rho_max) {
     if (!c->ready) return LBM_EINVAL;
     lbm_status st = use_dev(c);
     if (st) return st;
     if (is_fp64(c))
         CK(launch_diag<double>((const double*)c->f[c->cur], c->rho, c->Fx, c->Fy, c->nx, c->ny,
-                               c->plane, c->partials, c->nparts, c->dst, c->stream));
+                               c->plane, partials, nparts, c->dst, c->stream));
     else
         CK(launch_diag_mixed((const float*)c->f[c->cur], c->m_rh, c->m_rl, c->m_Fx, c->m_Fy,
-                             c->nx, c->ny, c->plane, c->partials, c->nparts, c->dst,
-                             c->stream));
+                             c->nx, c->ny, c->plane, partials, nparts, c->dst, c->stream));
     st = read_state(c);
     if (st) return st;
     if (mass) *mass = c->hst->diag[0];
@@ -588,6 +591,15 @@ lbm_status lbm_diag(lbm_ctx* c, double* mass, double* max_v, double* rho_min, do
     if (rho_min) *rho_min = c->hst->diag[2];
     if (rho_max) *rho_max = c->hst->diag[3];
     return LBM_OK;
+}
+int cplbm_ctx_device(const lbm_ctx* c) { return c->dev; }
+size_t cplbm_ctx_nodes(const lbm_ctx* c) { return c->N; }
+
+extern "C" {
+
+lbm_status lbm_diag(lbm_ctx* c, double* mass, double* max_v, double* rho_min, double* rho_max) {
+    if (!c) return LBM_EINVAL;
+    return cplbm_diag_with_partials(c, c->partials, c->nparts, mass, max_v, rho_min, rho_max);
 }
 
 lbm_status lbm_cfd(const double* d_u, double* d_d1, double* d_d2, int32_t nx, int32_t ny,
