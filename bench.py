@@ -44,8 +44,26 @@ PASS_NAMES = ["collide_stream", "cfd_x_rho", "cfd_y_rho_mu", "cfd_x_force", "cfd
 
 
 def pass_bytes(precision):
-    fb = 4 if precision == "mixed" else 8
-    return [9 * fb + 16 + 9 * fb + 8, 24, 32, 32, 32]
+    """Algorithmic bytes per node of each pass: every field read or written once
+    per pass that needs it, in the precision the path stores it."""
+    if precision == "mixed":
+        # f 36+36 (FP32), F 4+4, rho hi/lo 4+4 | rho 8 -> d_x rho 4, d_xx rho 4 |
+        # rho 8, d_xx 4 -> d_y 4, mu 4 | mu 4, rho_hi 4, d rho 4 -> F 4 (x and y)
+        return [88, 16, 20, 16, 16]
+    return [168, 24, 32, 32, 32]  # all FP64
+
+
+def measured_traffic(precision):
+    """DRAM bytes per node per launch from the committed ncu capture, if the
+    kernel sources are unchanged since (else None)."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "traffic_mixed.json")
+    if precision != "mixed" or not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    h = hashlib.sha256(b"".join(open(os.path.join(ROOT, s), "rb").read()
+                                for s in d["sources"])).hexdigest()[:16]
+    return d["bytes_per_node"] if h == d["sources_sha256_16"] else None
 
 
 def workload_name(w, precision):
@@ -286,8 +304,10 @@ def main():
         passes[nm] = {"ms": round(float(mean_pass[i]), 5), "alg_bytes_per_node": pb[i],
                       "GB/s": round(gbs, 1), "frac_hbm": round(gbs / peak, 4)}
     ach = pb[dom] * N / (mean_pass[dom] / 1e3) / 1e9
+    tr = measured_traffic(args.precision)
     roofline = {"bound": "hbm", "kernel": PASS_NAMES[dom], "achieved": ach, "peak": peak,
-                "unit": "GB/s", "frac": ach / peak, "traffic": None,
+                "unit": "GB/s", "frac": ach / peak,
+                "traffic": None if tr is None else tr[PASS_NAMES[dom]] * N,
                 "peak_kind": f"{peak_kind} copy bandwidth",
                 "alg_bytes_per_launch": pb[dom] * N}
     step_gbs = sum(pb) * N / (float(step_ms.mean()) / 1e3) / 1e9
@@ -302,7 +322,9 @@ def main():
                        "parallelism": f"replicas{world}" if world > 1 else "single"},
             "roofline": roofline,
             "step_roofline": {"alg_bytes_per_node": sum(pb), "achieved_GB/s": step_gbs,
-                              "frac": step_gbs / peak},
+                              "frac": step_gbs / peak,
+                              "frac_at_216B_fp64_field_convention":
+                                  216 * N / (float(step_ms.mean()) / 1e3) / 1e9 / peak},
             "passes": passes,
             "graph_back_to_back_mlups": graph_mlups,
             "e2e": e2e, "gpu_launches": 5 * args.steps, "clocks": clk}

@@ -148,19 +148,41 @@ struct LineGeo {
     int ngroups;    // line groups of kNL
 };
 
-// Input readers.  In<P>: a field in P's storage.
+// Asynchronous global -> shared copies (cp.async): the staging loads need no
+// registers, so a thread's whole share of the window is in flight at once.
+__device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+// Input fields: stage(t, i, ps, o) copies the element at global offset o into
+// staging slot i (planes `ps` apart).
 struct InD {
     const double* p;
-    __device__ __forceinline__ double get(size_t o) const { return __ldg(p + o); }
+    __device__ __forceinline__ void stage(double* t, int i, int, size_t o) const {
+        cp_async8(t + i, p + o);
+    }
 };
 struct InF {
     const float* p;
-    __device__ __forceinline__ float get(size_t o) const { return __ldg(p + o); }
+    __device__ __forceinline__ void stage(float* t, int i, int, size_t o) const {
+        cp_async4(t + i, p + o);
+    }
 };
 struct InDF {
     const float* h;
     const float* l;
-    __device__ __forceinline__ df get(size_t o) const { return df{__ldg(h + o), __ldg(l + o)}; }
+    __device__ __forceinline__ void stage(float* t, int i, int ps, size_t o) const {
+        cp_async4(t + i, h + o);
+        cp_async4(t + i + ps, l + o);
+    }
 };
 
 __device__ __forceinline__ int wrapi(long long v, int n) {
@@ -204,7 +226,6 @@ __global__ void __launch_bounds__(kNL * 32)
     constexpr int LWIN = kW + 8;
     const int p0 = wrapi((long long)s - g.H - 4, g.n);  // line position of window slot 0
     const bool short_line = g.n < LWIN;
-#pragma unroll 4
     for (int idx = tid; idx < kNL * LWIN; idx += kNL * 32) {
         int l, q;
         if (AXIS == 0) {
@@ -215,15 +236,16 @@ __global__ void __launch_bounds__(kNL * 32)
             l = idx - q * kNL;
         }
         const int line = line0 + l;
-        V1 v = P1::zero();
         if (line < g.nlines) {
             int p = p0 + q;
             if (short_line) p %= g.n;
             else if (p >= g.n) p -= g.n;
-            v = in.get((size_t)line * g.ls + (size_t)p * g.ps);
+            in.stage(tin, l * kLW + q, kPS, (size_t)line * g.ls + (size_t)p * g.ps);
+        } else {
+            P1::sput(tin, l * kLW + q, kPS, P1::zero());
         }
-        P1::sput(tin, l * kLW + q, kPS, v);
     }
+    cp_async_wait_all();
     __syncthreads();
 
     // ---- per-warp solve of one line ----
@@ -369,29 +391,44 @@ __global__ void __launch_bounds__(kNL * 32)
     __syncthreads();
 
     // ---- epilogue over the owned positions, coalesced ----
+    // Each thread takes elements tid, tid + 256, ...; operands are fetched in
+    // groups of kB before any of the group's results is written.
+    constexpr int kB = 4;
     const int nown = e - s;
+    const int lmax = min(kNL, g.nlines - line0);
+    const int total = kNL * nown;
     bool bad = false;
+    int l0 = 0, q0e = tid;  // AXIS 0 walk: position q0e within line l0
     if (AXIS == 0) {
-        for (int l = 0; l < kNL; ++l) {
-            const int line = line0 + l;
-            if (line >= g.nlines) break;
-            const size_t ob = (size_t)line * g.ls + (size_t)s;
-#pragma unroll 2
-            for (int q = tid; q < nown; q += kNL * 32) {
-                const int wq = g.H + q;
-                bad |= epi(ob + q, tout1[l * kSO + wq], SECOND ? tout2[l * kSO + wq] : (V2)0);
+        while (q0e >= nown && l0 < kNL) { q0e -= nown; ++l0; }
+    }
+    for (int base = tid; base < total; base += kB * kNL * 32) {
+        int slot[kB];
+        size_t off[kB];
+        typename Epi::Ops ops[kB];
+#pragma unroll
+        for (int k = 0; k < kB; ++k) {
+            int ll, qq;
+            if (AXIS == 0) {
+                ll = l0;
+                qq = q0e;
+                q0e += kNL * 32;
+                while (q0e >= nown && l0 < kNL) { q0e -= nown; ++l0; }
+            } else {
+                const int idx = base + k * kNL * 32;
+                qq = idx / kNL;
+                ll = idx - qq * kNL;
             }
+            const bool live = ll < lmax && qq < nown;
+            slot[k] = live ? ll * kSO + g.H + qq : -1;
+            off[k] = AXIS == 0 ? (size_t)(line0 + ll) * g.ls + (size_t)(s + qq)
+                               : (size_t)(line0 + ll) + (size_t)(s + qq) * g.ps;
+            if (live) ops[k] = epi.fetch(off[k]);
         }
-    } else {
-        const int lmax = min(kNL, g.nlines - line0);
-#pragma unroll 4
-        for (int idx = tid; idx < kNL * nown; idx += kNL * 32) {
-            const int q = idx / kNL, l = idx - q * kNL;
-            if (l >= lmax) continue;
-            const size_t o = (size_t)(line0 + l) + (size_t)(s + q) * g.ps;
-            const int wq = g.H + q;
-            bad |= epi(o, tout1[l * kSO + wq], SECOND ? tout2[l * kSO + wq] : (V2)0);
-        }
+#pragma unroll
+        for (int k = 0; k < kB; ++k)
+            if (slot[k] >= 0)
+                bad |= epi(off[k], tout1[slot[k]], SECOND ? tout2[slot[k]] : (V2)0, ops[k]);
     }
     if (bad) raise_flag(st, FLAG_EOS, st->t);
 }
@@ -401,8 +438,10 @@ template <class O, class V2>
 struct EpiStore {
     O* d1;
     V2* d2;
+    struct Ops {};
     __device__ __forceinline__ void init(const DevState*) {}
-    __device__ __forceinline__ bool operator()(size_t o, O a, V2 b) {
+    __device__ __forceinline__ Ops fetch(size_t) const { return Ops{}; }
+    __device__ __forceinline__ bool operator()(size_t o, O a, V2 b, const Ops&) {
         d1[o] = a;
         if (d2) d2[o] = b;
         return false;
@@ -420,15 +459,20 @@ struct EpiMu {
     R T, a, b, Rg, k2, kappa, cap;
     int64_t cap_steps;
     bool capped;
+    struct Ops {
+        RhoT r;
+        O xx;
+    };
     // the time level is read on the device: graph replays reuse the arguments
     __device__ __forceinline__ void init(const DevState* st) { capped = st->t < cap_steps; }
-    __device__ __forceinline__ bool operator()(size_t o, O d1, O d2) {
+    __device__ __forceinline__ Ops fetch(size_t o) const { return Ops{__ldg(rho + o), __ldg(dxx + o)}; }
+    __device__ __forceinline__ bool operator()(size_t o, O d1, O d2, const Ops& op) {
         dyr[o] = d1;
-        const R r = (R)rho[o];
+        const R r = (R)op.r;
         const R eta = R(0.25) * b * r;
         const R om = R(1) - eta;
         const R mu0 = Rg * T * ((R(3) - eta) / (om * om * om) + log(r) + R(1)) - R(2) * a * r;
-        R m = k2 * mu0 - kappa * ((R)dxx[o] + (R)d2);
+        R m = k2 * mu0 - kappa * ((R)op.xx + (R)d2);
         if (capped) m = m < cap ? m : cap;
         mu[o] = (O)m;
         return !(r > R(0) && eta < R(1) && m > -R(1e30) && m < R(1e30));
@@ -441,9 +485,14 @@ struct EpiForce {
     O* F;
     const RhoT* __restrict__ rho;
     const O* __restrict__ dr;
+    struct Ops {
+        RhoT r;
+        O d;
+    };
     __device__ __forceinline__ void init(const DevState*) {}
-    __device__ __forceinline__ bool operator()(size_t o, O dmu, O) {
-        F[o] = -(O)rho[o] * dmu + dr[o] * (O)(1.0 / 3.0);
+    __device__ __forceinline__ Ops fetch(size_t o) const { return Ops{__ldg(rho + o), __ldg(dr + o)}; }
+    __device__ __forceinline__ bool operator()(size_t o, O dmu, O, const Ops& op) {
+        F[o] = -(O)op.r * dmu + op.d * (O)(1.0 / 3.0);
         return false;
     }
 };
