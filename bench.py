@@ -4,8 +4,12 @@
 Workload (default): a 1024 x 1024 periodic static drop of radius 200 in its
 Maxwell gas, Carnahan-Starling EOS (a=1, b=4, R=1) at T_r = 0.5, mesh
 coefficient k = 0.5, 6th-order compact FD, tau = 1, kappa-hat = 0.1, tanh width
-8; populations in FP32, density / derivatives / chemical potential / force in
-FP64 ("mixed").  Synthetic, seeded inputs.
+8, in the mixed precision path (FP32 populations, the density as an exact
+double-float pair, double-float first derivatives of the density, FP32 for the
+rest).  Synthetic, seeded inputs.
+
+Also reported: `equilibrium`, the wall time from lbm_set_fields to
+Maxwell-accurate equilibrium of a flat interface (see equilibrium_time).
 
 One "step" is one time step: the five device passes (collide-stream, x- and
 y-line compact FD of rho with the chemical potential, x- and y-line compact FD
@@ -156,6 +160,48 @@ def cpu_baseline(w, target_s=12.0):
                       f"(after 1 untimed), plain C oracle, 1 thread, {dt:.1f} s"}
 
 
+EQ_WORKLOAD = dict(nx=8, ny=400, T_r=0.8, k=0.1, kappa=0.1, tau=1.0, order=6)
+
+
+def equilibrium_time(precision, max_steps=600_000):
+    """Wall time from lbm_set_fields to Maxwell-accurate equilibrium of a flat
+    interface (quasi-1-D, periodic, height 400, k = 0.1, T_r = 0.8; Sec. 5.1).
+    Checked every 500 steps: done when the bulk gas and liquid densities are both
+    within 1e-3 of the Maxwell pair and moved by < 1e-6 (relative) over the last
+    500 steps."""
+    import numpy as np
+    import paper_1906_09530_gb300 as P
+    from paper_1906_09530_gb300 import workloads as W
+    e = EQ_WORKLOAD
+    rg, rl = P.lbm_maxwell(e["T_r"])
+    rho0 = W.flat(e["nx"], e["ny"], rg, rl, e["ny"] / 2, 4.0 / e["k"])
+    sim = P.Simulation(e["nx"], e["ny"], e["T_r"], e["kappa"], e["tau"], e["k"],
+                       fd_order=e["order"], precision=precision)
+    ny = e["ny"]
+    t0 = time.perf_counter()
+    sim.set_fields(rho0)
+    prev = None
+    done = None
+    while sim.t < max_steps:
+        sim.step(500)
+        r = sim.fields()[0][:, 0]
+        g = np.r_[r[: ny // 10], r[-ny // 10:]].mean()
+        l = r[ny // 2 - ny // 20: ny // 2 + ny // 20].mean()
+        cur = (g, l)
+        if (prev is not None and abs(g / rg - 1) < 1e-3 and abs(l / rl - 1) < 1e-3
+                and abs(g / prev[0] - 1) < 1e-6 and abs(l / prev[1] - 1) < 1e-6):
+            done = time.perf_counter() - t0
+            break
+        prev = cur
+    steps = sim.t
+    sim.close()
+    return {"workload": f"flat-interface-{e['nx']}x{ny}-Tr{e['T_r']}-k{e['k']}-{precision}",
+            "wall_s": done, "steps": steps, "reached": done is not None,
+            "gas_rel_err": float(cur[0] / rg - 1), "liquid_rel_err": float(cur[1] / rl - 1),
+            "criterion": "both bulk densities within 1e-3 of Maxwell and steady to 1e-6 "
+                         "over 500 steps, checked every 500 steps"}
+
+
 def run_reference(args, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -206,6 +252,7 @@ def main():
     ap.add_argument("--size", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-equilibrium", action="store_true")
     args = ap.parse_args()
     w = dict(WORKLOAD)
     if args.size != 1024:
@@ -328,6 +375,8 @@ def main():
             "passes": passes,
             "graph_back_to_back_mlups": graph_mlups,
             "e2e": e2e, "gpu_launches": 5 * args.steps, "clocks": clk}
+    if rank == 0 and not args.no_equilibrium:
+        line["equilibrium"] = equilibrium_time(args.precision)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     if rank == 0:

@@ -1,0 +1,145 @@
+"""Physics acceptance of the CUDA path (mostly the mixed path) on the paper's
+benchmark problems, run to equilibrium on the GPU.
+
+  * coexistence of a flat interface against the Maxwell construction (Sec. 5.1),
+    and the mixed path against the FP64 path on the same problem;
+  * the chemical potential is flat inside each bulk phase (Sec. 5.1, Fig. 5);
+  * the Young-Laplace law: the pressure jump of static drops scales as 1/R
+    (Sec. 5.3, Eq. 40);
+  * Galilean invariance: a drop advected at u0 keeps its shape (Sec. 5.5);
+  * the chemical-potential upper limit keeps mass (Sec. 5.6).
+
+Measured levels these bounds were set against: flat
+coexistence at k = 0.1 settles to gas +7.5e-4 (T_r 0.8) / +1.2e-3 (T_r 0.7) and
+liquid within 2e-4 of Maxwell; drops give Delta P * R constant to < 1% across radii.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import thermo
+from paper_1906_09530_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+TC, _ = thermo.critical_point()
+
+
+def flat_run(T_r, k, ny, steps, precision):
+    from paper_1906_09530_gb300 import Simulation
+    rg, rl = thermo.maxwell(T_r)
+    s = Simulation(8, ny, T_r, 0.1, 1.0, k, fd_order=6, precision=precision)
+    s.set_fields(W.flat(8, ny, rg, rl, ny / 2, 4.0 / k))
+    s.step(steps)
+    rho, _, vy, mu = s.fields()
+    m = s.diag()[0]
+    s.close()
+    r = rho[:, 0]
+    gas = np.r_[r[: ny // 10], r[-ny // 10:]].mean()
+    liq = r[ny // 2 - ny // 20: ny // 2 + ny // 20].mean()
+    return gas / rg - 1, liq / rl - 1, r, mu[:, 0], m
+
+
+@pytest.mark.parametrize("T_r,gas_tol", [(0.8, 1e-3), (0.7, 1.5e-3)])
+def test_flat_coexistence_mixed_vs_maxwell(cuda, T_r, gas_tol):
+    """Sec. 5.1: flat interfaces (k = 0.1, height 400, periodic) settle at the
+    Maxwell densities; at T_r = 0.8 both within 1e-3."""
+    g, l, r, mu, _ = flat_run(T_r, 0.1, 400, 400_000, "mixed")
+    assert abs(l) <= 5e-4
+    assert abs(g) <= gas_tol
+    # Fig. 5: mu-hat flat inside each bulk phase, and nearly equal between them
+    ny = 400
+    mg = np.r_[mu[: ny // 10], mu[-ny // 10:]]
+    ml = mu[ny // 2 - ny // 20: ny // 2 + ny // 20]
+    scale = 0.01 * T_r * TC  # k^2 R T, the size of mu-hat's variations
+    assert mg.std() <= 2e-3 * scale and ml.std() <= 2e-3 * scale
+    assert abs(mg.mean() - ml.mean()) <= 5e-3 * scale
+
+
+def test_flat_coexistence_mixed_matches_fp64(cuda):
+    """The mixed path reproduces the FP64 path's equilibrium densities (bulk means
+    and every bulk node); the mass drift of each stays within its arithmetic's
+    bound (FP64: rounding; mixed: FP32 collision rounding, < 2e-8 per step)."""
+    steps = 300_000
+    gm, lm, rm, _, mm = flat_run(0.7, 0.1, 400, steps, "mixed")
+    gd, ld, rd, _, md = flat_run(0.7, 0.1, 400, steps, "fp64")
+    assert abs(gm - gd) <= 2e-4 and abs(lm - ld) <= 2e-4
+    bulk = np.r_[0:40, 170:230, 360:400]
+    assert np.max(np.abs(rm[bulk] - rd[bulk]) / rd[bulk]) <= 5e-4
+    rg, rl = thermo.maxwell(0.7)
+    m0 = 8 * W.flat(8, 400, rg, rl, 200, 40.0)[:, 0].sum()
+    assert abs(md - m0) / m0 <= 1e-10
+    assert abs(mm - m0) / m0 <= 2e-8 * steps
+
+
+def test_laplace_law_inverse_radius(cuda):
+    """Eq. 40: the bulk pressure jump k^2 [p0(rho_in) - p0(rho_out)] of static drops
+    is inversely proportional to the equal-area radius."""
+    from paper_1906_09530_gb300 import Simulation
+    T_r, k, n = 0.7, 0.25, 192
+    rg, rl = thermo.maxwell(T_r)
+    T = T_r * TC
+    dPR = []
+    for r0 in (29.0, 42.0, 58.0):
+        s = Simulation(n, n, T_r, 0.1, 1.0, k, fd_order=6, precision="mixed")
+        s.set_fields(W.drop(n, n, rg, rl, r0, 4.0 / k))
+        s.step(200_000)
+        rho, vx, vy, _ = s.fields()
+        s.close()
+        y, x = np.mgrid[0:n, 0:n]
+        d = np.hypot(x - n / 2, y - n / 2)
+        R = math.sqrt((rho > 0.5 * (rg + rl)).sum() / math.pi)
+        rin = rho[d < 0.5 * R].mean()
+        rout = rho[d > R + 0.5 * (n / 2 - R)].mean()
+        dP = k * k * (thermo.p0(rin, T) - thermo.p0(rout, T))
+        assert dP > 0 and rout > rg and rin > rl  # Laplace-shifted above Maxwell
+        assert np.hypot(vx, vy).max() < 1e-3  # spurious current
+        dPR.append(dP * R)
+    assert max(dPR) / min(dPR) - 1 <= 0.01
+
+
+def test_galilean_translation(cuda):
+    """Sec. 5.5: a drop advected at u0 = (0.05, 0) for 400 steps equals the drop at
+    rest shifted by 20 nodes, up to the lattice's O(u^2) Galilean error."""
+    from paper_1906_09530_gb300 import Simulation
+    T_r, k, n = 0.7, 0.5, 128
+    rg, rl = thermo.maxwell(T_r)
+    rho0 = W.drop(n, n, rg, rl, 24.0, 8.0)
+    out = []
+    for u0 in (0.0, 0.05):
+        s = Simulation(n, n, T_r, 0.1, 1.0, k, fd_order=6, precision="mixed")
+        s.set_fields(rho0, np.full((n, n), u0), None)
+        s.step(400)
+        out.append(s.fields()[0])
+        s.close()
+    rest, moved = out
+    back = np.roll(moved, -20, axis=1)
+    err = np.abs(back - rest).max() / (rl - rg)
+    assert err <= 0.1
+    # centre of the excess mass over the gas moved by u0 t (the uniform periodic
+    # gas has no visible displacement)
+    def xm(r):
+        ex = np.clip(r - rg, 0.0, None)
+        return (ex * np.arange(n)[None, :]).sum() / ex.sum()
+    assert xm(moved) - xm(rest) == pytest.approx(20.0, abs=0.5)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_upper_limit_keeps_mass_and_stability(cuda, precision):
+    """Sec. 5.6: with the chemical-potential upper limit acting for the first 500
+    steps, a low-temperature drop (T_r = 0.45, ratio 2.3e3) runs stably and the
+    limit leaves the mass alone (FP64: to rounding; mixed: within the FP32
+    collision's drift bound)."""
+    from paper_1906_09530_gb300 import Simulation
+    T_r, k, n = 0.45, 0.5, 256
+    rg, rl = thermo.maxwell(T_r)
+    mu_max = float(thermo.mu0(rl + 0.5 * (1.0 - rl), T_r * TC))
+    s = Simulation(n, n, T_r, 0.1, 1.0, k, fd_order=6, precision=precision, mu_max=mu_max,
+                   mu_cap_steps=500)
+    s.set_fields(W.drop(n, n, rg, rl, 50.0, 8.0))
+    m0 = s.diag()[0]
+    s.step(2000)
+    m1, vmax, rmin, rmax = s.diag()
+    s.close()
+    assert abs(m1 - m0) / m0 <= (1e-11 if precision == "fp64" else 2e-8 * 2000)
+    assert 0 < rmin and rmax < 1.0 and vmax < 0.5
