@@ -40,5 +40,32 @@ __device__ __forceinline__ df df_mul(df x, float ch, float cl) {
 }
 __device__ __forceinline__ float df_round(df x) { return __fadd_rn(x.hi, x.lo); }
 
+// x * c + y with the product left unnormalised before the sum (one
+// renormalisation instead of two; same error bound to within a unit).
+__device__ __forceinline__ df df_fma(df x, float ch, float cl, df y) {
+    const float p = __fmul_rn(x.hi, ch);
+    float e = fmaf(x.hi, ch, -p);
+    e = fmaf(x.hi, cl, e);
+    e = fmaf(x.lo, ch, e);
+    const df s = two_sum(p, y.hi);
+    return quick_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(e, y.lo)));
+}
+
+// Exact sum of nine positive floats as a double-float, for populations whose
+// largest member is normally f[0]: accumulating from f[0] with the exact
+// a + b = s + e split (valid when |running sum| >= |addend|, so exact here
+// whenever f[0] is the largest; otherwise an error of at most one unit of the
+// low part).
+__device__ __forceinline__ df sum9_exact(const float g[9]) {
+    float s = g[0], e = 0.0f;
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        const float t = __fadd_rn(s, g[i]);
+        e = __fadd_rn(e, __fsub_rn(g[i], __fsub_rn(t, s)));
+        s = t;
+    }
+    return quick_two_sum(s, e);
+}
+
 
 }  // namespace cplbm

@@ -84,7 +84,7 @@ struct PolDF {
     static __device__ __forceinline__ V zero() { return df{0.0f, 0.0f}; }
     static __device__ __forceinline__ V sub(V a, V b) { return df_sub(a, b); }
     static __device__ __forceinline__ V mulc(V a, K c) { return df_mul(a, c.hi, c.lo); }
-    static __device__ __forceinline__ V fmac(V a, K c, V b) { return df_add(df_mul(a, c.hi, c.lo), b); }
+    static __device__ __forceinline__ V fmac(V a, K c, V b) { return df_fma(a, c.hi, c.lo, b); }
     static __device__ __forceinline__ V up(V a, int o) {
         return df{__shfl_up_sync(kFull, a.hi, o), __shfl_up_sync(kFull, a.lo, o)};
     }

@@ -40,12 +40,6 @@ __host__ __device__ __forceinline__ constexpr int ey(int i) {
     return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
 }
 
-__device__ __forceinline__ df sum9_df(const float g[9]) {
-    df s{g[0], 0.0f};
-#pragma unroll
-    for (int i = 1; i < 9; ++i) s = df_add_f(s, g[i]);
-    return s;
-}
 
 __device__ __forceinline__ void raise_flag(DevState* st, unsigned bits, int64_t t) {
     atomicOr(&st->flag, bits);
@@ -53,47 +47,80 @@ __device__ __forceinline__ void raise_flag(DevState* st, unsigned bits, int64_t 
 }
 
 // ---------------------------------------------------------------------------
-// Pass 1, mixed: fused collide-stream in FP32 (same tile scheme as the FP64
-// kernel), the new density written as the exact DF sum of the nine streamed
-// populations.
+// Pass 1, mixed, sliding-window form: one warp owns 30 destination columns
+// (lanes 1..30; lanes 0 and 31 collide the one-column halo) and walks down a
+// strip of rows.  The post-collision populations of rows y-1, y and y+1 stay in
+// registers; the pull f_i(x, y) = f_i*(x - e_i) takes the row from those three
+// and the column from the lane itself or a neighbour lane (warp shuffle).  The
+// loads of the next row are issued before the current row is finished.  No
+// shared memory, no block barrier.
 // ---------------------------------------------------------------------------
-template <int BX, int BY>
-__global__ void __launch_bounds__(BX* BY)
-    k_cs_mixed(const float* __restrict__ fin, float* __restrict__ fout,
-               const float* __restrict__ Fx, const float* __restrict__ Fy,
-               float* __restrict__ rho_hi, float* __restrict__ rho_lo, int nx, int ny,
-               size_t plane, float omega, DevState* __restrict__ st) {
-    constexpr int HX = BX + 2, HY = BY + 2, HN = HX * HY;
-    __shared__ float sf[9][HN];
-    const int tid = threadIdx.x + BX * threadIdx.y;
-    const int gx0 = blockIdx.x * BX - 1, gy0 = blockIdx.y * BY - 1;
+constexpr int kSwWarps = 4;  // warps per block
+
+__global__ void __launch_bounds__(kSwWarps * 32)
+    k_cs_mixed_sw(const float* __restrict__ fin, float* __restrict__ fout,
+                  const float* __restrict__ Fx, const float* __restrict__ Fy,
+                  float* __restrict__ rho_hi, float* __restrict__ rho_lo, int nx, int ny,
+                  size_t plane, float omega, int nstrips, int nseg, int rows,
+                  DevState* __restrict__ st) {
+    const int lane = threadIdx.x & 31;
+    const int wid = blockIdx.x * kSwWarps + (threadIdx.x >> 5);
+    if (wid >= nstrips * nseg) return;  // uniform per warp
+    const int strip = wid % nstrips, seg = wid / nstrips;
+    const int x0 = strip * 30;
+    const int gx = wrap_near(x0 - 1 + lane, nx);
+    const int xo = x0 + lane - 1;
+    const bool writer = lane >= 1 && lane <= 30 && xo < nx;
+    const int y0 = seg * rows;
+    const int y1 = min(y0 + rows, ny);
     bool ok = true;
-    for (int k = tid; k < HN; k += BX * BY) {
-        const int ly = k / HX, lx = k - ly * HX;
-        const int gx = wrap_near(gx0 + lx, nx), gy = wrap_near(gy0 + ly, ny);
-        const size_t n = (size_t)gy * nx + gx;
-        float f[9];
+
+    float raw[11];
+    auto fetch = [&](int yr) {
+        const size_t n = (size_t)wrap_near(yr, ny) * nx + gx;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = fin[i * plane + n];
-        // moments (Eq. 3), exact-difference forcing (Eq. 5), BGK (Eq. 1)
-        ok &= collide_pairs<float>(f, Fx[n], Fy[n], omega, FLT_MAX);
+        for (int i = 0; i < 9; ++i) raw[i] = fin[i * plane + n];
+        raw[9] = Fx[n];
+        raw[10] = Fy[n];
+    };
+    auto collide_raw = [&](float out[9]) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) sf[i][k] = f[i];
-    }
-    __syncthreads();
-    const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y;
-    if (x < nx && y < ny) {
-        const int lx = threadIdx.x + 1, ly = threadIdx.y + 1;
-        const size_t n = (size_t)y * nx + x;
+        for (int i = 0; i < 9; ++i) out[i] = raw[i];
+        ok &= collide_pairs<float>(out, raw[9], raw[10], omega, FLT_MAX);
+    };
+    float A[9], B[9], C[9];
+    fetch(y0 - 1);
+    collide_raw(A);
+    fetch(y0);
+    collide_raw(B);
+    fetch(y0 + 1);
+    for (int y = y0; y < y1; ++y) {
+        collide_raw(C);  // row y+1
+        if (y + 1 < y1) fetch(y + 2);
+        // gather row y: e = (ex, ey) comes from row y - ey, column x - ex
         float g[9];
+        g[0] = B[0];
+        g[1] = __shfl_up_sync(0xffffffffu, B[1], 1);
+        g[2] = A[2];
+        g[3] = __shfl_down_sync(0xffffffffu, B[3], 1);
+        g[4] = C[4];
+        g[5] = __shfl_up_sync(0xffffffffu, A[5], 1);
+        g[6] = __shfl_down_sync(0xffffffffu, A[6], 1);
+        g[7] = __shfl_down_sync(0xffffffffu, C[7], 1);
+        g[8] = __shfl_up_sync(0xffffffffu, C[8], 1);
+        if (writer) {
+            const size_t n = (size_t)y * nx + xo;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) fout[i * plane + n] = g[i];
+            const df r = sum9_exact(g);
+            rho_hi[n] = r.hi;
+            rho_lo[n] = r.lo;
+        }
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            g[i] = sf[i][(ly - q_ey(i)) * HX + (lx - q_ex(i))];
-            fout[i * plane + n] = g[i];
+            A[i] = B[i];
+            B[i] = C[i];
         }
-        const df r = sum9_df(g);
-        rho_hi[n] = r.hi;
-        rho_lo[n] = r.lo;
     }
     if (!ok) raise_flag(st, FLAG_RHO, st->t);
 }
@@ -116,7 +143,7 @@ __global__ void k_init_mixed(const double* __restrict__ rho, const double* __res
             g[i] = (float)(w * r * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu));
             f[i * plane + n] = g[i];
         }
-        const df s = sum9_df(g);
+        const df s = sum9_exact(g);
         rh[n] = s.hi;
         rl[n] = s.lo;
     }
@@ -129,7 +156,7 @@ __global__ void k_rho_from_f_mixed(const float* __restrict__ f, float* __restric
         float g[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) g[i] = f[i * plane + n];
-        const df s = sum9_df(g);
+        const df s = sum9_exact(g);
         rh[n] = s.hi;
         rl[n] = s.lo;
     }
@@ -204,15 +231,18 @@ inline unsigned grid_for(size_t n, int threads) {
 
 }  // namespace
 
-constexpr int kCsMBX = 32, kCsMBY = 16;
-
 cudaError_t launch_cs_mixed(const float* fin, float* fout, const float* Fx, const float* Fy,
                             float* rh, float* rl, int nx, int ny, size_t plane, double omega,
                             DevState* st, cudaStream_t s) {
-    dim3 block(kCsMBX, kCsMBY);
-    dim3 grid((nx + kCsMBX - 1) / kCsMBX, (ny + kCsMBY - 1) / kCsMBY);
-    k_cs_mixed<kCsMBX, kCsMBY><<<grid, block, 0, s>>>(fin, fout, Fx, Fy, rh, rl, nx, ny, plane,
-                                                      (float)omega, st);
+    // rows per warp: 32 on large grids, fewer on small ones to keep >= ~4k warps
+    const int nstrips = (nx + 29) / 30;
+    int rows = 32;
+    while (rows > 8 && (long long)nstrips * ((ny + rows - 1) / rows) < 4096) rows /= 2;
+    const int nseg = (ny + rows - 1) / rows;
+    const long long warps = (long long)nstrips * nseg;
+    const unsigned blocks = (unsigned)((warps + kSwWarps - 1) / kSwWarps);
+    k_cs_mixed_sw<<<blocks, kSwWarps * 32, 0, s>>>(fin, fout, Fx, Fy, rh, rl, nx, ny, plane,
+                                                   (float)omega, nstrips, nseg, rows, st);
     return cudaGetLastError();
 }
 
