@@ -44,16 +44,20 @@ WORKLOAD = dict(nx=1024, ny=1024, T_r=0.5, k=0.5, kappa=0.1, tau=1.0, order=6, r
 METRIC = "MLUPS (million lattice-node updates per second) of the full time step"
 # algorithmic bytes per node of each pass: [collide-stream, x rho, y rho + mu, x mu + F_x,
 # y mu + F_y]; populations 4 B (mixed) or 8 B (fp64), fields 8 B
-PASS_NAMES = ["collide_stream", "cfd_x_rho", "cfd_y_rho_mu", "cfd_x_force", "cfd_y_force"]
+PASS_NAMES = {"fp64": ["collide_stream", "cfd_x_rho", "cfd_y_rho_mu", "cfd_x_force",
+                        "cfd_y_force"],
+              "mixed": ["collide_stream", "cfd_rho_xy", "mu_pointwise", "cfd_mu_force_xy"]}
 
 
 def pass_bytes(precision):
     """Algorithmic bytes per node of each pass: every field read or written once
     per pass that needs it, in the precision the path stores it."""
     if precision == "mixed":
-        # f 36+36 (FP32), F 4+4, rho hi/lo 4+4 | rho 8 -> d_x rho 4, d_xx rho 4 |
-        # rho 8, d_xx 4 -> d_y 4, mu 4 | mu 4, rho_hi 4, d rho 4 -> F 4 (x and y)
-        return [88, 16, 20, 16, 16]
+        # collide-stream: f 36 in + 36 out (FP32), F 8, rho hi/lo 8
+        # x|y lines of rho: rho hi/lo 8 read by each direction -> d_x, d_xx, d_y, d_yy 16
+        # mu-hat: rho_hi, d_xx, d_yy 12 -> mu 4
+        # x|y lines of mu-hat: mu 4 by each direction, rho_hi 4, d_x rho, d_y rho 8 -> F 8
+        return [88, 32, 16, 28]
     return [168, 24, 32, 32, 32]  # all FP64
 
 
@@ -294,10 +298,12 @@ def main():
 
     clocks = ClockSampler(bus_id(local))
     barrier()
+    names = PASS_NAMES[args.precision]
     pass_ms = np.zeros((args.steps, 5))
     for i in range(args.steps):
         flush.zero_()
         pass_ms[i] = sim.step_timed()
+    pass_ms = pass_ms[:, :len(names)]
     barrier()
     clk = clocks.stop()
     step_ms = pass_ms.sum(axis=1)
@@ -346,15 +352,15 @@ def main():
     peak, peak_kind = load_peaks()
     dom = int(np.argmax(mean_pass))
     passes = {}
-    for i, nm in enumerate(PASS_NAMES):
+    for i, nm in enumerate(names):
         gbs = pb[i] * N / (mean_pass[i] / 1e3) / 1e9
         passes[nm] = {"ms": round(float(mean_pass[i]), 5), "alg_bytes_per_node": pb[i],
                       "GB/s": round(gbs, 1), "frac_hbm": round(gbs / peak, 4)}
     ach = pb[dom] * N / (mean_pass[dom] / 1e3) / 1e9
     tr = measured_traffic(args.precision)
-    roofline = {"bound": "hbm", "kernel": PASS_NAMES[dom], "achieved": ach, "peak": peak,
+    roofline = {"bound": "hbm", "kernel": names[dom], "achieved": ach, "peak": peak,
                 "unit": "GB/s", "frac": ach / peak,
-                "traffic": None if tr is None else tr[PASS_NAMES[dom]] * N,
+                "traffic": None if tr is None or names[dom] not in tr else tr[names[dom]] * N,
                 "peak_kind": f"{peak_kind} copy bandwidth",
                 "alg_bytes_per_launch": pb[dom] * N}
     step_gbs = sum(pb) * N / (float(step_ms.mean()) / 1e3) / 1e9
@@ -374,7 +380,7 @@ def main():
                                   216 * N / (float(step_ms.mean()) / 1e3) / 1e9 / peak},
             "passes": passes,
             "graph_back_to_back_mlups": graph_mlups,
-            "e2e": e2e, "gpu_launches": 5 * args.steps, "clocks": clk}
+            "e2e": e2e, "gpu_launches": len(names) * args.steps, "clocks": clk}
     if rank == 0 and not args.no_equilibrium:
         line["equilibrium"] = equilibrium_time(args.precision)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -81,9 +81,9 @@ typedef struct {
 
 /* Bytes of device workspace lbm_init needs for this grid and options, or 0
  * if the arguments are invalid.  Layout: two population buffers, the fields
- * (FP64: rho, d_x rho, d_y rho, d_xx rho, mu-hat, F_x, F_y; MIXED: rho hi, rho lo
- * and the same six as FP32), reduction partials and a small device state
- * block, each 256-byte aligned. */
+ * (FP64: rho, d_x rho, d_y rho, d_xx rho, mu-hat, F_x, F_y; MIXED: rho hi, rho lo,
+ * d_x rho, d_y rho, d_xx rho (then mu-hat), d_yy rho, F_x, F_y as FP32), reduction partials
+ * and a small device state block, each 256-byte aligned. */
 size_t lbm_workspace_bytes(const lbm_grid *grid, const lbm_opts *opts);
 
 /* Create a simulation context.
@@ -126,10 +126,12 @@ lbm_status lbm_step_async(lbm_ctx *ctx, int64_t n);
 lbm_status lbm_check(lbm_ctx *ctx);
 
 /* Profiling: run one time step as direct launches (no graph) with a CUDA event
- * recorded on the stream before and after each of its five passes, wait for
- * it, and return the passes' durations in milliseconds:
- *   pass_ms[0] collide-stream, [1] x-lines of rho, [2] y-lines of rho + mu-hat,
- *   [3] x-lines of mu-hat + F_x, [4] y-lines of mu-hat + F_y. */
+ * recorded on the stream before and after each of its passes, wait for it, and
+ * return the passes' durations in milliseconds (5 slots).
+ * FP64: [0] collide-stream, [1] x-lines of rho, [2] y-lines of rho + mu-hat,
+ *       [3] x-lines of mu-hat + F_x, [4] y-lines of mu-hat + F_y.
+ * MIXED: [0] collide-stream, [1] x- and y-lines of rho, [2] mu-hat (pointwise),
+ *       [3] x- and y-lines of mu-hat + F; [4] is 0. */
 lbm_status lbm_step_timed(lbm_ctx *ctx, float *pass_ms);
 
 /* Outputs of the current state to host FP64 [ny][nx] arrays, any may be NULL:

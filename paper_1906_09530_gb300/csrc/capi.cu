@@ -2,15 +2,18 @@
 // the per-step pass schedule (captured in CUDA graphs), host<->device copies,
 // error flag and bounded waits.
 //
-// One time step is five device passes (all on the caller's stream):
+// FP64 path: one time step is five device passes (all on the caller's stream):
 //   1 collide-stream      f^t, F^t           -> f^{t+1}, rho^{t+1}      Eqs. 1-5
 //   2 x-lines of rho      rho                -> d_x rho, d_xx rho       Eqs. 37-39
 //   3 y-lines of rho      rho, d_xx rho      -> d_y rho, mu-hat         Eqs. 21, 33, Sec. 5.6
 //   4 x-lines of mu-hat   mu, rho, d_x rho   -> F_x                     Eq. 12
 //   5 y-lines of mu-hat   mu, rho, d_y rho   -> F_y                     Eq. 12
-// Passes 2-5 compute the force of the new time level; lbm_set_fields runs them
-// once on the initial density.  Each pass needs its input complete over whole
-// lines or all nodes, so they are separate launches.
+// Mixed path: four passes -- collide-stream; the x- and y-lines of rho in one
+// launch (d_x, d_xx, d_y, d_yy rho); mu-hat pointwise (stored over d_xx rho);
+// the x- and y-lines of mu-hat in one launch with the force epilogue.
+// Passes after the first compute the force of the new time level;
+// lbm_set_fields runs them once on the initial density.  Each needs its input
+// complete over whole lines or all nodes, so they are separate launches.
 #include <chrono>
 #include <climits>
 #include <cmath>
@@ -42,7 +45,7 @@ struct lbm_ctx {
     int cur;
     double *rho, *dxr, *dyr, *dxx, *mu, *Fx, *Fy;  // FP64 path
     // mixed path: density as hi/lo floats, the rest FP32
-    float *m_rh, *m_rl, *m_dxr, *m_dyr, *m_dxx, *m_mu, *m_Fx, *m_Fy;
+    float *m_rh, *m_rl, *m_dxr, *m_dyr, *m_dxx, *m_dyy, *m_Fx, *m_Fy;
     double* partials;
     int nparts;
     DevState* dst;   // device
@@ -109,14 +112,15 @@ lbm_status enqueue_force(lbm_ctx* c, cudaStream_t s, int bump, cudaEvent_t* ev =
     const int nx = c->nx, ny = c->ny, o = c->fd_order;
     auto mark = [&](int i) { return ev ? cudaEventRecord(ev[i], s) : cudaSuccess; };
     if (!is_fp64(c)) {
-        CK(lines_mixed_rho_x(c->m_rh, c->m_rl, c->m_dxr, c->m_dxx, nx, ny, o, c->dst, bump, s));
+        // x|y lines of rho together, mu-hat pointwise, x|y lines of mu-hat + force
+        CK(lines_mixed_rho_xy(c->m_rh, c->m_rl, c->m_dxr, c->m_dxx, c->m_dyr, c->m_dyy, nx, ny,
+                              o, c->dst, bump, s));
         CK(mark(0));
-        CK(lines_mixed_rho_y_mu(c->m_rh, c->m_rl, c->m_dxx, c->m_dyr, c->m_mu, nx, ny, o, c->phys,
-                                c->dst, s));
+        CK(launch_mu_mixed(c->m_rh, c->m_dxx, c->m_dyy, nx, ny, c->phys, c->dst, s));
         CK(mark(1));
-        CK(lines_mixed_force(c->m_mu, c->m_rh, c->m_dxr, c->m_Fx, nx, ny, 0, o, s));
+        CK(lines_mixed_force_xy(c->m_dxx, c->m_rh, c->m_dxr, c->m_dyr, c->m_Fx, c->m_Fy, nx, ny,
+                                o, s));
         CK(mark(2));
-        CK(lines_mixed_force(c->m_mu, c->m_rh, c->m_dyr, c->m_Fy, nx, ny, 1, o, s));
         CK(mark(3));
         return LBM_OK;
     }
@@ -321,7 +325,7 @@ lbm_status lbm_init(lbm_ctx** out, const lbm_grid* grid, const lbm_eos* eos, dou
         float* ff = (float*)fields;
         const size_t ffs = L.field_bytes / sizeof(float);
         float** slots[8] = {&c->m_rh, &c->m_rl, &c->m_dxr, &c->m_dyr,
-                            &c->m_dxx, &c->m_mu, &c->m_Fx, &c->m_Fy};
+                            &c->m_dxx, &c->m_dyy, &c->m_Fx, &c->m_Fy};
         for (int i = 0; i < 8; ++i) *slots[i] = ff + i * ffs;
     }
     c->partials = (double*)(c->ws + L.off_parts);
@@ -470,7 +474,8 @@ static lbm_status fields_to_device(lbm_ctx* c, double* rho, double* vx, double* 
     const size_t B = c->N * sizeof(double);
     if (!is_fp64(c)) {
         CK(launch_macro_mixed((const float*)c->f[c->cur], c->m_rh, c->m_rl, c->m_Fx, c->m_Fy,
-                              c->m_mu, rho, vx, vy, mu, c->nx, c->ny, c->plane, c->stream));
+                              rho, vx, vy, c->nx, c->ny, c->plane, c->stream));
+        if (mu) CK(launch_f_to_double<float>(c->m_dxx, mu, c->N, c->stream));  // holds mu-hat
         return LBM_OK;
     }
     if (vx || vy) {

@@ -75,9 +75,8 @@ cudaError_t launch_init_mixed(const double* rho, const double* ux, const double*
 cudaError_t launch_rho_from_f_mixed(const float* f, float* rh, float* rl, int nx, int ny,
                                     size_t plane, cudaStream_t s);
 cudaError_t launch_macro_mixed(const float* f, const float* rh, const float* rl,
-                               const float* Fx, const float* Fy, const float* mu, double* rho,
-                               double* vx, double* vy, double* mu_o, int nx, int ny,
-                               size_t plane, cudaStream_t s);
+                               const float* Fx, const float* Fy, double* rho, double* vx,
+                               double* vy, int nx, int ny, size_t plane, cudaStream_t s);
 cudaError_t launch_diag_mixed(const float* f, const float* rh, const float* rl, const float* Fx,
                               const float* Fy, int nx, int ny, size_t plane, double* partials,
                               int nparts, DevState* st, cudaStream_t s);
@@ -94,13 +93,19 @@ cudaError_t lines_fp64_force(const double* mu, const double* rho, const double* 
                              int nx, int ny, int axis, int order, cudaStream_t s);
 cudaError_t lines_fp64_plain(const double* u, double* d1, double* d2, int nx, int ny, int axis,
                              int order, cudaStream_t s);
-cudaError_t lines_mixed_rho_x(const float* rh, const float* rl, float* dxr, float* dxx, int nx,
-                              int ny, int order, DevState* st, int bump, cudaStream_t s);
-cudaError_t lines_mixed_rho_y_mu(const float* rh, const float* rl, const float* dxx, float* dyr,
-                                 float* mu, int nx, int ny, int order, const PhysParams& p,
-                                 DevState* st, cudaStream_t s);
-cudaError_t lines_mixed_force(const float* mu, const float* rh, const float* dr, float* F, int nx,
-                              int ny, int axis, int order, cudaStream_t s);
+// Mixed path, merged launches: the x- and y-lines of rho together (first and
+// second derivatives); then, after launch_mu_mixed, the x- and y-lines of
+// mu-hat together with the force epilogue.
+cudaError_t lines_mixed_rho_xy(const float* rh, const float* rl, float* dxr, float* dxx,
+                               float* dyr, float* dyy, int nx, int ny, int order, DevState* st,
+                               int bump, cudaStream_t s);
+cudaError_t lines_mixed_force_xy(const float* mu, const float* rh, const float* dxr,
+                                 const float* dyr, float* Fx, float* Fy, int nx, int ny,
+                                 int order, cudaStream_t s);
+// mu-hat = k^2 mu0(rho) - kappa (d_xx + d_yy) rho (Eqs. 21, 33, Sec. 5.6), FP32,
+// written over d_xx rho (`dxx_mu`); flags bad values.
+cudaError_t launch_mu_mixed(const float* rh, float* dxx_mu, const float* dyy, int nx, int ny,
+                            const PhysParams& p, DevState* st, cudaStream_t s);
 cudaError_t lines_mixed_plain(const float* uh, const float* ul, float* d1, float* d2, int nx,
                               int ny, int axis, int order, cudaStream_t s);
 

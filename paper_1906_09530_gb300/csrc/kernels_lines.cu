@@ -166,23 +166,29 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // staging slot i (planes `ps` apart).
 struct InD {
     const double* p;
-    __device__ __forceinline__ void stage(double* t, int i, int, size_t o) const {
+    __device__ __forceinline__ void init(const DevState*) {}
+    __device__ __forceinline__ void stage(double* t, int i, int, size_t o) {
         cp_async8(t + i, p + o);
     }
+    __device__ __forceinline__ bool flagged() const { return false; }
 };
 struct InF {
     const float* p;
-    __device__ __forceinline__ void stage(float* t, int i, int, size_t o) const {
+    __device__ __forceinline__ void init(const DevState*) {}
+    __device__ __forceinline__ void stage(float* t, int i, int, size_t o) {
         cp_async4(t + i, p + o);
     }
+    __device__ __forceinline__ bool flagged() const { return false; }
 };
 struct InDF {
     const float* h;
     const float* l;
-    __device__ __forceinline__ void stage(float* t, int i, int ps, size_t o) const {
+    __device__ __forceinline__ void init(const DevState*) {}
+    __device__ __forceinline__ void stage(float* t, int i, int ps, size_t o) {
         cp_async4(t + i, h + o);
         cp_async4(t + i + ps, l + o);
     }
+    __device__ __forceinline__ bool flagged() const { return false; }
 };
 
 __device__ __forceinline__ int wrapi(long long v, int n) {
@@ -199,9 +205,9 @@ __device__ __forceinline__ void raise_flag(DevState* st, unsigned bits, int64_t 
 // The kernel.  AXIS 0: lines along x (rows, stride 1); AXIS 1: lines along y.
 // ---------------------------------------------------------------------------
 template <int AXIS, class P1, class P2, bool SIXTH, bool SECOND, class In, class Epi>
-__global__ void __launch_bounds__(kNL * 32)
-    k_lines(In in, LineGeo g, LineConst<P1> k1, LineConst<P2> k2, Epi epi, DevState* st,
-            int bump) {
+__device__ __forceinline__ void lines_body(In& in, const LineGeo& g, const LineConst<P1>& k1,
+                                           const LineConst<P2>& k2, Epi& epi, DevState* st,
+                                           int bid) {
     using V1 = typename P1::V;
     using V2 = typename P2::V;
     using O1 = typename P1::O;
@@ -212,11 +218,8 @@ __global__ void __launch_bounds__(kNL * 32)
     O1* tout1 = reinterpret_cast<O1*>(tin + P1::kPlanes * kPS);     // [kNL][kSO]
     V2* tout2 = reinterpret_cast<V2*>(tout1 + kNL * kSO);           // [kNL][kSO]
 
-    if (bump && blockIdx.x == 0 && threadIdx.x == 0) st->t += 1;
-    epi.init(st);
-
-    const int grp = blockIdx.x % g.ngroups;
-    const int win = blockIdx.x / g.ngroups;
+    const int grp = bid % g.ngroups;
+    const int win = bid / g.ngroups;
     const int line0 = grp * kNL;
     const int s = win * g.own;                      // first owned position
     const int e = min(s + g.own, g.n);              // one past the last
@@ -430,7 +433,37 @@ __global__ void __launch_bounds__(kNL * 32)
             if (slot[k] >= 0)
                 bad |= epi(off[k], tout1[slot[k]], SECOND ? tout2[slot[k]] : (V2)0, ops[k]);
     }
+    bad |= in.flagged();
     if (bad) raise_flag(st, FLAG_EOS, st->t);
+}
+
+template <int AXIS, class P1, class P2, bool SIXTH, bool SECOND, class In, class Epi>
+__global__ void __launch_bounds__(kNL * 32)
+    k_lines(In in, LineGeo g, LineConst<P1> k1, LineConst<P2> k2, Epi epi, DevState* st,
+            int bump) {
+    if (bump && blockIdx.x == 0 && threadIdx.x == 0) st->t += 1;
+    epi.init(st);
+    in.init(st);
+    lines_body<AXIS, P1, P2, SIXTH, SECOND>(in, g, k1, k2, epi, st, (int)blockIdx.x);
+}
+
+// x-lines and y-lines of two independent solves in one launch: blocks below
+// nbx take the x windows, the rest the y windows.
+template <class P1, class P2, bool SIXTH, bool SECOND, class InX, class EpiX, class InY,
+          class EpiY>
+__global__ void __launch_bounds__(kNL * 32)
+    k_lines_xy(InX inx, LineGeo gx, EpiX ex, InY iny, LineGeo gy, EpiY ey, LineConst<P1> k1,
+               LineConst<P2> k2, DevState* st, int bump, int nbx) {
+    if (bump && blockIdx.x == 0 && threadIdx.x == 0) st->t += 1;
+    if ((int)blockIdx.x < nbx) {
+        ex.init(st);
+        inx.init(st);
+        lines_body<0, P1, P2, SIXTH, SECOND>(inx, gx, k1, k2, ex, st, (int)blockIdx.x);
+    } else {
+        ey.init(st);
+        iny.init(st);
+        lines_body<1, P1, P2, SIXTH, SECOND>(iny, gy, k1, k2, ey, st, (int)blockIdx.x - nbx);
+    }
 }
 
 // ---- epilogues: return true when a value is bad (flags the run) ----
@@ -587,6 +620,36 @@ cudaError_t launch_lines_t(In in, const LineGeo& g, int order, Epi epi, DevState
     return cudaGetLastError();
 }
 
+template <class P1, class P2, bool SIXTH, bool SECOND, class InX, class EpiX, class InY,
+          class EpiY>
+cudaError_t launch_xy_t(InX inx, EpiX ex, InY iny, EpiY ey, int nx, int ny, int order, int H,
+                        DevState* st, int bump, cudaStream_t s) {
+    auto kern = k_lines_xy<P1, P2, SIXTH, SECOND, InX, EpiX, InY, EpiY>;
+    const size_t smem = smem_bytes<P1, P2, SECOND>();
+    static bool attr = false;  // one flag per kernel instantiation
+    if (!attr) {
+        cudaError_t e =
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const LineGeo gx = make_geo(nx, ny, 0, H), gy = make_geo(nx, ny, 1, H);
+    const int nbx = gx.ngroups * gx.nwin;
+    const unsigned blocks = (unsigned)(nbx + gy.ngroups * gy.nwin);
+    kern<<<blocks, kNL * 32, smem, s>>>(inx, gx, ex, iny, gy, ey, make_const<P1>(order),
+                                        make_const<P2>(order), st, bump, nbx);
+    return cudaGetLastError();
+}
+
+template <class P1, class P2, bool SECOND, class InX, class EpiX, class InY, class EpiY>
+cudaError_t launch_xy(InX inx, EpiX ex, InY iny, EpiY ey, int nx, int ny, int order,
+                      double eps1, double eps2, DevState* st, int bump, cudaStream_t s) {
+    const int H = halo(order, eps1, SECOND, eps2);
+    if (order == 6)
+        return launch_xy_t<P1, P2, true, SECOND>(inx, ex, iny, ey, nx, ny, order, H, st, bump, s);
+    return launch_xy_t<P1, P2, false, SECOND>(inx, ex, iny, ey, nx, ny, order, H, st, bump, s);
+}
+
 // dispatch on axis and scheme order
 template <class P1, class P2, bool SECOND, class In, class Epi>
 cudaError_t launch_lines(In in, int nx, int ny, int axis, int order, double eps1, double eps2,
@@ -634,24 +697,19 @@ cudaError_t lines_fp64_plain(const double* u, double* d1, double* d2, int nx, in
 }
 
 // ---- mixed path ----
-cudaError_t lines_mixed_rho_x(const float* rh, const float* rl, float* dxr, float* dxx, int nx,
-                              int ny, int order, DevState* st, int bump, cudaStream_t s) {
-    return launch_lines<PolDF, PolF, true>(InDF{rh, rl}, nx, ny, 0, order, kEpsDF, kEpsF,
-                                           EpiStore<float, float>{dxr, dxx}, st, bump, s);
+cudaError_t lines_mixed_rho_xy(const float* rh, const float* rl, float* dxr, float* dxx,
+                               float* dyr, float* dyy, int nx, int ny, int order, DevState* st,
+                               int bump, cudaStream_t s) {
+    return launch_xy<PolDF, PolF, true>(InDF{rh, rl}, EpiStore<float, float>{dxr, dxx},
+                                        InDF{rh, rl}, EpiStore<float, float>{dyr, dyy}, nx, ny,
+                                        order, kEpsDF, kEpsF, st, bump, s);
 }
-cudaError_t lines_mixed_rho_y_mu(const float* rh, const float* rl, const float* dxx, float* dyr,
-                                 float* mu, int nx, int ny, int order, const PhysParams& p,
-                                 DevState* st, cudaStream_t s) {
-    EpiMu<float, float, float> epi{dyr, mu, rh, dxx, (float)p.T, (float)p.a, (float)p.b,
-                                   (float)p.R, (float)p.k2, (float)p.kappa,
-                                   (float)fmin(p.mu_cap, (double)FLT_MAX), p.cap_steps, false};
-    return launch_lines<PolDF, PolF, true>(InDF{rh, rl}, nx, ny, 1, order, kEpsDF, kEpsF, epi, st,
-                                           0, s);
-}
-cudaError_t lines_mixed_force(const float* mu, const float* rh, const float* dr, float* F, int nx,
-                              int ny, int axis, int order, cudaStream_t s) {
-    return launch_lines<PolF, PolF, false>(InF{mu}, nx, ny, axis, order, kEpsF, kEpsF,
-                                           EpiForce<float, float>{F, rh, dr}, nullptr, 0, s);
+cudaError_t lines_mixed_force_xy(const float* mu, const float* rh, const float* dxr,
+                                 const float* dyr, float* Fx, float* Fy, int nx, int ny,
+                                 int order, cudaStream_t s) {
+    return launch_xy<PolF, PolF, false>(InF{mu}, EpiForce<float, float>{Fx, rh, dxr}, InF{mu},
+                                        EpiForce<float, float>{Fy, rh, dyr}, nx, ny, order,
+                                        kEpsF, kEpsF, nullptr, 0, s);
 }
 cudaError_t lines_mixed_plain(const float* uh, const float* ul, float* d1, float* d2, int nx,
                               int ny, int axis, int order, cudaStream_t s) {

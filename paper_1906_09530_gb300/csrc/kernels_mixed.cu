@@ -165,9 +165,8 @@ __global__ void k_rho_from_f_mixed(const float* __restrict__ f, float* __restric
 // FP64 outputs of the mixed state: rho = hi + lo, v = u + F/(2 rho), mu-hat.
 __global__ void k_macro_mixed(const float* __restrict__ f, const float* __restrict__ rh,
                               const float* __restrict__ rl, const float* __restrict__ Fx,
-                              const float* __restrict__ Fy, const float* __restrict__ mu,
-                              double* rho_o, double* vx, double* vy, double* mu_o, size_t N,
-                              size_t plane) {
+                              const float* __restrict__ Fy, double* rho_o, double* vx, double* vy,
+                              size_t N, size_t plane) {
     for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
          n += (size_t)gridDim.x * blockDim.x) {
         double g[9];
@@ -179,8 +178,41 @@ __global__ void k_macro_mixed(const float* __restrict__ f, const float* __restri
         if (rho_o) rho_o[n] = r;
         if (vx) vx[n] = (jx + 0.5 * (double)Fx[n]) / r;
         if (vy) vy[n] = (jy + 0.5 * (double)Fy[n]) / r;
-        if (mu_o) mu_o[n] = (double)mu[n];
     }
+}
+
+// Chemical potential of the mixed path, pointwise after the line solves of rho:
+// mu-hat = k^2 mu0(rho) - kappa (d_xx + d_yy) rho (Eqs. 21, 33) in FP32, limited
+// from above while the time level t < cap_steps (Sec. 5.6; t read on the device
+// so that graph replays stay correct).  Written over d_xx rho, which nothing
+// needs afterwards.
+// FP32 constants of the chemical potential, converted on the host: FP64 -> FP32
+// conversions run on the FP64 pipe, which a per-thread conversion would make the
+// bottleneck of this pointwise kernel.
+struct MuConstF {
+    float T, a, b, R, k2, kappa, cap;
+    long long cap_steps;
+};
+
+__global__ void k_mu_mixed(const float* __restrict__ rh, float* dxx_mu,
+                           const float* __restrict__ dyy, size_t N, MuConstF p,
+                           DevState* __restrict__ st) {
+    const float T = p.T, a = p.a, b = p.b, R = p.R, k2 = p.k2, kappa = p.kappa, cap = p.cap;
+    const int64_t t = st->t;
+    const bool capped = t < p.cap_steps;
+    bool bad = false;
+    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
+         n += (size_t)gridDim.x * blockDim.x) {
+        const float r = rh[n];
+        const float eta = 0.25f * b * r;
+        const float om = 1.0f - eta;
+        const float mu0 = R * T * ((3.0f - eta) / (om * om * om) + logf(r) + 1.0f) - 2.0f * a * r;
+        float m = k2 * mu0 - kappa * (dxx_mu[n] + dyy[n]);
+        if (capped) m = fminf(m, cap);
+        bad |= !(r > 0.0f && eta < 1.0f && fabsf(m) < 1e30f);
+        dxx_mu[n] = m;
+    }
+    if (bad) raise_flag(st, FLAG_EOS, t);
 }
 
 constexpr int kDiagT = 256;
@@ -262,12 +294,19 @@ cudaError_t launch_rho_from_f_mixed(const float* f, float* rh, float* rl, int nx
 }
 
 cudaError_t launch_macro_mixed(const float* f, const float* rh, const float* rl,
-                               const float* Fx, const float* Fy, const float* mu, double* rho,
-                               double* vx, double* vy, double* mu_o, int nx, int ny,
-                               size_t plane, cudaStream_t s) {
+                               const float* Fx, const float* Fy, double* rho, double* vx,
+                               double* vy, int nx, int ny, size_t plane, cudaStream_t s) {
     const size_t N = (size_t)nx * ny;
-    k_macro_mixed<<<grid_for(N, 256), 256, 0, s>>>(f, rh, rl, Fx, Fy, mu, rho, vx, vy, mu_o, N,
-                                                   plane);
+    k_macro_mixed<<<grid_for(N, 256), 256, 0, s>>>(f, rh, rl, Fx, Fy, rho, vx, vy, N, plane);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mu_mixed(const float* rh, float* dxx_mu, const float* dyy, int nx, int ny,
+                            const PhysParams& p, DevState* st, cudaStream_t s) {
+    const size_t N = (size_t)nx * ny;
+    const MuConstF c{(float)p.T, (float)p.a, (float)p.b, (float)p.R, (float)p.k2,
+                     (float)p.kappa, (float)fmin(p.mu_cap, (double)FLT_MAX), p.cap_steps};
+    k_mu_mixed<<<grid_for(N, 256), 256, 0, s>>>(rh, dxx_mu, dyy, N, c, st);
     return cudaGetLastError();
 }
 
