@@ -9,15 +9,17 @@ double-float pair, double-float first derivatives of the density, FP32 for the
 rest).  Synthetic, seeded inputs.
 
 Also reported: `equilibrium`, the wall time from lbm_set_fields to
-Maxwell-accurate equilibrium of a flat interface (see equilibrium_time).
+Maxwell-accurate equilibrium of a flat interface (see equilibrium_time), and
+`large_grid`, the same drop at 4096 x 4096 (working set far above L2).
 
-One "step" is one time step: the five device passes (collide-stream, x- and
-y-line compact FD of rho with the chemical potential, x- and y-line compact FD
-of mu with the force).  Timing: W warm-up steps, then K steps, each bracketed by
-CUDA events recorded by the library on its stream around every pass; between
-steps a 512 MB buffer is written to flush the L2 (not timed).  value = nodes x K
-/ sum of step times.  e2e = the same metric through the public host API
-(lbm_set_fields from pinned host memory, K steps, lbm_fields back to host),
+One "step" is one time step: the device passes of the chosen precision (mixed:
+collide-stream, x|y compact FD of rho, pointwise chemical potential, x|y
+compact FD of mu with the force; fp64: collide-stream and four single-axis line
+passes).  Timing: W warm-up steps, then K steps, each bracketed by CUDA events
+recorded by the library on its stream around every pass; between steps a 512 MB
+buffer is written and another 512 MB read to flush the L2 (not timed).  value =
+nodes x K / sum of step times.  e2e = the same metric through the public host
+API (lbm_set_fields from pinned host memory, K steps, lbm_fields back to host),
 wall clock.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
@@ -206,6 +208,38 @@ def equilibrium_time(precision, max_steps=600_000):
                          "over 500 steps, checked every 500 steps"}
 
 
+def large_grid(precision, steps, warmup, size=4096):
+    """The bench drop scaled to size^2 (radius scaled with it): a working set far
+    above the 129 MB L2, so no flush is needed.  Per-pass CUDA-event times and the
+    step's algorithmic bytes against the measured copy bandwidth."""
+    import numpy as np
+    import paper_1906_09530_gb300 as P
+    from paper_1906_09530_gb300 import workloads as W
+    w = dict(WORKLOAD)
+    s = size / w["nx"]
+    w.update(nx=size, ny=size, radius=w["radius"] * s)
+    rg, rl = P.lbm_maxwell(w["T_r"])
+    sim = P.Simulation(w["nx"], w["ny"], w["T_r"], w["kappa"], w["tau"], w["k"],
+                       fd_order=w["order"], precision=precision)
+    sim.set_fields(W.drop(w["nx"], w["ny"], rg, rl, w["radius"], w["width"]))
+    sim.step(warmup)
+    names = PASS_NAMES[precision]
+    ms = np.array([sim.step_timed() for _ in range(steps)])[:, :len(names)]
+    sim.close()
+    N = w["nx"] * w["ny"]
+    step_ms = float(ms.sum(axis=1).mean())
+    pb = pass_bytes(precision)
+    peak, peak_kind = load_peaks()
+    gbs = sum(pb) * N / (step_ms / 1e3) / 1e9
+    return {"workload": workload_name(w, precision), "nodes": N, "steps": steps,
+            "mlups": N / (step_ms / 1e3) / 1e6, "ms_per_step": step_ms,
+            "passes_ms": {nm: round(float(ms[:, i].mean()), 5) for i, nm in enumerate(names)},
+            "step_roofline": {"alg_bytes_per_node": sum(pb), "achieved_GB/s": gbs,
+                              "peak": peak, "frac": gbs / peak,
+                              "peak_kind": f"{peak_kind} copy bandwidth"},
+            "l2": "working set above L2 (no flush)"}
+
+
 def run_reference(args, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -257,6 +291,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-equilibrium", action="store_true")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the 4096^2 line (default: measured after the main one)")
     args = ap.parse_args()
     w = dict(WORKLOAD)
     if args.size != 1024:
@@ -288,7 +324,11 @@ def main():
                        fd_order=w["order"], precision=args.precision)
     sim.set_fields(rho0)
     sim.step(args.warmup)
+    # L2 flush between timed steps: write 512 MB (evicts the simulation's data),
+    # then read another 512 MB so that L2 holds clean lines and the step does not
+    # pay for writing back the flush buffer's dirty lines
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    clean = torch.zeros(128 << 20, dtype=torch.float32, device="cuda")
 
     def barrier():
         torch.cuda.synchronize()
@@ -302,6 +342,7 @@ def main():
     pass_ms = np.zeros((args.steps, 5))
     for i in range(args.steps):
         flush.zero_()
+        clean.amax()
         pass_ms[i] = sim.step_timed()
     pass_ms = pass_ms[:, :len(names)]
     barrier()
@@ -371,7 +412,7 @@ def main():
             "dtype": "f32+f64" if args.precision == "mixed" else "f64",
             "data": "synthetic",
             "config": {"workload": workload_name(w, args.precision), "nodes": N,
-                       "l2": "512 MB write between timed steps (L2 flushed)",
+                       "l2": "512 MB write + 512 MB read between timed steps (L2 flushed, left clean)",
                        "parallelism": f"replicas{world}" if world > 1 else "single"},
             "roofline": roofline,
             "step_roofline": {"alg_bytes_per_node": sum(pb), "achieved_GB/s": step_gbs,
@@ -381,6 +422,9 @@ def main():
             "passes": passes,
             "graph_back_to_back_mlups": graph_mlups,
             "e2e": e2e, "gpu_launches": len(names) * args.steps, "clocks": clk}
+    if not args.no_large and args.size < 4096:
+        line["large_grid"] = large_grid(args.precision, min(args.steps, 100),
+                                        max(args.warmup, 3))
     if rank == 0 and not args.no_equilibrium:
         line["equilibrium"] = equilibrium_time(args.precision)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
