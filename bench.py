@@ -9,8 +9,10 @@ double-float pair, double-float first derivatives of the density, FP32 for the
 rest).  Synthetic, seeded inputs.
 
 Also reported: `equilibrium`, the wall time from lbm_set_fields to
-Maxwell-accurate equilibrium of a flat interface (see equilibrium_time), and
-`large_grid`, the same drop at 4096 x 4096 (working set far above L2).
+Maxwell-accurate equilibrium of a flat interface (see equilibrium_time);
+`large_grid`, the same drop at 4096 x 4096 (working set far above L2); and
+`batch`, 256 independent instances of uneven sizes and temperatures advanced
+by one launch per pass (see batch_config).
 
 One "step" is one time step: the device passes of the chosen precision (mixed:
 collide-stream, x|y compact FD of rho, pointwise chemical potential, x|y
@@ -240,6 +242,72 @@ def large_grid(precision, steps, warmup, size=4096):
             "l2": "working set above L2 (no flush)"}
 
 
+def batch_config(steps, warmup, n=256):
+    """The batched path on many independent instances (uneven sides 64-512, T_r
+    log-spaced 0.3-0.9, drops and flat interfaces; workloads.batch_instances):
+    one launch per pass for all of them, strip heights autotuned.  Compared with
+    the same instances stepped one after another as lone contexts (each with its
+    own two-step CUDA graph)."""
+    import numpy as np
+    import torch
+    import paper_1906_09530_gb300 as P
+    from paper_1906_09530_gb300 import workloads as W
+    specs = W.batch_instances(n)
+    keys = ("nx", "ny", "T_r", "k", "kappa", "tau")
+    b = P.Batch([{k: d[k] for k in keys} for d in specs])
+    fields = []
+    for i, d in enumerate(specs):
+        fields.append(W.batch_field(d, *P.lbm_maxwell(d["T_r"])))
+        b.set_fields(i, fields[-1])
+    b.autotune(3)
+    b.step(warmup)
+    ms = np.array([b.step_timed() for _ in range(steps)])
+    N = sum(d["nx"] * d["ny"] for d in specs)
+    step_ms = float(ms.sum(axis=1).mean())
+    # graph replay of the whole batch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kb = max(2, steps // 2 * 2)
+    torch.cuda.synchronize()
+    e0.record()
+    b.step(kb)
+    e1.record()
+    torch.cuda.synchronize()
+    graph_ms = e0.elapsed_time(e1) / kb
+    b.close()
+    # the same instances as lone contexts, one after another
+    sims = []
+    for d, r in zip(specs, fields):
+        s = P.Simulation(d["nx"], d["ny"], d["T_r"], d["kappa"], d["tau"], d["k"], fd_order=6,
+                         precision="mixed")
+        s.set_fields(r)
+        s.step(2)
+        sims.append(s)
+    torch.cuda.synchronize()
+    e0.record()
+    for s in sims:
+        s.step_async(2)
+    e1.record()
+    torch.cuda.synchronize()
+    lone_ms = e0.elapsed_time(e1) / 2
+    for s in sims:
+        s.check()
+        s.close()
+    pb = sum(pass_bytes("mixed"))
+    peak, peak_kind = load_peaks()
+    return {"workload": f"batch-{n}-instances-sides64-512-Tr0.3-0.9-mixed", "instances": n,
+            "nodes": N, "steps": steps,
+            "mlups": N / (step_ms / 1e3) / 1e6,
+            "graph_mlups": N / (graph_ms / 1e3) / 1e6,
+            "lone_sequential_mlups": N / (lone_ms / 1e3) / 1e6,
+            "passes_ms": {nm: round(float(ms[:, i].mean()), 5)
+                          for i, nm in enumerate(PASS_NAMES["mixed"])},
+            "step_roofline": {"alg_bytes_per_node": pb,
+                              "frac": pb * N / (step_ms / 1e3) / 1e9 / peak,
+                              "peak": peak, "peak_kind": f"{peak_kind} copy bandwidth"},
+            "launches_per_step": 4,
+            "l2": "working set above L2 (no flush)"}
+
+
 def run_reference(args, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -291,6 +359,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-equilibrium", action="store_true")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batched-instances line")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the 4096^2 line (default: measured after the main one)")
     args = ap.parse_args()
@@ -425,6 +495,8 @@ def main():
     if not args.no_large and args.size < 4096:
         line["large_grid"] = large_grid(args.precision, min(args.steps, 100),
                                         max(args.warmup, 3))
+    if not args.no_batch and args.precision == "mixed":
+        line["batch"] = batch_config(min(args.steps, 50), max(args.warmup // 10, 3))
     if rank == 0 and not args.no_equilibrium:
         line["equilibrium"] = equilibrium_time(args.precision)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -202,6 +202,96 @@ int64_t lbm_failed_step(const lbm_ctx *ctx);
 /* Host wait limit, in seconds, for lbm_step / lbm_check / copies (default 600). */
 lbm_status lbm_set_timeout(lbm_ctx *ctx, double seconds);
 
+/* ---- Batches: many independent instances advanced together -------------
+ *
+ * A batch holds n periodic instances of the MIXED path, each with its own grid,
+ * T_r, kappa-hat, tau, k and upper limit, and one EOS and one fd_order.  Every
+ * time step runs the four passes of the mixed path once for the whole batch
+ * (one launch per pass, blocks mapped to instances), two steps per CUDA graph,
+ * so small instances do not each pay for their own launches.  Within one
+ * instance the arithmetic is that of a single lbm_ctx with the same arguments:
+ * a batch member and a lone context give bit-identical results.
+ *
+ * Workspace: one device buffer owned by the caller (256-byte aligned,
+ * lbm_batch_workspace_bytes long): the instances' populations and fields, their
+ * device state blocks, the per-instance argument tables and block maps.  It must
+ * outlive the batch.  Host arrays are [ny][nx] FP64 of the instance's own grid.
+ */
+typedef struct lbm_batch lbm_batch; /* opaque, owned by the library */
+
+typedef struct {
+    lbm_grid grid;         /* nx, ny >= 8, periodic in both directions */
+    double T_r;            /* T / T_c in (0, 1) */
+    double kappa;          /* kappa-hat > 0 (Eq. 33, mesh space) */
+    double tau;            /* relaxation time > 0.5 (Eq. 1) */
+    double mesh_coeff;     /* k in (0, 1] (Eq. 25) */
+    double mu_max;         /* upper limit, momentum-space units (Sec. 5.6); +INFINITY: off */
+    int64_t mu_cap_steps;  /* the limit acts while the instance's time level < this */
+} lbm_instance;
+
+/* Bytes of device workspace for the batch (0 if an argument is invalid).
+ * opts->prec must be LBM_PREC_MIXED; opts->mu_max / mu_cap_steps are unused
+ * (each instance carries its own). */
+size_t lbm_batch_workspace_bytes(const lbm_instance *inst, int32_t n, const lbm_opts *opts);
+
+/* Create a batch of n >= 1 instances on the current CUDA device.  LBM_EINVAL for
+ * an out-of-range instance, LBM_ENOTIMPL for walls, another EOS or FP64, and
+ * LBM_ENOMEM if ws_bytes is too small.  Copies the argument tables to the
+ * workspace and returns when they are there. */
+lbm_status lbm_batch_init(lbm_batch **out, const lbm_instance *inst, int32_t n,
+                          const lbm_eos *eos, const lbm_opts *opts, void *d_workspace,
+                          size_t ws_bytes, void *cuda_stream);
+
+/* Initial state of instance i: f = f^eq(rho, u) with u = 0 where ux / uy are NULL;
+ * its force is computed at once and its time level set to 0.  Every instance
+ * must be set before the first step.  Returns when done; LBM_EUNSTABLE if the
+ * input itself is flagged (instance i stays unset). */
+lbm_status lbm_batch_set_fields(lbm_batch *b, int32_t i, const double *h_rho,
+                                const double *h_ux, const double *h_uy);
+
+/* Advance every instance by n >= 0 time steps and check the device error flags.
+ * LBM_EUNSTABLE: an instance flagged rho <= 0, a non-finite value or the EOS
+ * pole (see lbm_batch_failed); that instance's state is undefined and it must be
+ * set again before the next step, the others are valid.  LBM_EINVAL if any
+ * instance has not been set. */
+lbm_status lbm_batch_step(lbm_batch *b, int64_t n);
+
+/* One step with CUDA events around each pass; pass_ms[0..3] receive the times
+ * of collide-stream, the x|y lines of rho, mu-hat and the x|y lines of mu-hat
+ * with the force, each over the whole batch (milliseconds). */
+lbm_status lbm_batch_step_timed(lbm_batch *b, float *pass_ms);
+
+/* Outputs of instance i as in lbm_fields (any pointer may be NULL). */
+lbm_status lbm_batch_fields(lbm_batch *b, int32_t i, double *h_rho, double *h_vx,
+                            double *h_vy, double *h_mu);
+
+/* Per-instance diagnostics into host arrays of n doubles (any may be NULL):
+ * mass, max |v|, min rho, max rho. */
+lbm_status lbm_batch_diag(lbm_batch *b, double *mass, double *max_v, double *rho_min,
+                          double *rho_max);
+
+/* Time the collide-stream pass of one instance of each distinct grid size for
+ * each strip height the kernel supports (reps launches each, CUDA events), keep
+ * the fastest for every instance of that size, and rebuild the batch's tables.
+ * The simulation state is left as it was.  Returns when done. */
+lbm_status lbm_batch_autotune(lbm_batch *b, int32_t reps);
+
+/* The strip height in use for instance i (rows of the collide-stream warps). */
+int32_t lbm_batch_tile_rows(const lbm_batch *b, int32_t i);
+
+/* Time level of instance i (-1 if out of range). */
+int64_t lbm_batch_time(const lbm_batch *b, int32_t i);
+
+/* After LBM_EUNSTABLE: the first flagged instance (smallest flagged time level,
+ * then smallest index) and its flagged time level; -1 / -1 if none. */
+lbm_status lbm_batch_failed(const lbm_batch *b, int32_t *inst, int64_t *step);
+
+/* Host wait limit, in seconds (default 600). */
+lbm_status lbm_batch_set_timeout(lbm_batch *b, double seconds);
+
+/* Release the batch (not the workspace or the stream). */
+void lbm_batch_free(lbm_batch *b);
+
 const char *lbm_strerror(lbm_status s);
 
 /* Release the context (not the workspace or the stream, which the caller owns). */

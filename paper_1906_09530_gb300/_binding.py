@@ -33,6 +33,12 @@ class LbmOpts(C.Structure):
                 ("mu_cap_steps", C.c_int64)]
 
 
+class LbmInstance(C.Structure):
+    _fields_ = [("grid", LbmGrid), ("T_r", C.c_double), ("kappa", C.c_double),
+                ("tau", C.c_double), ("mesh_coeff", C.c_double), ("mu_max", C.c_double),
+                ("mu_cap_steps", C.c_int64)]
+
+
 class LbmError(RuntimeError):
     def __init__(self, status, what):
         self.status = status
@@ -77,6 +83,22 @@ def lib():
             "lbm_time": (C.c_int64, [_vp]),
             "lbm_failed_step": (C.c_int64, [_vp]),
             "lbm_set_timeout": (C.c_int, [_vp, C.c_double]),
+            "lbm_batch_workspace_bytes": (C.c_size_t, [C.POINTER(LbmInstance), _i32,
+                                                        C.POINTER(LbmOpts)]),
+            "lbm_batch_init": (C.c_int, [C.POINTER(_vp), C.POINTER(LbmInstance), _i32,
+                                         C.POINTER(LbmEos), C.POINTER(LbmOpts), _vp,
+                                         C.c_size_t, _vp]),
+            "lbm_batch_set_fields": (C.c_int, [_vp, _i32, _vp, _vp, _vp]),
+            "lbm_batch_step": (C.c_int, [_vp, _i64]),
+            "lbm_batch_step_timed": (C.c_int, [_vp, C.POINTER(C.c_float)]),
+            "lbm_batch_fields": (C.c_int, [_vp, _i32, _vp, _vp, _vp, _vp]),
+            "lbm_batch_diag": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
+            "lbm_batch_autotune": (C.c_int, [_vp, _i32]),
+            "lbm_batch_tile_rows": (_i32, [_vp, _i32]),
+            "lbm_batch_time": (C.c_int64, [_vp, _i32]),
+            "lbm_batch_failed": (C.c_int, [_vp, C.POINTER(_i32), C.POINTER(C.c_int64)]),
+            "lbm_batch_set_timeout": (C.c_int, [_vp, C.c_double]),
+            "lbm_batch_free": (None, [_vp]),
             "lbm_strerror": (C.c_char_p, [C.c_int]),
             "lbm_free": (None, [_vp]),
         }
@@ -273,6 +295,100 @@ class Simulation:
     def close(self):
         if getattr(self, "ctx", None):
             lib().lbm_free(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many independent periodic instances of the mixed path advanced together
+    (lbm_batch_* of the C ABI): one launch per pass for the whole batch.
+
+    `instances` is a sequence of dicts with keys nx, ny, T_r, and optionally
+    kappa (0.1), tau (1.0), k (0.5), mu_max (inf), mu_cap_steps (0).
+    """
+
+    def __init__(self, instances, fd_order=6, eos=None, device=None, stream=None):
+        import torch
+        self.n = len(instances)
+        arr = (LbmInstance * self.n)()
+        self.shapes = []
+        for i, d in enumerate(instances):
+            arr[i] = LbmInstance(LbmGrid(d["nx"], d["ny"], 1, 1), d["T_r"],
+                                 d.get("kappa", 0.1), d.get("tau", 1.0), d.get("k", 0.5),
+                                 d.get("mu_max", math.inf), d.get("mu_cap_steps", 0))
+            self.shapes.append((d["ny"], d["nx"]))
+        self._inst = arr
+        self.opts = LbmOpts(LBM_PREC_MIXED, fd_order, math.inf, 0)
+        self.eos = eos or cs_eos()
+        nbytes = lib().lbm_batch_workspace_bytes(arr, self.n, C.byref(self.opts))
+        if nbytes == 0:
+            raise LbmError(LBM_EINVAL, "lbm_batch_workspace_bytes")
+        self.device = torch.device(device if device is not None else "cuda")
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream()
+            self.ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            self.ctx = C.c_void_p()
+            _check(lib().lbm_batch_init(C.byref(self.ctx), arr, self.n, C.byref(self.eos),
+                                        C.byref(self.opts), self.ws.data_ptr(), nbytes,
+                                        self.stream.cuda_stream), "lbm_batch_init")
+
+    def set_fields(self, i, rho, ux=None, uy=None):
+        ny, nx = self.shapes[i]
+        arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+                for a in (rho, ux, uy)]
+        for a in arrs:
+            if a is not None and a.size != nx * ny:
+                raise ValueError("field size does not match instance grid")
+        _check(lib().lbm_batch_set_fields(self.ctx, i, *[_hptr(a) for a in arrs]),
+               "lbm_batch_set_fields")
+
+    def step(self, n=1):
+        _check(lib().lbm_batch_step(self.ctx, n), "lbm_batch_step")
+
+    def step_timed(self):
+        """One step of the whole batch; returns the 4 pass times in ms."""
+        ms = (C.c_float * 4)()
+        _check(lib().lbm_batch_step_timed(self.ctx, ms), "lbm_batch_step_timed")
+        return list(ms)
+
+    def fields(self, i):
+        ny, nx = self.shapes[i]
+        out = [np.empty((ny, nx)) for _ in range(4)]
+        _check(lib().lbm_batch_fields(self.ctx, i, *[_hptr(a) for a in out]),
+               "lbm_batch_fields")
+        return tuple(out)
+
+    def diag(self):
+        """Arrays (mass, max|v|, rho_min, rho_max), one entry per instance."""
+        out = [np.empty(self.n) for _ in range(4)]
+        _check(lib().lbm_batch_diag(self.ctx, *[_hptr(a) for a in out]), "lbm_batch_diag")
+        return tuple(out)
+
+    def autotune(self, reps=5):
+        _check(lib().lbm_batch_autotune(self.ctx, reps), "lbm_batch_autotune")
+
+    def tile_rows(self, i):
+        return lib().lbm_batch_tile_rows(self.ctx, i)
+
+    def time(self, i):
+        return lib().lbm_batch_time(self.ctx, i)
+
+    def failed(self):
+        i, t = _i32(), C.c_int64()
+        _check(lib().lbm_batch_failed(self.ctx, C.byref(i), C.byref(t)), "lbm_batch_failed")
+        return i.value, t.value
+
+    def set_timeout(self, seconds):
+        _check(lib().lbm_batch_set_timeout(self.ctx, seconds), "lbm_batch_set_timeout")
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lib().lbm_batch_free(self.ctx)
             self.ctx = None
 
     def __del__(self):

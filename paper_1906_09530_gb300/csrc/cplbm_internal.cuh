@@ -81,6 +81,78 @@ cudaError_t launch_diag_mixed(const float* f, const float* rh, const float* rl, 
                               const float* Fy, int nx, int ny, size_t plane, double* partials,
                               int nparts, DevState* st, cudaStream_t s);
 
+// ---- batched mixed path: per-instance argument blocks -----------------------
+// A batch runs many independent instances (each its own grid, temperature,
+// tau, k, kappa and state block) through the same four passes, one launch per
+// pass for the whole batch.  Every launch reads, per block, the instance index
+// from a block map and that instance's argument block; inside an instance the
+// work is the single-instance kernel's, block for block.
+
+// Collide-stream arguments of one instance (mixed path).
+struct CsArgs {
+    const float* fin;
+    float* fout;
+    const float* Fx;
+    const float* Fy;
+    float* rh;
+    float* rl;
+    int nx, ny;
+    size_t plane;
+    float omega;
+    int nstrips, nseg, rows;  // warp strips of 30 columns x `rows` rows
+    DevState* st;
+};
+struct CsBatchInst {
+    CsArgs a;      // fin / fout are taken from f[] by the launch's `from`
+    float* f[2];
+    int blk0;      // first block of this instance in the launch
+};
+// FP32 constants of the chemical potential, converted on the host: FP64 -> FP32
+// conversions run on the FP64 pipe, which a per-thread conversion would make the
+// bottleneck of the pointwise kernel.
+struct MuConstF {
+    float T, a, b, R, k2, kappa, cap;
+    long long cap_steps;
+};
+constexpr int kMuBatchT = 256;  // threads (= nodes) per block of the batched mu-hat pass
+struct MuBatchInst {
+    const float* rh;
+    float* mu;  // holds d_xx rho on entry
+    const float* dyy;
+    size_t N;
+    MuConstF c;
+    DevState* st;
+    int blk0;
+};
+// Pointers and sizes of one instance's mixed fields, for the batched line passes.
+struct MixedLinesView {
+    const float* rh;
+    const float* rl;
+    float *dxr, *dyr, *dxx, *dyy;  // dxx holds mu-hat after the mu pass
+    float *Fx, *Fy;
+    int nx, ny;
+    DevState* st;
+};
+
+CsArgs cs_mixed_args(const float* fin, float* fout, const float* Fx, const float* Fy,
+                     float* rh, float* rl, int nx, int ny, size_t plane, double omega,
+                     DevState* st, int rows);  // rows <= 0: the default choice
+int cs_mixed_blocks(const CsArgs& a);
+cudaError_t launch_cs_mixed_args(const CsArgs& a, cudaStream_t s);
+cudaError_t launch_cs_mixed_batch(const CsBatchInst* d, const int* map, int nblocks, int from,
+                                  cudaStream_t s);
+MuConstF mu_mixed_const(const PhysParams& p);
+cudaError_t launch_mu_mixed_batch(const MuBatchInst* d, const int* map, int nblocks,
+                                  cudaStream_t s);
+// Line passes: descriptor size per instance, blocks per instance, descriptor
+// written to host memory (copied to the device by the caller), the launches.
+// `rho`: the x|y lines of the density (else of mu-hat with the force).
+size_t lines_batch_desc_bytes(bool rho);
+int lines_batch_blocks(int nx, int ny, int order, bool rho);
+void lines_batch_fill(bool rho, const MixedLinesView& v, int order, int blk0, void* host_dst);
+cudaError_t lines_batch_launch(bool rho, const void* d_desc, const int* map, int nblocks,
+                               int order, int bump, cudaStream_t s);
+
 // Warp-cooperative compact-FD line solves (kernels_lines.cu).  axis 0: lines
 // along x, 1: along y.  Passes 2-5 of the FP64 path and of the mixed path, and
 // the stand-alone derivatives.

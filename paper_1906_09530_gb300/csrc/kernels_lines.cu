@@ -31,10 +31,12 @@
 // everything else (see kernels_mixed.cu for why).
 #include <cfloat>
 #include <cmath>
+#include <cstring>
 #include <type_traits>
 
 #include "cplbm_internal.cuh"
 #include "df.cuh"
+#include "lattice.cuh"
 
 namespace cplbm {
 namespace {
@@ -530,6 +532,48 @@ __global__ void __launch_bounds__(kNL * 32, 3)
     }
 }
 
+// Batched x|y lines: block b belongs to instance map[b]; within the instance the
+// blocks are those of k_lines_xy for its grid.  Each instance bumps its own
+// time level.
+template <class InX, class EpiX, class InY, class EpiY>
+struct LinesXYInst {
+    InX inx;
+    EpiX ex;
+    InY iny;
+    EpiY ey;
+    LineGeo gx, gy;
+    int nbx;   // x-line blocks of this instance
+    int blk0;  // first block of this instance in the launch
+    DevState* st;
+};
+
+template <class P1, class P2, bool SIXTH, bool SECOND, class InX, class EpiX, class InY,
+          class EpiY>
+__global__ void __launch_bounds__(kNL * 32, 3)
+    k_lines_xy_batch(const LinesXYInst<InX, EpiX, InY, EpiY>* __restrict__ d,
+                     const int* __restrict__ map, LineConst<P1> k1, LineConst<PolF> k1f,
+                     LineConst<P2> k2, int bump) {
+    const LinesXYInst<InX, EpiX, InY, EpiY>& D = d[map[blockIdx.x]];
+    DevState* st = D.st;
+    const int local = (int)blockIdx.x - D.blk0;
+    if (bump && local == 0 && threadIdx.x == 0) st->t += 1;
+    if (local < D.nbx) {
+        InX in = D.inx;
+        EpiX epi = D.ex;
+        const LineGeo g = D.gx;
+        epi.init(st);
+        in.init(st);
+        lines_body<0, P1, P2, SIXTH, SECOND>(in, g, k1, k1f, k2, epi, st, local);
+    } else {
+        InY in = D.iny;
+        EpiY epi = D.ey;
+        const LineGeo g = D.gy;
+        epi.init(st);
+        in.init(st);
+        lines_body<1, P1, P2, SIXTH, SECOND>(in, g, k1, k1f, k2, epi, st, local - D.nbx);
+    }
+}
+
 // ---- epilogues: return true when a value is bad (flags the run) ----
 template <class O, class V2>
 struct EpiStore {
@@ -589,7 +633,8 @@ struct EpiForce {
     __device__ __forceinline__ void init(const DevState*) {}
     __device__ __forceinline__ Ops fetch(size_t o) const { return Ops{__ldg(rho + o), __ldg(dr + o)}; }
     __device__ __forceinline__ bool operator()(size_t o, O dmu, O, const Ops& op) {
-        F[o] = -(O)op.r * dmu + op.d * (O)(1.0 / 3.0);
+        // explicit rounding: the epilogue is inlined in several kernels
+        F[o] = rn_fma(-(O)op.r, dmu, rn_mul(op.d, (O)(1.0 / 3.0)));
         return false;
     }
 };
@@ -732,6 +777,32 @@ cudaError_t launch_lines(In in, int nx, int ny, int axis, int order, double eps1
 // rounding levels the recursions are cut at
 constexpr double kEpsD = 1e-17, kEpsDF = 1e-15, kEpsF = 1e-8;
 
+// ---- batched mixed line passes ----
+using RhoInst = LinesXYInst<InDF, EpiStore<float, float>, InDF, EpiStore<float, float>>;
+using ForceInst = LinesXYInst<InF, EpiForce<float, float>, InF, EpiForce<float, float>>;
+
+int halo_of(bool rho, int order) {
+    return rho ? halo(order, kEpsDF, true, kEpsF) : halo(order, kEpsF, false, kEpsF);
+}
+
+template <class P1, class P2, bool SIXTH, bool SECOND, class Inst>
+cudaError_t launch_batch_t(const Inst* d, const int* map, int nblocks, int order, int bump,
+                           cudaStream_t s) {
+    auto kern = k_lines_xy_batch<P1, P2, SIXTH, SECOND, decltype(Inst::inx), decltype(Inst::ex),
+                                 decltype(Inst::iny), decltype(Inst::ey)>;
+    const size_t smem = smem_bytes<P1, P2, SECOND>();
+    static bool attr = false;  // one flag per kernel instantiation
+    if (!attr) {
+        cudaError_t e =
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    kern<<<nblocks, kNL * 32, smem, s>>>(d, map, make_const<P1>(order), make_const<PolF>(order),
+                                         make_const<P2>(order), bump);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 // ---- FP64 path ----
@@ -783,6 +854,44 @@ cudaError_t lines_mixed_plain(const float* uh, const float* ul, float* d1, float
                                                EpiStore<float, float>{d1, d2}, nullptr, 0, s);
     return launch_lines<PolDF, PolF, false>(InDF{uh, ul}, nx, ny, axis, order, kEpsDF, kEpsF,
                                             EpiStore<float, float>{d1, nullptr}, nullptr, 0, s);
+}
+
+// ---- batched mixed path ----
+size_t lines_batch_desc_bytes(bool rho) { return rho ? sizeof(RhoInst) : sizeof(ForceInst); }
+
+int lines_batch_blocks(int nx, int ny, int order, bool rho) {
+    const int H = halo_of(rho, order);
+    const LineGeo gx = make_geo(nx, ny, 0, H), gy = make_geo(nx, ny, 1, H);
+    return gx.ngroups * gx.nwin + gy.ngroups * gy.nwin;
+}
+
+void lines_batch_fill(bool rho, const MixedLinesView& v, int order, int blk0, void* host_dst) {
+    const int H = halo_of(rho, order);
+    const LineGeo gx = make_geo(v.nx, v.ny, 0, H), gy = make_geo(v.nx, v.ny, 1, H);
+    if (rho) {
+        RhoInst d{InDF{v.rh, v.rl}, EpiStore<float, float>{v.dxr, v.dxx},
+                  InDF{v.rh, v.rl}, EpiStore<float, float>{v.dyr, v.dyy},
+                  gx, gy, gx.ngroups * gx.nwin, blk0, v.st};
+        std::memcpy(host_dst, &d, sizeof(d));
+    } else {
+        ForceInst d{InF{v.dxx}, EpiForce<float, float>{v.Fx, v.rh, v.dxr},
+                    InF{v.dxx}, EpiForce<float, float>{v.Fy, v.rh, v.dyr},
+                    gx, gy, gx.ngroups * gx.nwin, blk0, v.st};
+        std::memcpy(host_dst, &d, sizeof(d));
+    }
+}
+
+cudaError_t lines_batch_launch(bool rho, const void* d_desc, const int* map, int nblocks,
+                               int order, int bump, cudaStream_t s) {
+    if (nblocks <= 0) return cudaSuccess;
+    if (rho) {
+        const RhoInst* d = static_cast<const RhoInst*>(d_desc);
+        return order == 6 ? launch_batch_t<PolDF, PolF, true, true>(d, map, nblocks, order, bump, s)
+                          : launch_batch_t<PolDF, PolF, false, true>(d, map, nblocks, order, bump, s);
+    }
+    const ForceInst* d = static_cast<const ForceInst*>(d_desc);
+    return order == 6 ? launch_batch_t<PolF, PolF, true, false>(d, map, nblocks, order, 0, s)
+                      : launch_batch_t<PolF, PolF, false, false>(d, map, nblocks, order, 0, s);
 }
 
 }  // namespace cplbm

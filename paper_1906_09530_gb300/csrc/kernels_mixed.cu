@@ -57,22 +57,23 @@ __device__ __forceinline__ void raise_flag(DevState* st, unsigned bits, int64_t 
 // ---------------------------------------------------------------------------
 constexpr int kSwWarps = 4;  // warps per block
 
-__global__ void __launch_bounds__(kSwWarps * 32)
-    k_cs_mixed_sw(const float* __restrict__ fin, float* __restrict__ fout,
-                  const float* __restrict__ Fx, const float* __restrict__ Fy,
-                  float* __restrict__ rho_hi, float* __restrict__ rho_lo, int nx, int ny,
-                  size_t plane, float omega, int nstrips, int nseg, int rows,
-                  DevState* __restrict__ st) {
+__device__ __forceinline__ void cs_mixed_body(const CsArgs& a, int wid) {
+    const float* __restrict__ fin = a.fin;
+    float* __restrict__ fout = a.fout;
+    const float* __restrict__ Fx = a.Fx;
+    const float* __restrict__ Fy = a.Fy;
+    const int nx = a.nx, ny = a.ny;
+    const size_t plane = a.plane;
+    const float omega = a.omega;
     const int lane = threadIdx.x & 31;
-    const int wid = blockIdx.x * kSwWarps + (threadIdx.x >> 5);
-    if (wid >= nstrips * nseg) return;  // uniform per warp
-    const int strip = wid % nstrips, seg = wid / nstrips;
+    if (wid >= a.nstrips * a.nseg) return;  // uniform per warp
+    const int strip = wid % a.nstrips, seg = wid / a.nstrips;
     const int x0 = strip * 30;
     const int gx = wrap_near(x0 - 1 + lane, nx);
     const int xo = x0 + lane - 1;
     const bool writer = lane >= 1 && lane <= 30 && xo < nx;
-    const int y0 = seg * rows;
-    const int y1 = min(y0 + rows, ny);
+    const int y0 = seg * a.rows;
+    const int y1 = min(y0 + a.rows, ny);
     bool ok = true;
 
     float raw[11];
@@ -113,8 +114,8 @@ __global__ void __launch_bounds__(kSwWarps * 32)
 #pragma unroll
             for (int i = 0; i < 9; ++i) fout[i * plane + n] = g[i];
             const df r = sum9_exact(g);
-            rho_hi[n] = r.hi;
-            rho_lo[n] = r.lo;
+            a.rh[n] = r.hi;
+            a.rl[n] = r.lo;
         }
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
@@ -122,7 +123,22 @@ __global__ void __launch_bounds__(kSwWarps * 32)
             B[i] = C[i];
         }
     }
-    if (!ok) raise_flag(st, FLAG_RHO, st->t);
+    if (!ok) raise_flag(a.st, FLAG_RHO, a.st->t);
+}
+
+__global__ void __launch_bounds__(kSwWarps * 32) k_cs_mixed_sw(CsArgs a) {
+    cs_mixed_body(a, blockIdx.x * kSwWarps + (threadIdx.x >> 5));
+}
+
+// Batched: block b belongs to instance map[b]; its warps continue that
+// instance's warp numbering from the instance's first block.
+__global__ void __launch_bounds__(kSwWarps * 32)
+    k_cs_mixed_batch(const CsBatchInst* __restrict__ d, const int* __restrict__ map, int from) {
+    const CsBatchInst& D = d[map[blockIdx.x]];
+    CsArgs a = D.a;
+    a.fin = D.f[from];
+    a.fout = D.f[1 - from];
+    cs_mixed_body(a, ((int)blockIdx.x - D.blk0) * kSwWarps + (threadIdx.x >> 5));
 }
 
 // f = f^eq(rho, u) in FP64, stored as FP32; rho = DF sum of the stored floats.
@@ -186,33 +202,45 @@ __global__ void k_macro_mixed(const float* __restrict__ f, const float* __restri
 // from above while the time level t < cap_steps (Sec. 5.6; t read on the device
 // so that graph replays stay correct).  Written over d_xx rho, which nothing
 // needs afterwards.
-// FP32 constants of the chemical potential, converted on the host: FP64 -> FP32
-// conversions run on the FP64 pipe, which a per-thread conversion would make the
-// bottleneck of this pointwise kernel.
-struct MuConstF {
-    float T, a, b, R, k2, kappa, cap;
-    long long cap_steps;
-};
-
-__global__ void k_mu_mixed(const float* __restrict__ rh, float* dxx_mu,
-                           const float* __restrict__ dyy, size_t N, MuConstF p,
-                           DevState* __restrict__ st) {
+__device__ __forceinline__ void mu_mixed_body(const float* __restrict__ rh, float* dxx_mu,
+                                              const float* __restrict__ dyy, size_t N,
+                                              const MuConstF& p, DevState* __restrict__ st,
+                                              size_t n0, size_t stride) {
     const float T = p.T, a = p.a, b = p.b, R = p.R, k2 = p.k2, kappa = p.kappa, cap = p.cap;
     const int64_t t = st->t;
     const bool capped = t < p.cap_steps;
     bool bad = false;
-    for (size_t n = blockIdx.x * (size_t)blockDim.x + threadIdx.x; n < N;
-         n += (size_t)gridDim.x * blockDim.x) {
+    for (size_t n = n0; n < N; n += stride) {
         const float r = rh[n];
-        const float eta = 0.25f * b * r;
-        const float om = 1.0f - eta;
-        const float mu0 = R * T * ((3.0f - eta) / (om * om * om) + logf(r) + 1.0f) - 2.0f * a * r;
-        float m = k2 * mu0 - kappa * (dxx_mu[n] + dyy[n]);
+        const float eta = rn_mul(rn_mul(0.25f, b), r);
+        const float om = rn_sub(1.0f, eta);
+        // explicit rounding: the body is inlined in the lone and batched kernels
+        const float rt = rn_mul(R, T);
+        const float cs = rn_add(rn_add(rn_div(rn_sub(3.0f, eta), rn_mul(rn_mul(om, om), om)),
+                                       logf(r)),
+                                1.0f);
+        const float mu0 = rn_fma(rt, cs, -rn_mul(rn_mul(2.0f, a), r));
+        float m = rn_fma(k2, mu0, -rn_mul(kappa, rn_add(dxx_mu[n], dyy[n])));
         if (capped) m = fminf(m, cap);
         bad |= !(r > 0.0f && eta < 1.0f && fabsf(m) < 1e30f);
         dxx_mu[n] = m;
     }
     if (bad) raise_flag(st, FLAG_EOS, t);
+}
+
+__global__ void k_mu_mixed(const float* __restrict__ rh, float* dxx_mu,
+                           const float* __restrict__ dyy, size_t N, MuConstF p,
+                           DevState* __restrict__ st) {
+    mu_mixed_body(rh, dxx_mu, dyy, N, p, st, blockIdx.x * (size_t)blockDim.x + threadIdx.x,
+                  (size_t)gridDim.x * blockDim.x);
+}
+
+// Batched: one node per thread, blocks of kMuBatchT threads mapped to instances.
+__global__ void __launch_bounds__(kMuBatchT)
+    k_mu_mixed_batch(const MuBatchInst* __restrict__ d, const int* __restrict__ map) {
+    const MuBatchInst& D = d[map[blockIdx.x]];
+    const size_t n = ((size_t)blockIdx.x - D.blk0) * kMuBatchT + threadIdx.x;
+    mu_mixed_body(D.rh, D.mu, D.dyy, D.N, D.c, D.st, n, D.N);
 }
 
 constexpr int kDiagT = 256;
@@ -263,18 +291,42 @@ inline unsigned grid_for(size_t n, int threads) {
 
 }  // namespace
 
+CsArgs cs_mixed_args(const float* fin, float* fout, const float* Fx, const float* Fy,
+                     float* rh, float* rl, int nx, int ny, size_t plane, double omega,
+                     DevState* st, int rows) {
+    // rows per warp: 32 on large grids, fewer on small ones to keep >= ~4k warps
+    const int nstrips = (nx + 29) / 30;
+    if (rows <= 0) {
+        rows = 32;
+        while (rows > 8 && (long long)nstrips * ((ny + rows - 1) / rows) < 4096) rows /= 2;
+    }
+    CsArgs a{fin, fout, Fx, Fy, rh, rl, nx, ny, plane, (float)omega, nstrips,
+             (ny + rows - 1) / rows, rows, st};
+    return a;
+}
+
+int cs_mixed_blocks(const CsArgs& a) {
+    const long long warps = (long long)a.nstrips * a.nseg;
+    return (int)((warps + kSwWarps - 1) / kSwWarps);
+}
+
 cudaError_t launch_cs_mixed(const float* fin, float* fout, const float* Fx, const float* Fy,
                             float* rh, float* rl, int nx, int ny, size_t plane, double omega,
                             DevState* st, cudaStream_t s) {
-    // rows per warp: 32 on large grids, fewer on small ones to keep >= ~4k warps
-    const int nstrips = (nx + 29) / 30;
-    int rows = 32;
-    while (rows > 8 && (long long)nstrips * ((ny + rows - 1) / rows) < 4096) rows /= 2;
-    const int nseg = (ny + rows - 1) / rows;
-    const long long warps = (long long)nstrips * nseg;
-    const unsigned blocks = (unsigned)((warps + kSwWarps - 1) / kSwWarps);
-    k_cs_mixed_sw<<<blocks, kSwWarps * 32, 0, s>>>(fin, fout, Fx, Fy, rh, rl, nx, ny, plane,
-                                                   (float)omega, nstrips, nseg, rows, st);
+    const CsArgs a = cs_mixed_args(fin, fout, Fx, Fy, rh, rl, nx, ny, plane, omega, st, 0);
+    k_cs_mixed_sw<<<cs_mixed_blocks(a), kSwWarps * 32, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cs_mixed_args(const CsArgs& a, cudaStream_t s) {
+    k_cs_mixed_sw<<<cs_mixed_blocks(a), kSwWarps * 32, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cs_mixed_batch(const CsBatchInst* d, const int* map, int nblocks, int from,
+                                  cudaStream_t s) {
+    if (nblocks <= 0) return cudaSuccess;
+    k_cs_mixed_batch<<<nblocks, kSwWarps * 32, 0, s>>>(d, map, from);
     return cudaGetLastError();
 }
 
@@ -301,12 +353,22 @@ cudaError_t launch_macro_mixed(const float* f, const float* rh, const float* rl,
     return cudaGetLastError();
 }
 
+MuConstF mu_mixed_const(const PhysParams& p) {
+    return MuConstF{(float)p.T, (float)p.a, (float)p.b, (float)p.R, (float)p.k2,
+                    (float)p.kappa, (float)fmin(p.mu_cap, (double)FLT_MAX), p.cap_steps};
+}
+
 cudaError_t launch_mu_mixed(const float* rh, float* dxx_mu, const float* dyy, int nx, int ny,
                             const PhysParams& p, DevState* st, cudaStream_t s) {
     const size_t N = (size_t)nx * ny;
-    const MuConstF c{(float)p.T, (float)p.a, (float)p.b, (float)p.R, (float)p.k2,
-                     (float)p.kappa, (float)fmin(p.mu_cap, (double)FLT_MAX), p.cap_steps};
-    k_mu_mixed<<<grid_for(N, 256), 256, 0, s>>>(rh, dxx_mu, dyy, N, c, st);
+    k_mu_mixed<<<grid_for(N, 256), 256, 0, s>>>(rh, dxx_mu, dyy, N, mu_mixed_const(p), st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mu_mixed_batch(const MuBatchInst* d, const int* map, int nblocks,
+                                  cudaStream_t s) {
+    if (nblocks <= 0) return cudaSuccess;
+    k_mu_mixed_batch<<<nblocks, kMuBatchT, 0, s>>>(d, map);
     return cudaGetLastError();
 }
 

@@ -10,6 +10,8 @@ fed from here, so their inputs are bit-identical.
   * noise     multiplicative uniform noise rho <- rho (1 + eps), eps in [-A, A],
               drawn from splitmix64 of (seed, node index): a counter-based
               generator, so any node's value can be recomputed on its own.
+  * batch     a seeded set of many independent instances (uneven grid sides and
+              temperatures, drops and flat interfaces) for the batched path.
 """
 import numpy as np
 
@@ -61,3 +63,34 @@ def shear_wave(nx, ny, rho0, amplitude):
     y = np.arange(ny, dtype=np.float64)[:, None] * np.ones((1, nx))
     return (np.full((ny, nx), rho0), amplitude * np.sin(2 * np.pi * y / ny),
             np.zeros((ny, nx)))
+
+
+BATCH_SIDES = (64, 128, 256, 512)
+
+
+def batch_instances(n=256, seed=1234, t_lo=0.3, t_hi=0.9):
+    """n independent periodic instances: square grids with sides drawn uniformly
+    from BATCH_SIDES (splitmix64 of (seed, i)), T_r log-spaced from t_lo to t_hi,
+    each a drop of radius side/4 or a flat slab of thickness side/2 (again from
+    splitmix64).  k = 0.5 for T_r >= 0.45 and 0.3 below (k = 0.5 drops blow up at
+    T_r <= 0.4), kappa-hat = 0.1, tau = 1, tanh width 4/k."""
+    idx = np.arange(n, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        key = splitmix64(np.uint64(seed) * np.uint64(0x100000001B3) + idx)
+    sides = [BATCH_SIDES[int(v)] for v in (key >> np.uint64(40)) % np.uint64(len(BATCH_SIDES))]
+    kinds = ["drop" if int(v) else "flat" for v in (key >> np.uint64(20)) & np.uint64(1)]
+    trs = np.geomspace(t_lo, t_hi, n) if n > 1 else np.array([t_lo])
+    out = []
+    for i in range(n):
+        k = 0.5 if trs[i] >= 0.45 else 0.3
+        out.append(dict(nx=sides[i], ny=sides[i], T_r=float(trs[i]), k=k, kappa=0.1, tau=1.0,
+                        kind=kinds[i], width=4.0 / k))
+    return out
+
+
+def batch_field(spec, rho_g, rho_l):
+    """Initial density of one batch instance from its coexistence pair."""
+    n = spec["nx"]
+    if spec["kind"] == "drop":
+        return drop(spec["nx"], spec["ny"], rho_g, rho_l, 0.25 * n, spec["width"])
+    return flat(spec["nx"], spec["ny"], rho_g, rho_l, 0.5 * spec["ny"], spec["width"])
