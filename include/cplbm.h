@@ -55,10 +55,13 @@ enum { LBM_EOS_CS = 0 };
 
 /* Precision.  FP64: everything in double.  MIXED: populations and the
  * collide-stream pass in float; the density kept exactly as a double-float pair
- * (hi + lo floats) and its first compact-FD derivatives computed in double-float
- * arithmetic; second derivatives, chemical potential and force in float; all
- * reductions and outputs in double. */
-enum { LBM_PREC_FP64 = 0, LBM_PREC_MIXED = 1 };
+ * (hi + lo floats); its compact-FD derivatives in float when the Maxwell density
+ * ratio at T_r is below 1e4, else in double-float arithmetic wherever a line
+ * window spans more than a factor 32 of density (first derivatives, rounded once
+ * to float); second derivatives, chemical potential and force in float; all
+ * reductions and outputs in double.  MIXED_DF: as MIXED, with the double-float
+ * derivatives at every density ratio. */
+enum { LBM_PREC_FP64 = 0, LBM_PREC_MIXED = 1, LBM_PREC_MIXED_DF = 2 };
 
 typedef struct {
     int32_t nx, ny;                 /* lattice size, each >= 8 */
@@ -230,7 +233,8 @@ typedef struct {
 } lbm_instance;
 
 /* Bytes of device workspace for the batch (0 if an argument is invalid).
- * opts->prec must be LBM_PREC_MIXED; opts->mu_max / mu_cap_steps are unused
+ * opts->prec must be LBM_PREC_MIXED or LBM_PREC_MIXED_DF (chosen per instance by
+ * its density ratio, as for a lone context); opts->mu_max / mu_cap_steps are unused
  * (each instance carries its own). */
 size_t lbm_batch_workspace_bytes(const lbm_instance *inst, int32_t n, const lbm_opts *opts);
 

@@ -15,7 +15,8 @@ from . import _build
 
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ENOTIMPL = range(7)
 LBM_EOS_CS = 0
-LBM_PREC_FP64, LBM_PREC_MIXED = 0, 1
+LBM_PREC_FP64, LBM_PREC_MIXED, LBM_PREC_MIXED_DF = 0, 1, 2
+_PRECISIONS = {"fp64": LBM_PREC_FP64, "mixed": LBM_PREC_MIXED, "mixed_df": LBM_PREC_MIXED_DF}
 
 
 class LbmGrid(C.Structure):
@@ -205,7 +206,7 @@ class Simulation:
         import torch
         self.nx, self.ny = nx, ny
         self.device = torch.device(device if device is not None else "cuda")
-        prec = {"fp64": LBM_PREC_FP64, "mixed": LBM_PREC_MIXED}[precision]
+        prec = _PRECISIONS[precision]
         self.grid = LbmGrid(nx, ny, 1, 1)
         self.opts = LbmOpts(prec, fd_order, mu_max, mu_cap_steps)
         self.eos = eos or cs_eos()
@@ -310,9 +311,11 @@ class Batch:
 
     `instances` is a sequence of dicts with keys nx, ny, T_r, and optionally
     kappa (0.1), tau (1.0), k (0.5), mu_max (inf), mu_cap_steps (0).
+    `precision` is "mixed" or "mixed_df", as for Simulation.
     """
 
-    def __init__(self, instances, fd_order=6, eos=None, device=None, stream=None):
+    def __init__(self, instances, fd_order=6, precision="mixed", eos=None, device=None,
+                 stream=None):
         import torch
         self.n = len(instances)
         arr = (LbmInstance * self.n)()
@@ -323,7 +326,7 @@ class Batch:
                                  d.get("mu_max", math.inf), d.get("mu_cap_steps", 0))
             self.shapes.append((d["ny"], d["nx"]))
         self._inst = arr
-        self.opts = LbmOpts(LBM_PREC_MIXED, fd_order, math.inf, 0)
+        self.opts = LbmOpts(_PRECISIONS[precision], fd_order, math.inf, 0)
         self.eos = eos or cs_eos()
         nbytes = lib().lbm_batch_workspace_bytes(arr, self.n, C.byref(self.opts))
         if nbytes == 0:

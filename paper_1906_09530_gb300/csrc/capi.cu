@@ -31,6 +31,7 @@ struct lbm_ctx {
     int nx, ny;
     size_t N, plane;
     int prec, fd_order;
+    bool rho_df;  // mixed: density lines in double-float (else FP32)
     double T, Tc, rhoc, kappa, tau, k;
     double mu_max;
     int64_t mu_cap_steps;
@@ -71,7 +72,9 @@ struct Layout {
 
 bool grid_ok(const lbm_grid* g) { return g && g->nx >= 8 && g->ny >= 8; }
 bool opts_ok(const lbm_opts* o) {
-    return o && (o->prec == LBM_PREC_FP64 || o->prec == LBM_PREC_MIXED) &&
+    return o &&
+           (o->prec == LBM_PREC_FP64 || o->prec == LBM_PREC_MIXED ||
+            o->prec == LBM_PREC_MIXED_DF) &&
            (o->fd_order == 4 || o->fd_order == 6) && !std::isnan(o->mu_max);
 }
 
@@ -113,8 +116,12 @@ lbm_status enqueue_force(lbm_ctx* c, cudaStream_t s, int bump, cudaEvent_t* ev =
     auto mark = [&](int i) { return ev ? cudaEventRecord(ev[i], s) : cudaSuccess; };
     if (!is_fp64(c)) {
         // x|y lines of rho together, mu-hat pointwise, x|y lines of mu-hat + force
-        CK(lines_mixed_rho_xy(c->m_rh, c->m_rl, c->m_dxr, c->m_dxx, c->m_dyr, c->m_dyy, nx, ny,
-                              o, c->dst, bump, s));
+        if (c->rho_df)
+            CK(lines_mixed_rho_xy(c->m_rh, c->m_rl, c->m_dxr, c->m_dxx, c->m_dyr, c->m_dyy, nx,
+                                  ny, o, c->dst, bump, s));
+        else
+            CK(lines_mixed_rho_xy_f32(c->m_rh, c->m_dxr, c->m_dxx, c->m_dyr, c->m_dyy, nx, ny, o,
+                                      c->dst, bump, s));
         CK(mark(0));
         CK(launch_mu_mixed(c->m_rh, c->m_dxx, c->m_dyy, nx, ny, c->phys, c->dst, s));
         CK(mark(1));
@@ -289,6 +296,12 @@ lbm_status lbm_init(lbm_ctx** out, const lbm_grid* grid, const lbm_eos* eos, dou
     c->plane = L.plane;
     c->prec = opts->prec;
     c->fd_order = opts->fd_order;
+    c->rho_df = opts->prec == LBM_PREC_MIXED_DF;
+    if (opts->prec == LBM_PREC_MIXED) {
+        double rg, rl;
+        c->rho_df = cs_maxwell(eos->a, eos->b, eos->R, T_r * Tc, &rg, &rl) != 0 ||
+                    !(rl < kDfRatio * rg);
+    }
     c->Tc = Tc;
     c->rhoc = rc;
     c->T = T_r * Tc;

@@ -44,7 +44,8 @@ struct InstHost {
     double* partials;
     int64_t t;
     bool ready;
-    int rows;  // collide-stream strip height (0: the single-instance default)
+    bool rho_df;  // density lines in double-float (else FP32), as for a lone context
+    int rows;     // collide-stream strip height (0: the single-instance default)
 };
 
 struct Region {
@@ -71,18 +72,22 @@ int mu_blocks_for(size_t N) { return (int)((N + kMuBatchT - 1) / kMuBatchT); }
 // Offsets of the table region, sized for the largest block counts (the
 // smallest strip height) so that autotuning never needs more room.
 struct Tables {
-    size_t cs, mu, rho, force, state, map_cs, map_mu, map_rho, map_force, end;
-    int nb_cs, nb_mu, nb_rho, nb_force;  // current counts
+    size_t cs, mu, rho_df, rho_f32, force, state;
+    size_t map_cs, map_mu, map_rho_df, map_rho_f32, map_force, end;
+    int nb_cs, nb_mu, nb_rho_df, nb_rho_f32, nb_force;  // current counts
 };
 
 Tables table_layout(const lbm_instance* inst, int n, int order, size_t base) {
+    // each density map is sized for every instance in it (the double-float
+    // windows are the shorter ones, so their count bounds both kinds)
     long long cs_max = 0, mu = 0, rho = 0, force = 0;
     for (int i = 0; i < n; ++i) {
         const int nx = inst[i].grid.nx, ny = inst[i].grid.ny;
         cs_max += cs_blocks_for(nx, ny, kRowChoices[0]);
         mu += mu_blocks_for((size_t)nx * ny);
-        rho += lines_batch_blocks(nx, ny, order, true);
-        force += lines_batch_blocks(nx, ny, order, false);
+        rho += std::max(lines_batch_blocks(nx, ny, order, LineBatchKind::kRhoDF),
+                        lines_batch_blocks(nx, ny, order, LineBatchKind::kRhoF32));
+        force += lines_batch_blocks(nx, ny, order, LineBatchKind::kForce);
     }
     Tables t;
     size_t o = base;
@@ -93,15 +98,17 @@ Tables table_layout(const lbm_instance* inst, int n, int order, size_t base) {
     };
     t.cs = take(n * sizeof(CsBatchInst));
     t.mu = take(n * sizeof(MuBatchInst));
-    t.rho = take(n * lines_batch_desc_bytes(true));
-    t.force = take(n * lines_batch_desc_bytes(false));
+    t.rho_df = take(n * lines_batch_desc_bytes(LineBatchKind::kRhoDF));
+    t.rho_f32 = take(n * lines_batch_desc_bytes(LineBatchKind::kRhoF32));
+    t.force = take(n * lines_batch_desc_bytes(LineBatchKind::kForce));
     t.state = take(n * sizeof(DevState));
     t.map_cs = take(cs_max * sizeof(int));
     t.map_mu = take(mu * sizeof(int));
-    t.map_rho = take(rho * sizeof(int));
+    t.map_rho_df = take(rho * sizeof(int));
+    t.map_rho_f32 = take(rho * sizeof(int));
     t.map_force = take(force * sizeof(int));
     t.end = o;
-    t.nb_cs = t.nb_mu = t.nb_rho = t.nb_force = 0;
+    t.nb_cs = t.nb_mu = t.nb_rho_df = t.nb_rho_f32 = t.nb_force = 0;
     return t;
 }
 
@@ -170,11 +177,13 @@ MixedLinesView view_of(const lbm_batch* b, int i) {
 lbm_status upload_tables(lbm_batch* b) {
     Tables& t = b->tb;
     const int n = b->n;
+    const size_t bdf = lines_batch_desc_bytes(LineBatchKind::kRhoDF);
+    const size_t bf = lines_batch_desc_bytes(LineBatchKind::kRhoF32);
+    const size_t bfo = lines_batch_desc_bytes(LineBatchKind::kForce);
     std::vector<CsBatchInst> cs(n);
     std::vector<MuBatchInst> mu(n);
-    std::vector<unsigned char> rho(n * lines_batch_desc_bytes(true));
-    std::vector<unsigned char> force(n * lines_batch_desc_bytes(false));
-    std::vector<int> mcs, mmu, mrho, mforce;
+    std::vector<unsigned char> rdf(n * bdf), rf(n * bf), force(n * bfo);
+    std::vector<int> mcs, mmu, mrdf, mrf, mforce;
     for (int i : b->order_by_size) {
         const InstHost& h = b->inst[i];
         DevState* st = b->dst + i;
@@ -192,34 +201,40 @@ lbm_status upload_tables(lbm_batch* b) {
         mu[i] = m;
 
         const MixedLinesView v = view_of(b, i);
-        lines_batch_fill(true, v, b->order, (int)mrho.size(),
-                         rho.data() + i * lines_batch_desc_bytes(true));
-        mrho.insert(mrho.end(), lines_batch_blocks(h.nx, h.ny, b->order, true), i);
-        lines_batch_fill(false, v, b->order, (int)mforce.size(),
-                         force.data() + i * lines_batch_desc_bytes(false));
-        mforce.insert(mforce.end(), lines_batch_blocks(h.nx, h.ny, b->order, false), i);
+        const LineBatchKind rk = h.rho_df ? LineBatchKind::kRhoDF : LineBatchKind::kRhoF32;
+        std::vector<int>& mr = h.rho_df ? mrdf : mrf;
+        lines_batch_fill(rk, v, b->order, (int)mr.size(),
+                         h.rho_df ? rdf.data() + i * bdf : rf.data() + i * bf);
+        mr.insert(mr.end(), lines_batch_blocks(h.nx, h.ny, b->order, rk), i);
+        lines_batch_fill(LineBatchKind::kForce, v, b->order, (int)mforce.size(),
+                         force.data() + i * bfo);
+        mforce.insert(mforce.end(), lines_batch_blocks(h.nx, h.ny, b->order, LineBatchKind::kForce),
+                      i);
     }
     // the table region was sized for the largest counts
     const size_t cap_cs = (t.map_mu - t.map_cs) / sizeof(int);
     if (mcs.size() > cap_cs) return LBM_ENOMEM;
     t.nb_cs = (int)mcs.size();
     t.nb_mu = (int)mmu.size();
-    t.nb_rho = (int)mrho.size();
+    t.nb_rho_df = (int)mrdf.size();
+    t.nb_rho_f32 = (int)mrf.size();
     t.nb_force = (int)mforce.size();
     cudaStream_t s = b->stream;
     char* ws = b->ws;
-    CK(cudaMemcpyAsync(ws + t.cs, cs.data(), n * sizeof(CsBatchInst), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(ws + t.mu, mu.data(), n * sizeof(MuBatchInst), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(ws + t.rho, rho.data(), rho.size(), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(ws + t.force, force.data(), force.size(), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(ws + t.map_cs, mcs.data(), mcs.size() * sizeof(int),
-                       cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(ws + t.map_mu, mmu.data(), mmu.size() * sizeof(int),
-                       cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(ws + t.map_rho, mrho.data(), mrho.size() * sizeof(int),
-                       cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(ws + t.map_force, mforce.data(), mforce.size() * sizeof(int),
-                       cudaMemcpyHostToDevice, s));
+    auto put = [&](size_t off, const void* src, size_t bytes) {
+        return bytes ? cudaMemcpyAsync(ws + off, src, bytes, cudaMemcpyHostToDevice, s)
+                     : cudaSuccess;
+    };
+    CK(put(t.cs, cs.data(), n * sizeof(CsBatchInst)));
+    CK(put(t.mu, mu.data(), n * sizeof(MuBatchInst)));
+    CK(put(t.rho_df, rdf.data(), rdf.size()));
+    CK(put(t.rho_f32, rf.data(), rf.size()));
+    CK(put(t.force, force.data(), force.size()));
+    CK(put(t.map_cs, mcs.data(), mcs.size() * sizeof(int)));
+    CK(put(t.map_mu, mmu.data(), mmu.size() * sizeof(int)));
+    CK(put(t.map_rho_df, mrdf.data(), mrdf.size() * sizeof(int)));
+    CK(put(t.map_rho_f32, mrf.data(), mrf.size() * sizeof(int)));
+    CK(put(t.map_force, mforce.data(), mforce.size() * sizeof(int)));
     // the host vectors are pageable: the copies have completed when this returns
     return wait_stream(b);
 }
@@ -234,12 +249,16 @@ lbm_status enqueue_step(lbm_batch* b, cudaStream_t s, int from, cudaEvent_t* ev 
     auto mark = [&](int i) { return ev ? cudaEventRecord(ev[i], s) : cudaSuccess; };
     CK(launch_cs_mixed_batch(at<CsBatchInst>(b, t.cs), at<int>(b, t.map_cs), t.nb_cs, from, s));
     CK(mark(1));
-    CK(lines_batch_launch(true, b->ws + t.rho, at<int>(b, t.map_rho), t.nb_rho, b->order, 1, s));
+    // every instance is in exactly one of the two density launches
+    CK(lines_batch_launch(LineBatchKind::kRhoF32, b->ws + t.rho_f32, at<int>(b, t.map_rho_f32),
+                          t.nb_rho_f32, b->order, 1, s));
+    CK(lines_batch_launch(LineBatchKind::kRhoDF, b->ws + t.rho_df, at<int>(b, t.map_rho_df),
+                          t.nb_rho_df, b->order, 1, s));
     CK(mark(2));
     CK(launch_mu_mixed_batch(at<MuBatchInst>(b, t.mu), at<int>(b, t.map_mu), t.nb_mu, s));
     CK(mark(3));
-    CK(lines_batch_launch(false, b->ws + t.force, at<int>(b, t.map_force), t.nb_force, b->order,
-                          0, s));
+    CK(lines_batch_launch(LineBatchKind::kForce, b->ws + t.force, at<int>(b, t.map_force),
+                          t.nb_force, b->order, 0, s));
     CK(mark(4));
     return LBM_OK;
 }
@@ -312,8 +331,12 @@ lbm_status instance_force(lbm_batch* b, int i) {
     const InstHost& h = b->inst[i];
     DevState* st = b->dst + i;
     cudaStream_t s = b->stream;
-    CK(lines_mixed_rho_xy(h.rh, h.rl, h.dxr, h.dxx, h.dyr, h.dyy, h.nx, h.ny, b->order, st, 0,
-                          s));
+    if (h.rho_df)
+        CK(lines_mixed_rho_xy(h.rh, h.rl, h.dxr, h.dxx, h.dyr, h.dyy, h.nx, h.ny, b->order, st,
+                              0, s));
+    else
+        CK(lines_mixed_rho_xy_f32(h.rh, h.dxr, h.dxx, h.dyr, h.dyy, h.nx, h.ny, b->order, st, 0,
+                                  s));
     CK(launch_mu_mixed(h.rh, h.dxx, h.dyy, h.nx, h.ny, h.phys, st, s));
     CK(lines_mixed_force_xy(h.dxx, h.rh, h.dxr, h.dyr, h.Fx, h.Fy, h.nx, h.ny, b->order, s));
     return LBM_OK;
@@ -324,7 +347,8 @@ lbm_status instance_force(lbm_batch* b, int i) {
 extern "C" {
 
 size_t lbm_batch_workspace_bytes(const lbm_instance* inst, int32_t n, const lbm_opts* opts) {
-    if (!inst || n < 1 || !opts || opts->prec != LBM_PREC_MIXED ||
+    if (!inst || n < 1 || !opts ||
+        (opts->prec != LBM_PREC_MIXED && opts->prec != LBM_PREC_MIXED_DF) ||
         (opts->fd_order != 4 && opts->fd_order != 6))
         return 0;
     size_t o = 0;
@@ -342,7 +366,9 @@ lbm_status lbm_batch_init(lbm_batch** out, const lbm_instance* inst, int32_t n,
     *out = nullptr;
     if (!inst || n < 1 || !opts || !eos) return LBM_EINVAL;
     if (opts->fd_order != 4 && opts->fd_order != 6) return LBM_EINVAL;
-    if (opts->prec != LBM_PREC_MIXED || eos->kind != LBM_EOS_CS) return LBM_ENOTIMPL;
+    if ((opts->prec != LBM_PREC_MIXED && opts->prec != LBM_PREC_MIXED_DF) ||
+        eos->kind != LBM_EOS_CS)
+        return LBM_ENOTIMPL;
     if (!(eos->a > 0 && eos->b > 0 && eos->R > 0)) return LBM_EINVAL;
     for (int i = 0; i < n; ++i) {
         if (!inst[i].grid.periodic_x || !inst[i].grid.periodic_y) return LBM_ENOTIMPL;
@@ -406,6 +432,12 @@ lbm_status lbm_batch_init(lbm_batch** out, const lbm_instance* inst, int32_t n,
         h.t = 0;
         h.ready = false;
         h.rows = 0;
+        h.rho_df = opts->prec == LBM_PREC_MIXED_DF;
+        if (!h.rho_df) {
+            double rg, rl;
+            h.rho_df = cs_maxwell(eos->a, eos->b, eos->R, p.T, &rg, &rl) != 0 ||
+                       !(rl < kDfRatio * rg);
+        }
         o += r.total;
     }
     b->tb = table_layout(inst, n, b->order, o);

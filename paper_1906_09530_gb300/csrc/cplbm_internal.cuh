@@ -146,12 +146,22 @@ cudaError_t launch_mu_mixed_batch(const MuBatchInst* d, const int* map, int nblo
                                   cudaStream_t s);
 // Line passes: descriptor size per instance, blocks per instance, descriptor
 // written to host memory (copied to the device by the caller), the launches.
-// `rho`: the x|y lines of the density (else of mu-hat with the force).
-size_t lines_batch_desc_bytes(bool rho);
-int lines_batch_blocks(int nx, int ny, int order, bool rho);
-void lines_batch_fill(bool rho, const MixedLinesView& v, int order, int blk0, void* host_dst);
-cudaError_t lines_batch_launch(bool rho, const void* d_desc, const int* map, int nblocks,
-                               int order, int bump, cudaStream_t s);
+enum class LineBatchKind {
+    kRhoDF,   // x|y lines of the density, double-float where a window needs it
+    kRhoF32,  // x|y lines of the density in FP32 (the hi part only)
+    kForce,   // x|y lines of mu-hat with the force epilogue
+};
+size_t lines_batch_desc_bytes(LineBatchKind kind);
+int lines_batch_blocks(int nx, int ny, int order, LineBatchKind kind);
+void lines_batch_fill(LineBatchKind kind, const MixedLinesView& v, int order, int blk0,
+                      void* host_dst);
+cudaError_t lines_batch_launch(LineBatchKind kind, const void* d_desc, const int* map,
+                               int nblocks, int order, int bump, cudaStream_t s);
+
+// Below this Maxwell density ratio the mixed path solves the density's lines in
+// FP32 (measured: coexistence densities within 2e-4 of the FP64 path); at and
+// above it, in double-float wherever a window spans more than a factor 32.
+constexpr double kDfRatio = 1e4;
 
 // Warp-cooperative compact-FD line solves (kernels_lines.cu).  axis 0: lines
 // along x, 1: along y.  Passes 2-5 of the FP64 path and of the mixed path, and
@@ -171,6 +181,10 @@ cudaError_t lines_fp64_plain(const double* u, double* d1, double* d2, int nx, in
 cudaError_t lines_mixed_rho_xy(const float* rh, const float* rl, float* dxr, float* dxx,
                                float* dyr, float* dyy, int nx, int ny, int order, DevState* st,
                                int bump, cudaStream_t s);
+// The same in FP32 on the hi part of the density (below kDfRatio).
+cudaError_t lines_mixed_rho_xy_f32(const float* rh, float* dxr, float* dxx, float* dyr,
+                                   float* dyy, int nx, int ny, int order, DevState* st, int bump,
+                                   cudaStream_t s);
 cudaError_t lines_mixed_force_xy(const float* mu, const float* rh, const float* dxr,
                                  const float* dyr, float* Fx, float* Fy, int nx, int ny,
                                  int order, cudaStream_t s);

@@ -779,10 +779,15 @@ constexpr double kEpsD = 1e-17, kEpsDF = 1e-15, kEpsF = 1e-8;
 
 // ---- batched mixed line passes ----
 using RhoInst = LinesXYInst<InDF, EpiStore<float, float>, InDF, EpiStore<float, float>>;
+using RhoF32Inst = LinesXYInst<InF, EpiStore<float, float>, InF, EpiStore<float, float>>;
 using ForceInst = LinesXYInst<InF, EpiForce<float, float>, InF, EpiForce<float, float>>;
 
-int halo_of(bool rho, int order) {
-    return rho ? halo(order, kEpsDF, true, kEpsF) : halo(order, kEpsF, false, kEpsF);
+int halo_of(LineBatchKind kind, int order) {
+    switch (kind) {
+        case LineBatchKind::kRhoDF: return halo(order, kEpsDF, true, kEpsF);
+        case LineBatchKind::kRhoF32: return halo(order, kEpsF, true, kEpsF);
+        default: return halo(order, kEpsF, false, kEpsF);
+    }
 }
 
 template <class P1, class P2, bool SIXTH, bool SECOND, class Inst>
@@ -840,6 +845,13 @@ cudaError_t lines_mixed_rho_xy(const float* rh, const float* rl, float* dxr, flo
                                         InDF{rh, rl}, EpiStore<float, float>{dyr, dyy}, nx, ny,
                                         order, kEpsDF, kEpsF, st, bump, s);
 }
+cudaError_t lines_mixed_rho_xy_f32(const float* rh, float* dxr, float* dxx, float* dyr,
+                                   float* dyy, int nx, int ny, int order, DevState* st, int bump,
+                                   cudaStream_t s) {
+    return launch_xy<PolF, PolF, true>(InF{rh}, EpiStore<float, float>{dxr, dxx}, InF{rh},
+                                       EpiStore<float, float>{dyr, dyy}, nx, ny, order, kEpsF,
+                                       kEpsF, st, bump, s);
+}
 cudaError_t lines_mixed_force_xy(const float* mu, const float* rh, const float* dxr,
                                  const float* dyr, float* Fx, float* Fy, int nx, int ny,
                                  int order, cudaStream_t s) {
@@ -857,41 +869,57 @@ cudaError_t lines_mixed_plain(const float* uh, const float* ul, float* d1, float
 }
 
 // ---- batched mixed path ----
-size_t lines_batch_desc_bytes(bool rho) { return rho ? sizeof(RhoInst) : sizeof(ForceInst); }
+size_t lines_batch_desc_bytes(LineBatchKind kind) {
+    switch (kind) {
+        case LineBatchKind::kRhoDF: return sizeof(RhoInst);
+        case LineBatchKind::kRhoF32: return sizeof(RhoF32Inst);
+        default: return sizeof(ForceInst);
+    }
+}
 
-int lines_batch_blocks(int nx, int ny, int order, bool rho) {
-    const int H = halo_of(rho, order);
+int lines_batch_blocks(int nx, int ny, int order, LineBatchKind kind) {
+    const int H = halo_of(kind, order);
     const LineGeo gx = make_geo(nx, ny, 0, H), gy = make_geo(nx, ny, 1, H);
     return gx.ngroups * gx.nwin + gy.ngroups * gy.nwin;
 }
 
-void lines_batch_fill(bool rho, const MixedLinesView& v, int order, int blk0, void* host_dst) {
-    const int H = halo_of(rho, order);
+void lines_batch_fill(LineBatchKind kind, const MixedLinesView& v, int order, int blk0,
+                      void* host_dst) {
+    const int H = halo_of(kind, order);
     const LineGeo gx = make_geo(v.nx, v.ny, 0, H), gy = make_geo(v.nx, v.ny, 1, H);
-    if (rho) {
+    const int nbx = gx.ngroups * gx.nwin;
+    if (kind == LineBatchKind::kRhoDF) {
         RhoInst d{InDF{v.rh, v.rl}, EpiStore<float, float>{v.dxr, v.dxx},
-                  InDF{v.rh, v.rl}, EpiStore<float, float>{v.dyr, v.dyy},
-                  gx, gy, gx.ngroups * gx.nwin, blk0, v.st};
+                  InDF{v.rh, v.rl}, EpiStore<float, float>{v.dyr, v.dyy}, gx, gy, nbx, blk0, v.st};
+        std::memcpy(host_dst, &d, sizeof(d));
+    } else if (kind == LineBatchKind::kRhoF32) {
+        RhoF32Inst d{InF{v.rh}, EpiStore<float, float>{v.dxr, v.dxx},
+                     InF{v.rh}, EpiStore<float, float>{v.dyr, v.dyy}, gx, gy, nbx, blk0, v.st};
         std::memcpy(host_dst, &d, sizeof(d));
     } else {
         ForceInst d{InF{v.dxx}, EpiForce<float, float>{v.Fx, v.rh, v.dxr},
-                    InF{v.dxx}, EpiForce<float, float>{v.Fy, v.rh, v.dyr},
-                    gx, gy, gx.ngroups * gx.nwin, blk0, v.st};
+                    InF{v.dxx}, EpiForce<float, float>{v.Fy, v.rh, v.dyr}, gx, gy, nbx, blk0, v.st};
         std::memcpy(host_dst, &d, sizeof(d));
     }
 }
 
-cudaError_t lines_batch_launch(bool rho, const void* d_desc, const int* map, int nblocks,
-                               int order, int bump, cudaStream_t s) {
+cudaError_t lines_batch_launch(LineBatchKind kind, const void* d_desc, const int* map,
+                               int nblocks, int order, int bump, cudaStream_t s) {
     if (nblocks <= 0) return cudaSuccess;
-    if (rho) {
+    const bool six = order == 6;
+    if (kind == LineBatchKind::kRhoDF) {
         const RhoInst* d = static_cast<const RhoInst*>(d_desc);
-        return order == 6 ? launch_batch_t<PolDF, PolF, true, true>(d, map, nblocks, order, bump, s)
-                          : launch_batch_t<PolDF, PolF, false, true>(d, map, nblocks, order, bump, s);
+        return six ? launch_batch_t<PolDF, PolF, true, true>(d, map, nblocks, order, bump, s)
+                   : launch_batch_t<PolDF, PolF, false, true>(d, map, nblocks, order, bump, s);
+    }
+    if (kind == LineBatchKind::kRhoF32) {
+        const RhoF32Inst* d = static_cast<const RhoF32Inst*>(d_desc);
+        return six ? launch_batch_t<PolF, PolF, true, true>(d, map, nblocks, order, bump, s)
+                   : launch_batch_t<PolF, PolF, false, true>(d, map, nblocks, order, bump, s);
     }
     const ForceInst* d = static_cast<const ForceInst*>(d_desc);
-    return order == 6 ? launch_batch_t<PolF, PolF, true, false>(d, map, nblocks, order, 0, s)
-                      : launch_batch_t<PolF, PolF, false, false>(d, map, nblocks, order, 0, s);
+    return six ? launch_batch_t<PolF, PolF, true, false>(d, map, nblocks, order, 0, s)
+               : launch_batch_t<PolF, PolF, false, false>(d, map, nblocks, order, 0, s);
 }
 
 }  // namespace cplbm

@@ -31,6 +31,9 @@ def _instances():
         dict(nx=512, ny=512, T_r=0.55, k=0.5, tau=1.0, kappa=0.1),
         dict(nx=8, ny=400, T_r=0.8, k=0.1, tau=1.0, kappa=0.1),
         dict(nx=96, ny=96, T_r=0.45, k=0.5, tau=1.0, kappa=0.1, mu_cap_steps=5),
+        # density ratios above 1e4: double-float density lines in "mixed" too
+        dict(nx=160, ny=128, T_r=0.36, k=0.3, tau=1.0, kappa=0.1),
+        dict(nx=8, ny=256, T_r=0.32, k=0.2, tau=1.0, kappa=0.1),
     ]
     tc = thermo.critical_point()[0]
     spec[6]["mu_max"] = float(thermo.mu0(0.5 * (1 + thermo.maxwell(0.45)[1]), 0.45 * tc))
@@ -45,25 +48,28 @@ def _instances():
     return spec, rhos
 
 
-def _lone(d, rho, fd_order=6):
+def _lone(d, rho, fd_order=6, precision="mixed"):
     from paper_1906_09530_gb300 import Simulation
     s = Simulation(d["nx"], d["ny"], d["T_r"], d["kappa"], d["tau"], d["k"], fd_order=fd_order,
-                   precision="mixed", mu_max=d.get("mu_max", math.inf),
+                   precision=precision, mu_max=d.get("mu_max", math.inf),
                    mu_cap_steps=d.get("mu_cap_steps", 0))
     s.set_fields(rho)
     return s
 
 
-@pytest.mark.parametrize("fd_order,steps", [(6, 7), (4, 10)])
-def test_batch_bitexact_vs_lone_contexts(cuda, fd_order, steps):
+@pytest.mark.parametrize("fd_order,steps,precision",
+                         [(6, 7, "mixed"), (4, 10, "mixed"), (6, 5, "mixed_df")])
+def test_batch_bitexact_vs_lone_contexts(cuda, fd_order, steps, precision):
+    """Both density-line kinds (FP32 below ratio 1e4, double-float above, or
+    double-float everywhere with "mixed_df") in one batch."""
     from paper_1906_09530_gb300 import Batch
     spec, rhos = _instances()
-    b = Batch(spec, fd_order=fd_order)
+    b = Batch(spec, fd_order=fd_order, precision=precision)
     for i, r in enumerate(rhos):
         b.set_fields(i, r)
     b.step(steps)
     for i, (d, r) in enumerate(zip(spec, rhos)):
-        s = _lone(d, r, fd_order)
+        s = _lone(d, r, fd_order, precision)
         s.step(steps)
         want = s.fields()
         got = b.fields(i)

@@ -213,9 +213,12 @@ def test_config2_full_size_steps(cuda):
     assert rel_point(g.fields()[0], o.fields()[0]) <= 1e-12
 
 
-def test_config2_mixed_full_size_steps(cuda):
+@pytest.mark.parametrize("precision", ["mixed", "mixed_df"])
+def test_config2_mixed_full_size_steps(cuda, precision):
+    """1024^2, T_r = 0.45 (ratio 2.3e3: FP32 density lines in "mixed", double-float
+    in "mixed_df"), every node after 4 steps against the oracle."""
     c = cases.config2(0.45)
-    g = cases.gpu_sim(c, precision="mixed")
+    g = cases.gpu_sim(c, precision=precision)
     g.set_fields(c["rho"])
     g.step(4)
     o = cases.oracle_sim(c)
@@ -224,13 +227,14 @@ def test_config2_mixed_full_size_steps(cuda):
     assert rel_point(g.fields()[0], o.fields()[0]) <= 2e-6
 
 
+@pytest.mark.parametrize("precision", ["mixed", "mixed_df"])
 @pytest.mark.parametrize("case", ["config1", "ragged4", "ragged6"])
-def test_mixed_force_stage_t0(cuda, case):
+def test_mixed_force_stage_t0(cuda, case, precision):
     """Mixed path at t = 0: f^eq rounded to FP32, density kept exactly; mu-hat and
     the force in FP32 against the FP64 oracle."""
     c = {"config1": cases.config1(), "ragged4": cases.ragged(order=4),
          "ragged6": cases.ragged(order=6)}[case]
-    g = cases.gpu_sim(c, precision="mixed")
+    g = cases.gpu_sim(c, precision=precision)
     g.set_fields(c["rho"])
     rho, vx, vy, mu = g.fields()
     o = cases.oracle_sim(c)
