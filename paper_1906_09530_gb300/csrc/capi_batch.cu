@@ -67,7 +67,7 @@ int cs_blocks_for(int nx, int ny, int rows) {
     return cs_mixed_blocks(cs_mixed_args(nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
                                          nx, ny, 0, 1.0, nullptr, rows));
 }
-int mu_blocks_for(size_t N) { return (int)((N + kMuBatchT - 1) / kMuBatchT); }
+int mu_blocks_for(size_t N) { return (int)(((N + 3) / 4 + kMuBatchT - 1) / kMuBatchT); }
 
 // Offsets of the table region, sized for the largest block counts (the
 // smallest strip height) so that autotuning never needs more room.

@@ -114,7 +114,7 @@ struct MuConstF {
     float T, a, b, R, k2, kappa, cap;
     long long cap_steps;
 };
-constexpr int kMuBatchT = 256;  // threads (= nodes) per block of the batched mu-hat pass
+constexpr int kMuBatchT = 256;  // threads per block of the batched mu-hat pass (4 nodes each)
 struct MuBatchInst {
     const float* rh;
     float* mu;  // holds d_xx rho on entry

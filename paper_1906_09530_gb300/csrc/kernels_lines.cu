@@ -149,6 +149,7 @@ struct LineGeo {
     int own;        // owned positions per window
     int nwin;       // windows per line
     int ngroups;    // line groups of kNL
+    int vec;        // nx % 4 == 0: 16-byte staging (x-lines) and epilogue (float fields)
 };
 
 // Asynchronous global -> shared copies (cp.async): the staging loads need no
@@ -160,6 +161,10 @@ __device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc) {
 __device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.wait_all;\n" ::: "memory");
@@ -173,6 +178,10 @@ struct InD {
     __device__ __forceinline__ void stage(double* t, int i, int, size_t o) {
         cp_async8(t + i, p + o);
     }
+    __device__ __forceinline__ void stage4(double* t, int i, int, size_t o) {
+        cp_async16(t + i, p + o);
+        cp_async16(t + i + 2, p + o + 2);
+    }
     __device__ __forceinline__ bool flagged() const { return false; }
 };
 struct InF {
@@ -180,6 +189,10 @@ struct InF {
     __device__ __forceinline__ void init(const DevState*) {}
     __device__ __forceinline__ void stage(float* t, int i, int, size_t o) {
         cp_async4(t + i, p + o);
+    }
+    // four consecutive elements, 16-byte aligned on both sides
+    __device__ __forceinline__ void stage4(float* t, int i, int, size_t o) {
+        cp_async16(t + i, p + o);
     }
     __device__ __forceinline__ bool flagged() const { return false; }
 };
@@ -190,6 +203,10 @@ struct InDF {
     __device__ __forceinline__ void stage(float* t, int i, int ps, size_t o) {
         cp_async4(t + i, h + o);
         cp_async4(t + i + ps, l + o);
+    }
+    __device__ __forceinline__ void stage4(float* t, int i, int ps, size_t o) {
+        cp_async16(t + i, h + o);
+        cp_async16(t + i + ps, l + o);
     }
     __device__ __forceinline__ bool flagged() const { return false; }
 };
@@ -397,23 +414,43 @@ __device__ __forceinline__ void lines_body(In& in, const LineGeo& g, const LineC
     constexpr int LWIN = kW + 8;
     const int p0 = wrapi((long long)s - g.H - 4, g.n);  // line position of window slot 0
     const bool short_line = g.n < LWIN;
-    for (int idx = tid; idx < kNL * LWIN; idx += kNL * 32) {
-        int l, q;
-        if (AXIS == 0) {
-            l = idx / LWIN;
-            q = idx - l * LWIN;
-        } else {
-            q = idx / kNL;
-            l = idx - q * kNL;
+    if (AXIS == 0 && g.vec) {
+        // rows: 16-byte chunks (p0, H and own are multiples of 4, and so is the
+        // line length, so no chunk straddles the periodic wrap)
+        constexpr int CW = LWIN / 4;
+        for (int idx = tid; idx < kNL * CW; idx += kNL * 32) {
+            const int l = idx / CW;
+            const int q = 4 * (idx - l * CW);
+            const int line = line0 + l;
+            if (line < g.nlines) {
+                int p = p0 + q;
+                if (short_line) p %= g.n;
+                else if (p >= g.n) p -= g.n;
+                in.stage4(tin, l * kLW + q, kPS, (size_t)line * g.ls + (size_t)p);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) P1::sput(tin, l * kLW + q + k, kPS, P1::zero());
+            }
         }
-        const int line = line0 + l;
-        if (line < g.nlines) {
-            int p = p0 + q;
-            if (short_line) p %= g.n;
-            else if (p >= g.n) p -= g.n;
-            in.stage(tin, l * kLW + q, kPS, (size_t)line * g.ls + (size_t)p * g.ps);
-        } else {
-            P1::sput(tin, l * kLW + q, kPS, P1::zero());
+    } else {
+        for (int idx = tid; idx < kNL * LWIN; idx += kNL * 32) {
+            int l, q;
+            if (AXIS == 0) {
+                l = idx / LWIN;
+                q = idx - l * LWIN;
+            } else {
+                q = idx / kNL;
+                l = idx - q * kNL;
+            }
+            const int line = line0 + l;
+            if (line < g.nlines) {
+                int p = p0 + q;
+                if (short_line) p %= g.n;
+                else if (p >= g.n) p -= g.n;
+                in.stage(tin, l * kLW + q, kPS, (size_t)line * g.ls + (size_t)p * g.ps);
+            } else {
+                P1::sput(tin, l * kLW + q, kPS, P1::zero());
+            }
         }
     }
     cp_async_wait_all();
@@ -464,8 +501,60 @@ __device__ __forceinline__ void lines_body(In& in, const LineGeo& g, const LineC
     constexpr int kB = 4;
     const int nown = e - s;
     const int lmax = min(kNL, g.nlines - line0);
-    const int total = kNL * nown;
     bool bad = false;
+    if constexpr (sizeof(O1) == 4 && sizeof(V2) == 4) {
+        if (g.vec) {
+            // float fields, nx % 4 == 0: chunks of four outputs, 16-byte stores.
+            // x-lines: four consecutive positions of one line; y-lines: one
+            // position of four adjacent lines (columns line0 + 4h .. + 3).
+            const int cpl = AXIS == 0 ? nown / 4 : 2;  // chunks per line / per position
+            const int total = AXIS == 0 ? kNL * cpl : 2 * nown;
+            for (int base = tid; base < total; base += kB * kNL * 32) {
+                int sl[kB];
+                size_t off[kB];
+                typename Epi::Ops4 ops[kB];
+#pragma unroll
+                for (int k = 0; k < kB; ++k) {
+                    const int idx = base + k * kNL * 32;
+                    bool live;
+                    if (AXIS == 0) {
+                        const int ll = idx / cpl;
+                        const int qq = 4 * (idx - ll * cpl);
+                        live = idx < total && ll < lmax;
+                        sl[k] = ll * kSO + g.H + qq;
+                        off[k] = (size_t)(line0 + ll) * g.ls + (size_t)(s + qq);
+                    } else {
+                        const int qq = idx >> 1, h4 = 4 * (idx & 1);
+                        live = idx < total && h4 < lmax;
+                        sl[k] = h4 * kSO + g.H + qq;
+                        off[k] = (size_t)(line0 + h4) + (size_t)(s + qq) * g.ps;
+                    }
+                    if (!live) sl[k] = -1;
+                    else ops[k] = epi.fetch4(off[k]);
+                }
+#pragma unroll
+                for (int k = 0; k < kB; ++k) {
+                    if (sl[k] < 0) continue;
+                    float4 a, b = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (AXIS == 0) {
+                        a = *reinterpret_cast<const float4*>(tout1 + sl[k]);
+                        if (SECOND) b = *reinterpret_cast<const float4*>(tout2 + sl[k]);
+                    } else {
+                        a = make_float4(tout1[sl[k]], tout1[sl[k] + kSO], tout1[sl[k] + 2 * kSO],
+                                        tout1[sl[k] + 3 * kSO]);
+                        if (SECOND)
+                            b = make_float4(tout2[sl[k]], tout2[sl[k] + kSO],
+                                            tout2[sl[k] + 2 * kSO], tout2[sl[k] + 3 * kSO]);
+                    }
+                    bad |= epi.put4(off[k], a, b, ops[k]);
+                }
+            }
+            bad |= in.flagged();
+            if (bad) raise_flag(st, FLAG_EOS, st->t);
+            return;
+        }
+    }
+    const int total = kNL * nown;
     int l0 = 0, q0e = tid;  // AXIS 0 walk: position q0e within line l0
     if (AXIS == 0) {
         while (q0e >= nown && l0 < kNL) { q0e -= nown; ++l0; }
@@ -580,11 +669,19 @@ struct EpiStore {
     O* d1;
     V2* d2;
     struct Ops {};
+    struct Ops4 {};
     __device__ __forceinline__ void init(const DevState*) {}
     __device__ __forceinline__ Ops fetch(size_t) const { return Ops{}; }
     __device__ __forceinline__ bool operator()(size_t o, O a, V2 b, const Ops&) {
         d1[o] = a;
         if (d2) d2[o] = b;
+        return false;
+    }
+    // four consecutive outputs (float fields only)
+    __device__ __forceinline__ Ops4 fetch4(size_t) const { return Ops4{}; }
+    __device__ __forceinline__ bool put4(size_t o, float4 a, float4 b, const Ops4&) {
+        *reinterpret_cast<float4*>(d1 + o) = a;
+        if (d2) *reinterpret_cast<float4*>(d2 + o) = b;
         return false;
     }
 };
@@ -604,6 +701,9 @@ struct EpiMu {
         RhoT r;
         O xx;
     };
+    struct Ops4 {};  // the FP64 path has no vector epilogue
+    __device__ __forceinline__ Ops4 fetch4(size_t) const { return Ops4{}; }
+    __device__ __forceinline__ bool put4(size_t, float4, float4, const Ops4&) { return false; }
     // the time level is read on the device: graph replays reuse the arguments
     __device__ __forceinline__ void init(const DevState* st) { capped = st->t < cap_steps; }
     __device__ __forceinline__ Ops fetch(size_t o) const { return Ops{__ldg(rho + o), __ldg(dxx + o)}; }
@@ -635,6 +735,23 @@ struct EpiForce {
     __device__ __forceinline__ bool operator()(size_t o, O dmu, O, const Ops& op) {
         // explicit rounding: the epilogue is inlined in several kernels
         F[o] = rn_fma(-(O)op.r, dmu, rn_mul(op.d, (O)(1.0 / 3.0)));
+        return false;
+    }
+    struct Ops4 {
+        float4 r, d;
+    };
+    __device__ __forceinline__ Ops4 fetch4(size_t o) const {
+        return Ops4{__ldg(reinterpret_cast<const float4*>(rho + o)),
+                    __ldg(reinterpret_cast<const float4*>(dr + o))};
+    }
+    __device__ __forceinline__ bool put4(size_t o, float4 dmu, float4, const Ops4& op) {
+        const float t = 1.0f / 3.0f;
+        float4 f;
+        f.x = rn_fma(-op.r.x, dmu.x, rn_mul(op.d.x, t));
+        f.y = rn_fma(-op.r.y, dmu.y, rn_mul(op.d.y, t));
+        f.z = rn_fma(-op.r.z, dmu.z, rn_mul(op.d.z, t));
+        f.w = rn_fma(-op.r.w, dmu.w, rn_mul(op.d.w, t));
+        *reinterpret_cast<float4*>(F + o) = f;
         return false;
     }
 };
@@ -696,11 +813,15 @@ LineGeo make_geo(int nx, int ny, int axis, int H) {
     } else {
         g.n = ny; g.nlines = nx; g.ps = nx; g.ls = 1;
     }
+    // the halo is rounded up to a multiple of 4 so that windows start on
+    // 16-byte boundaries (own = kW - 2H is then a multiple of 4 too)
+    H = (H + 3) / 4 * 4;
     g.H = H;
     g.own = kW - 2 * H;
     if (g.own > g.n) g.own = g.n;
     g.nwin = (g.n + g.own - 1) / g.own;
     g.ngroups = (g.nlines + kNL - 1) / kNL;
+    g.vec = nx % 4 == 0;
     return g;
 }
 

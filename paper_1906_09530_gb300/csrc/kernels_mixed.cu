@@ -202,28 +202,48 @@ __global__ void k_macro_mixed(const float* __restrict__ f, const float* __restri
 // from above while the time level t < cap_steps (Sec. 5.6; t read on the device
 // so that graph replays stay correct).  Written over d_xx rho, which nothing
 // needs afterwards.
+__device__ __forceinline__ float mu_node(float r, float xx, float yy, const MuConstF& p,
+                                         bool capped, bool& bad) {
+    // explicit rounding: the body is inlined in the lone and batched kernels
+    const float eta = rn_mul(rn_mul(0.25f, p.b), r);
+    const float om = rn_sub(1.0f, eta);
+    const float rt = rn_mul(p.R, p.T);
+    const float cs = rn_add(rn_add(rn_div(rn_sub(3.0f, eta), rn_mul(rn_mul(om, om), om)),
+                                   logf(r)),
+                            1.0f);
+    const float mu0 = rn_fma(rt, cs, -rn_mul(rn_mul(2.0f, p.a), r));
+    float m = rn_fma(p.k2, mu0, -rn_mul(p.kappa, rn_add(xx, yy)));
+    if (capped) m = fminf(m, p.cap);
+    bad |= !(r > 0.0f && eta < 1.0f && fabsf(m) < 1e30f);
+    return m;
+}
+
+// Chunks of four nodes (16-byte loads and stores: the planes are 256-byte
+// aligned), chunk c0, c0 + stride, ...; a short last chunk node by node.
 __device__ __forceinline__ void mu_mixed_body(const float* __restrict__ rh, float* dxx_mu,
                                               const float* __restrict__ dyy, size_t N,
                                               const MuConstF& p, DevState* __restrict__ st,
-                                              size_t n0, size_t stride) {
-    const float T = p.T, a = p.a, b = p.b, R = p.R, k2 = p.k2, kappa = p.kappa, cap = p.cap;
+                                              size_t c0, size_t stride) {
     const int64_t t = st->t;
     const bool capped = t < p.cap_steps;
     bool bad = false;
-    for (size_t n = n0; n < N; n += stride) {
-        const float r = rh[n];
-        const float eta = rn_mul(rn_mul(0.25f, b), r);
-        const float om = rn_sub(1.0f, eta);
-        // explicit rounding: the body is inlined in the lone and batched kernels
-        const float rt = rn_mul(R, T);
-        const float cs = rn_add(rn_add(rn_div(rn_sub(3.0f, eta), rn_mul(rn_mul(om, om), om)),
-                                       logf(r)),
-                                1.0f);
-        const float mu0 = rn_fma(rt, cs, -rn_mul(rn_mul(2.0f, a), r));
-        float m = rn_fma(k2, mu0, -rn_mul(kappa, rn_add(dxx_mu[n], dyy[n])));
-        if (capped) m = fminf(m, cap);
-        bad |= !(r > 0.0f && eta < 1.0f && fabsf(m) < 1e30f);
-        dxx_mu[n] = m;
+    const size_t nch = (N + 3) / 4;
+    for (size_t c = c0; c < nch; c += stride) {
+        const size_t n = 4 * c;
+        if (n + 4 <= N) {
+            const float4 r = *reinterpret_cast<const float4*>(rh + n);
+            const float4 x = *reinterpret_cast<const float4*>(dxx_mu + n);
+            const float4 y = *reinterpret_cast<const float4*>(dyy + n);
+            float4 m;
+            m.x = mu_node(r.x, x.x, y.x, p, capped, bad);
+            m.y = mu_node(r.y, x.y, y.y, p, capped, bad);
+            m.z = mu_node(r.z, x.z, y.z, p, capped, bad);
+            m.w = mu_node(r.w, x.w, y.w, p, capped, bad);
+            *reinterpret_cast<float4*>(dxx_mu + n) = m;
+        } else {
+            for (size_t q = n; q < N; ++q)
+                dxx_mu[q] = mu_node(rh[q], dxx_mu[q], dyy[q], p, capped, bad);
+        }
     }
     if (bad) raise_flag(st, FLAG_EOS, t);
 }
@@ -235,12 +255,12 @@ __global__ void k_mu_mixed(const float* __restrict__ rh, float* dxx_mu,
                   (size_t)gridDim.x * blockDim.x);
 }
 
-// Batched: one node per thread, blocks of kMuBatchT threads mapped to instances.
+// Batched: blocks of kMuBatchT threads, four nodes per thread, mapped to instances.
 __global__ void __launch_bounds__(kMuBatchT)
     k_mu_mixed_batch(const MuBatchInst* __restrict__ d, const int* __restrict__ map) {
     const MuBatchInst& D = d[map[blockIdx.x]];
-    const size_t n = ((size_t)blockIdx.x - D.blk0) * kMuBatchT + threadIdx.x;
-    mu_mixed_body(D.rh, D.mu, D.dyy, D.N, D.c, D.st, n, D.N);
+    const size_t c = ((size_t)blockIdx.x - D.blk0) * kMuBatchT + threadIdx.x;
+    mu_mixed_body(D.rh, D.mu, D.dyy, D.N, D.c, D.st, c, (D.N + 3) / 4);
 }
 
 constexpr int kDiagT = 256;
@@ -361,7 +381,8 @@ MuConstF mu_mixed_const(const PhysParams& p) {
 cudaError_t launch_mu_mixed(const float* rh, float* dxx_mu, const float* dyy, int nx, int ny,
                             const PhysParams& p, DevState* st, cudaStream_t s) {
     const size_t N = (size_t)nx * ny;
-    k_mu_mixed<<<grid_for(N, 256), 256, 0, s>>>(rh, dxx_mu, dyy, N, mu_mixed_const(p), st);
+    k_mu_mixed<<<grid_for((N + 3) / 4, 256), 256, 0, s>>>(rh, dxx_mu, dyy, N, mu_mixed_const(p),
+                                                           st);
     return cudaGetLastError();
 }
 
