@@ -187,3 +187,20 @@ def test_batch_rejects_bad_instances(cuda):
         Batch([dict(nx=64, ny=4, T_r=0.7)])
     with pytest.raises(LbmError):
         Batch([dict(nx=64, ny=64, T_r=0.7, tau=0.5)])
+
+
+def test_batch_step_timed_matches_step(cuda):
+    from paper_1906_09530_gb300 import Batch
+    spec, rhos = _instances()
+    a, b = Batch(spec), Batch(spec)
+    for i, r in enumerate(rhos):
+        a.set_fields(i, r)
+        b.set_fields(i, r)
+    for _ in range(3):
+        ms = a.step_timed()
+        assert len(ms) == 4 and all(0 < m < 1e3 for m in ms)
+    b.step(3)
+    for i in range(len(spec)):
+        assert np.array_equal(a.fields(i)[0], b.fields(i)[0])
+    a.close()
+    b.close()

@@ -354,3 +354,25 @@ def test_set_fields_device_matches_host(cuda):
     ra = a.fields()[0]
     rb = b.fields_device()[0].cpu().numpy()
     assert np.array_equal(ra, rb)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_step_timed_matches_step(cuda, precision):
+    """lbm_step_timed (one step of direct launches with an event record around
+    each pass) advances the state exactly like lbm_step, from either population
+    buffer, and reports positive pass times (the FP64 path five, the mixed path
+    four and a zero)."""
+    c = cases.ragged(nx=64, ny=48)
+    a = cases.gpu_sim(c, precision=precision)
+    b = cases.gpu_sim(c, precision=precision)
+    a.set_fields(c["rho"])
+    b.set_fields(c["rho"])
+    for _ in range(5):
+        ms = a.step_timed()
+        npass = 5 if precision == "fp64" else 4
+        assert all(0 < m < 1e3 for m in ms[:npass])
+        assert all(m >= 0 for m in ms)
+    b.step(5)
+    assert a.t == b.t == 5
+    for x, y in zip(a.fields(), b.fields()):
+        assert np.array_equal(x, y)
