@@ -16,7 +16,10 @@
  *   k      proportional coefficient of Eq. 25 (mesh_coeff)
  *   kappa  the mesh-space kappa-hat of Eq. 33
  *   T      absolute temperature (T = T_r * T_c, Sec. 3.2)
- *   a,b,R  Carnahan-Starling constants of Eq. 20 (the paper uses a=1, b=4, R=1)
+ *   a,b,R  EOS constants (Carnahan-Starling, Eq. 20: the paper uses a=1, b=4, R=1)
+ *   eos    0 CS (Eqs. 20-21), 1 VDW (Eqs. 14-15), 2 RK, 3 RKS (Eqs. 16-17),
+ *          4 PR (Eqs. 18-19); eos_alpha the temperature function alpha(T) of
+ *          RK/RKS/PR at the run's T (1 for CS and VDW)
  *
  * Populations are stored structure-of-arrays, f[i][y][x], i = 0..8 in the
  * velocity order of Sec. 2.
@@ -42,6 +45,8 @@ typedef struct {
     double alpha;           /* compact-FD alpha of Eq. 37/38: 1/4 (4th) or 1/3 (6th) */
     double mu_max;          /* chemical-potential upper limit (Sec. 5.6), momentum units */
     int64_t mu_cap_steps;   /* the limit acts while the time level t < mu_cap_steps */
+    int32_t eos;            /* EOS kind, see the header comment (0: CS) */
+    double eos_alpha;       /* alpha(T) of Eqs. 16-19 */
 } orc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -64,6 +69,38 @@ double orc_cs_mu0(double rho, double T, double a, double b, double R)
     double eta = b * rho / 4.0;
     double den = (1.0 - eta) * (1.0 - eta) * (1.0 - eta);
     return R * T * ((3.0 - eta) / den + log(rho) + 1.0) - 2.0 * a * rho;
+}
+
+/* Pressure of each EOS of Sec. 3.2 as printed: VDW Eq. 14, RK/RKS Eq. 16,
+ * PR Eq. 18, CS Eq. 20.  al is alpha(T) (unused by VDW and CS). */
+double orc_p0(int kind, double rho, double T, double a, double b, double R, double al)
+{
+    if (kind == 0)
+        return orc_cs_p0(rho, T, a, b, R);
+    double rep = rho * R * T / (1.0 - b * rho);
+    if (kind == 1)
+        return rep - a * rho * rho;
+    if (kind == 2 || kind == 3)
+        return rep - a * al * rho * rho / (1.0 + b * rho);
+    return rep - a * al * rho * rho / (1.0 + 2.0 * b * rho - b * b * rho * rho);
+}
+
+/* Chemical potential without the gradient term of each EOS as printed:
+ * VDW Eq. 15, RK/RKS Eq. 17, PR Eq. 19, CS Eq. 21. */
+double orc_mu0(int kind, double rho, double T, double a, double b, double R, double al)
+{
+    if (kind == 0)
+        return orc_cs_mu0(rho, T, a, b, R);
+    double om = 1.0 - b * rho;
+    if (kind == 1)
+        return R * T * (log(rho / om) + 1.0 / om) - 2.0 * a * rho;
+    if (kind == 2 || kind == 3)
+        return R * T * log(rho / om) + R * T / om - a * al / b * log(1.0 + b * rho) -
+               a * al * rho / (1.0 + b * rho);
+    double s2 = sqrt(2.0);
+    return R * T * log(rho / om) -
+           a * al / (2.0 * s2 * b) * log((s2 - 1.0 + b * rho) / (s2 + 1.0 - b * rho)) +
+           R * T / om - a * al * rho / (1.0 + 2.0 * b * rho - b * b * rho * rho);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -229,7 +266,7 @@ int orc_force_stage(const orc_params *p, int64_t t, const double *rho, double *m
     err |= cfd_y(p, dyr, dyyr);
     double k2 = p->k * p->k;
     for (size_t n = 0; n < N; ++n) {
-        double m = k2 * orc_cs_mu0(rho[n], p->T, p->a, p->b, p->R) -
+        double m = k2 * orc_mu0(p->eos, rho[n], p->T, p->a, p->b, p->R, p->eos_alpha) -
                    p->kappa * (dxxr[n] + dyyr[n]);
         if (t < p->mu_cap_steps && m > k2 * p->mu_max)
             m = k2 * p->mu_max;

@@ -22,7 +22,11 @@ class OrcParams(C.Structure):
                 ("R", C.c_double),
                 ("kappa", C.c_double), ("tau", C.c_double), ("k", C.c_double),
                 ("alpha", C.c_double),
-                ("mu_max", C.c_double), ("mu_cap_steps", C.c_int64)]
+                ("mu_max", C.c_double), ("mu_cap_steps", C.c_int64),
+                ("eos", C.c_int32), ("eos_alpha", C.c_double)]
+
+# EOS kinds of the C oracle (its header comment)
+EOS_KIND = {"cs": 0, "vdw": 1, "rk": 2, "rks": 3, "pr": 4}
 
 
 def lib():
@@ -34,6 +38,10 @@ def lib():
         L.orc_cs_p0.argtypes = [C.c_double] * 5
         L.orc_cs_mu0.restype = C.c_double
         L.orc_cs_mu0.argtypes = [C.c_double] * 5
+        L.orc_p0.restype = C.c_double
+        L.orc_p0.argtypes = [C.c_int] + [C.c_double] * 6
+        L.orc_mu0.restype = C.c_double
+        L.orc_mu0.argtypes = [C.c_int] + [C.c_double] * 6
         L.orc_cfd_line.restype = C.c_int
         L.orc_cfd_line.argtypes = [dp, C.c_ssize_t, dp, C.c_ssize_t, C.c_int,
                                    C.c_double, C.c_double]
@@ -62,6 +70,15 @@ def _ptr(a):
 def cs_p0(rho, T, a=1.0, b=4.0, R=1.0):
     """Carnahan-Starling pressure, Eq. 20 (scalar)."""
     return lib().orc_cs_p0(rho, T, a, b, R)
+
+
+def eos_p0(kind, rho, T, a, b, R, alpha):
+    """The C oracle's p0 of EOS `kind` (a name of EOS_KIND)."""
+    return lib().orc_p0(EOS_KIND[kind], rho, T, a, b, R, alpha)
+
+
+def eos_mu0(kind, rho, T, a, b, R, alpha):
+    return lib().orc_mu0(EOS_KIND[kind], rho, T, a, b, R, alpha)
 
 
 def cs_mu0(rho, T, a=1.0, b=4.0, R=1.0):
@@ -99,9 +116,14 @@ class OracleSim:
     """One periodic D2Q9 simulation advanced by the C oracle, FP64."""
 
     def __init__(self, nx, ny, T, kappa, tau, k, fd_order, mu_max=math.inf,
-                 mu_cap_steps=0, a=1.0, b=4.0, R=1.0):
+                 mu_cap_steps=0, a=1.0, b=4.0, R=1.0, eos=None):
+        """`eos`: an oracle.eos.Eos (its kind, a, b, R and alpha(T) replace the
+        Carnahan-Starling defaults)."""
+        kind, al = 0, 1.0
+        if eos is not None:
+            kind, a, b, R, al = EOS_KIND[eos.kind], eos.a, eos.b, eos.R, eos.alpha(T)
         self.p = OrcParams(nx, ny, T, a, b, R, kappa, tau, k, cfd_alpha(fd_order),
-                           mu_max, mu_cap_steps)
+                           mu_max, mu_cap_steps, kind, al)
         self.nx, self.ny = nx, ny
         self.t = 0
         self.f = np.zeros((9, ny, nx))
