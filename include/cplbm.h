@@ -50,8 +50,15 @@ typedef enum {
     LBM_ENOTIMPL = 6   /* option recognised but not built (e.g. non-periodic) */
 } lbm_status;
 
-/* Equation of state.  Only Carnahan-Starling is on the hot path. */
-enum { LBM_EOS_CS = 0 };
+/* Equation of state (Sec. 3.2); p0 and mu0 exactly as printed:
+ *   LBM_EOS_CS   Carnahan-Starling, Eqs. 20-21 (the paper: a=1, b=4, R=1)
+ *   LBM_EOS_VDW  van der Waals, Eqs. 14-15 (a=9/49, b=2/21)
+ *   LBM_EOS_RK   Redlich-Kwong, Eqs. 16-17 with alpha(T) = 1/sqrt(T)
+ *   LBM_EOS_RKS  Soave-Redlich-Kwong, Eqs. 16-17 with alpha(T_r) of the acentric
+ *                factor omega (a=2/49, b=2/21)
+ *   LBM_EOS_PR   Peng-Robinson, Eqs. 18-19 with its alpha(T_r) and omega
+ *                (a=2/49, b=2/21; omega 0.344 for water, 0.011 for methane) */
+enum { LBM_EOS_CS = 0, LBM_EOS_VDW = 1, LBM_EOS_RK = 2, LBM_EOS_RKS = 3, LBM_EOS_PR = 4 };
 
 /* Precision.  FP64: everything in double.  MIXED: populations and the
  * collide-stream pass in float; the density kept exactly as a double-float pair
@@ -69,9 +76,9 @@ typedef struct {
 } lbm_grid;
 
 typedef struct {
-    int32_t kind;          /* LBM_EOS_CS */
-    double a, b, R, omega; /* Eq. 20: the paper's CS values are a=1, b=4, R=1;
-                              omega (acentric factor) is unused by CS */
+    int32_t kind;          /* LBM_EOS_* */
+    double a, b, R, omega; /* attraction a, volume correction b, gas constant R
+                              (all > 0); omega: acentric factor (RKS and PR only) */
 } lbm_eos;
 
 typedef struct {

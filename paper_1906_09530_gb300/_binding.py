@@ -14,7 +14,7 @@ import numpy as np
 from . import _build
 
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ENOTIMPL = range(7)
-LBM_EOS_CS = 0
+LBM_EOS_CS, LBM_EOS_VDW, LBM_EOS_RK, LBM_EOS_RKS, LBM_EOS_PR = range(5)
 LBM_PREC_FP64, LBM_PREC_MIXED, LBM_PREC_MIXED_DF = 0, 1, 2
 _PRECISIONS = {"fp64": LBM_PREC_FP64, "mixed": LBM_PREC_MIXED, "mixed_df": LBM_PREC_MIXED_DF}
 
@@ -123,6 +123,19 @@ def _check(status, what):
 def cs_eos(a=1.0, b=4.0, R=1.0):
     """Carnahan-Starling EOS parameters (Eq. 20; the paper's values by default)."""
     return LbmEos(LBM_EOS_CS, a, b, R, 0.0)
+
+
+# EOS kinds and the paper's a, b for each (Sec. 3.2)
+EOS_KINDS = {"cs": (LBM_EOS_CS, 1.0, 4.0), "vdw": (LBM_EOS_VDW, 9 / 49, 2 / 21),
+             "rk": (LBM_EOS_RK, 2 / 49, 2 / 21), "rks": (LBM_EOS_RKS, 2 / 49, 2 / 21),
+             "pr": (LBM_EOS_PR, 2 / 49, 2 / 21)}
+
+
+def make_eos(kind="cs", a=None, b=None, R=1.0, omega=0.0):
+    """EOS parameters by name ("cs", "vdw", "rk", "rks", "pr"); a and b default to
+    the paper's values, omega is the acentric factor of RKS and PR."""
+    k, a0, b0 = EOS_KINDS[kind]
+    return LbmEos(k, a0 if a is None else a, b0 if b is None else b, R, omega)
 
 
 def lbm_critical(eos=None):

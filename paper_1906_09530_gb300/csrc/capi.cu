@@ -253,17 +253,24 @@ size_t lbm_workspace_bytes(const lbm_grid* grid, const lbm_opts* opts) {
     return layout(grid->nx, grid->ny, opts->prec).total;
 }
 
+static bool eos_valid(const lbm_eos* eos) {
+    return eos && eos->kind >= LBM_EOS_CS && eos->kind <= LBM_EOS_PR && eos->a > 0 &&
+           eos->b > 0 && eos->R > 0 && std::isfinite(eos->omega);
+}
+
 lbm_status lbm_critical(const lbm_eos* eos, double* Tc, double* rhoc) {
-    if (!eos || eos->kind != LBM_EOS_CS || !Tc || !rhoc) return LBM_EINVAL;
-    return cs_critical(eos->a, eos->b, eos->R, Tc, rhoc) ? LBM_EINVAL : LBM_OK;
+    if (!eos_valid(eos) || !Tc || !rhoc) return LBM_EINVAL;
+    return eos_critical(eos->kind, eos->a, eos->b, eos->R, Tc, rhoc) ? LBM_EINVAL : LBM_OK;
 }
 
 lbm_status lbm_maxwell(const lbm_eos* eos, double T_r, double* rho_g, double* rho_l) {
-    if (!eos || eos->kind != LBM_EOS_CS || !rho_g || !rho_l) return LBM_EINVAL;
+    if (!eos_valid(eos) || !rho_g || !rho_l) return LBM_EINVAL;
     if (!(T_r > 0 && T_r < 1)) return LBM_EINVAL;
     double Tc, rc;
-    if (cs_critical(eos->a, eos->b, eos->R, &Tc, &rc)) return LBM_EINVAL;
-    return cs_maxwell(eos->a, eos->b, eos->R, T_r * Tc, rho_g, rho_l) ? LBM_EINVAL : LBM_OK;
+    if (eos_critical(eos->kind, eos->a, eos->b, eos->R, &Tc, &rc)) return LBM_EINVAL;
+    return eos_maxwell(eos->kind, eos->a, eos->b, eos->R, eos->omega, T_r * Tc, rho_g, rho_l)
+               ? LBM_EINVAL
+               : LBM_OK;
 }
 
 lbm_status lbm_init(lbm_ctx** out, const lbm_grid* grid, const lbm_eos* eos, double T_r,
@@ -273,15 +280,15 @@ lbm_status lbm_init(lbm_ctx** out, const lbm_grid* grid, const lbm_eos* eos, dou
     *out = nullptr;
     if (!grid_ok(grid) || !opts_ok(opts) || !eos) return LBM_EINVAL;
     if (!grid->periodic_x || !grid->periodic_y) return LBM_ENOTIMPL;
-    if (eos->kind != LBM_EOS_CS) return LBM_ENOTIMPL;
+    if (!eos_valid(eos)) return LBM_EINVAL;
     if (!(T_r > 0 && T_r < 1) || !(kappa > 0) || !(tau > 0.5) ||
-        !(mesh_coeff > 0 && mesh_coeff <= 1) || !(eos->a > 0 && eos->b > 0 && eos->R > 0))
+        !(mesh_coeff > 0 && mesh_coeff <= 1))
         return LBM_EINVAL;
     if (!d_workspace || ((uintptr_t)d_workspace % kAlign)) return LBM_EINVAL;
     const Layout L = layout(grid->nx, grid->ny, opts->prec);
     if (ws_bytes < L.total) return LBM_ENOMEM;
     double Tc, rc;
-    if (cs_critical(eos->a, eos->b, eos->R, &Tc, &rc)) return LBM_EINVAL;
+    if (eos_critical(eos->kind, eos->a, eos->b, eos->R, &Tc, &rc)) return LBM_EINVAL;
 
     lbm_ctx* c = new (std::nothrow) lbm_ctx();
     if (!c) return LBM_ENOMEM;
@@ -299,7 +306,8 @@ lbm_status lbm_init(lbm_ctx** out, const lbm_grid* grid, const lbm_eos* eos, dou
     c->rho_df = opts->prec == LBM_PREC_MIXED_DF;
     if (opts->prec == LBM_PREC_MIXED) {
         double rg, rl;
-        c->rho_df = cs_maxwell(eos->a, eos->b, eos->R, T_r * Tc, &rg, &rl) != 0 ||
+        c->rho_df = eos_maxwell(eos->kind, eos->a, eos->b, eos->R, eos->omega, T_r * Tc, &rg,
+                                &rl) != 0 ||
                     !(rl < kDfRatio * rg);
     }
     c->Tc = Tc;
@@ -310,6 +318,8 @@ lbm_status lbm_init(lbm_ctx** out, const lbm_grid* grid, const lbm_eos* eos, dou
     c->k = mesh_coeff;
     c->mu_max = opts->mu_max;
     c->mu_cap_steps = opts->mu_cap_steps;
+    c->phys.eos = eos->kind;
+    c->phys.alpha = eos_alpha(eos->kind, eos->a, eos->b, eos->R, eos->omega, c->T);
     c->phys.T = c->T;
     c->phys.a = eos->a;
     c->phys.b = eos->b;

@@ -366,10 +366,10 @@ lbm_status lbm_batch_init(lbm_batch** out, const lbm_instance* inst, int32_t n,
     *out = nullptr;
     if (!inst || n < 1 || !opts || !eos) return LBM_EINVAL;
     if (opts->fd_order != 4 && opts->fd_order != 6) return LBM_EINVAL;
-    if ((opts->prec != LBM_PREC_MIXED && opts->prec != LBM_PREC_MIXED_DF) ||
-        eos->kind != LBM_EOS_CS)
-        return LBM_ENOTIMPL;
-    if (!(eos->a > 0 && eos->b > 0 && eos->R > 0)) return LBM_EINVAL;
+    if (opts->prec != LBM_PREC_MIXED && opts->prec != LBM_PREC_MIXED_DF) return LBM_ENOTIMPL;
+    if (!(eos->kind >= LBM_EOS_CS && eos->kind <= LBM_EOS_PR && eos->a > 0 && eos->b > 0 &&
+          eos->R > 0 && std::isfinite(eos->omega)))
+        return LBM_EINVAL;
     for (int i = 0; i < n; ++i) {
         if (!inst[i].grid.periodic_x || !inst[i].grid.periodic_y) return LBM_ENOTIMPL;
         if (!instance_ok(inst[i])) return LBM_EINVAL;
@@ -379,7 +379,7 @@ lbm_status lbm_batch_init(lbm_batch** out, const lbm_instance* inst, int32_t n,
     if (need == 0) return LBM_EINVAL;
     if (ws_bytes < need) return LBM_ENOMEM;
     double Tc, rc;
-    if (cs_critical(eos->a, eos->b, eos->R, &Tc, &rc)) return LBM_EINVAL;
+    if (eos_critical(eos->kind, eos->a, eos->b, eos->R, &Tc, &rc)) return LBM_EINVAL;
 
     lbm_batch* b = new (std::nothrow) lbm_batch();
     if (!b) return LBM_ENOMEM;
@@ -420,7 +420,9 @@ lbm_status lbm_batch_init(lbm_batch** out, const lbm_instance* inst, int32_t n,
         for (int q = 0; q < 8; ++q) *slots[q] = fields + q * fs;
         h.partials = (double*)(base + r.parts_off);
         PhysParams& p = h.phys;
+        p.eos = eos->kind;
         p.T = in.T_r * Tc;
+        p.alpha = eos_alpha(eos->kind, eos->a, eos->b, eos->R, eos->omega, p.T);
         p.a = eos->a;
         p.b = eos->b;
         p.R = eos->R;
@@ -435,7 +437,8 @@ lbm_status lbm_batch_init(lbm_batch** out, const lbm_instance* inst, int32_t n,
         h.rho_df = opts->prec == LBM_PREC_MIXED_DF;
         if (!h.rho_df) {
             double rg, rl;
-            h.rho_df = cs_maxwell(eos->a, eos->b, eos->R, p.T, &rg, &rl) != 0 ||
+            h.rho_df = eos_maxwell(eos->kind, eos->a, eos->b, eos->R, eos->omega, p.T, &rg,
+                                   &rl) != 0 ||
                        !(rl < kDfRatio * rg);
         }
         o += r.total;

@@ -26,7 +26,9 @@ enum : unsigned int {
 
 // Physical parameters the kernels need.
 struct PhysParams {
-    double T, a, b, R;   // EOS (Eq. 20), T absolute
+    int eos;             // LBM_EOS_* (Sec. 3.2)
+    double alpha;        // alpha(T) of Eqs. 16-19 at this T (1 for CS and VDW)
+    double T, a, b, R;   // EOS constants, T absolute
     double k2;           // k^2 (Eq. 33)
     double kappa;        // kappa-hat (Eq. 33)
     double omega;        // 1 / tau (Eq. 1)
@@ -110,10 +112,33 @@ struct CsBatchInst {
 // FP32 constants of the chemical potential, converted on the host: FP64 -> FP32
 // conversions run on the FP64 pipe, which a per-thread conversion would make the
 // bottleneck of the pointwise kernel.
+template <class T>
+struct EosC {
+    int kind;   // LBM_EOS_*
+    T rt;       // R T
+    T a2;       // 2 a (CS, VDW)
+    T b;        // b (cubic EOSs) or b / 4 (CS)
+    T aal;      // a alpha(T) (RK, RKS, PR)
+    T clog;     // a alpha / b (RK, RKS) or a alpha / (2 sqrt 2 b) (PR)
+};
 struct MuConstF {
-    float T, a, b, R, k2, kappa, cap;
+    EosC<float> e;
+    float k2, kappa, cap;
     long long cap_steps;
 };
+// The EOS constants of PhysParams in arithmetic T (host).
+template <class T>
+EosC<T> eos_const(const PhysParams& p) {
+    EosC<T> c;
+    c.kind = p.eos;
+    c.rt = (T)(p.R * p.T);
+    c.a2 = (T)(2 * p.a);
+    c.b = (T)(p.eos == LBM_EOS_CS ? 0.25 * p.b : p.b);
+    c.aal = (T)(p.a * p.alpha);
+    c.clog = (T)(p.eos == LBM_EOS_PR ? p.a * p.alpha / (2 * 1.4142135623730951 * p.b)
+                                     : p.a * p.alpha / p.b);
+    return c;
+}
 constexpr int kMuBatchT = 256;  // threads per block of the batched mu-hat pass (4 nodes each)
 struct MuBatchInst {
     const float* rh;
@@ -195,8 +220,12 @@ cudaError_t launch_mu_mixed(const float* rh, float* dxx_mu, const float* dyy, in
 cudaError_t lines_mixed_plain(const float* uh, const float* ul, float* d1, float* d2, int nx,
                               int ny, int axis, int order, cudaStream_t s);
 
-// Host thermodynamics of the product library (independent of the oracle).
-int cs_critical(double a, double b, double R, double* Tc, double* rhoc);
-int cs_maxwell(double a, double b, double R, double T, double* rho_g, double* rho_l);
+// Host thermodynamics of the product library (independent of the oracle), for
+// the EOS kinds LBM_EOS_* (Sec. 3.2).  Return 0 or -1 (invalid arguments, or
+// T outside (0, T_c) for the Maxwell pair).
+int eos_critical(int kind, double a, double b, double R, double* Tc, double* rhoc);
+double eos_alpha(int kind, double a, double b, double R, double omega, double T);
+int eos_maxwell(int kind, double a, double b, double R, double omega, double T,
+                double* rho_g, double* rho_l);
 
 }  // namespace cplbm

@@ -36,6 +36,7 @@
 
 #include "cplbm_internal.cuh"
 #include "df.cuh"
+#include "eos.cuh"
 #include "lattice.cuh"
 
 namespace cplbm {
@@ -686,15 +687,17 @@ struct EpiStore {
     }
 };
 
-// mu-hat = k^2 mu0(rho) - kappa (d_xx + d_yy) rho, Eqs. 21 and 33, limited from
-// above while t < cap_steps (Sec. 5.6).  R is the arithmetic of the EOS.
+// mu-hat = k^2 mu0(rho) - kappa (d_xx + d_yy) rho, Eq. 33 with the mu0 of
+// Eqs. 15, 17, 19 or 21, limited from above while t < cap_steps (Sec. 5.6).  R
+// is the arithmetic of the EOS.
 template <class R, class O, class RhoT>
 struct EpiMu {
     O* dyr;
     O* mu;
     const RhoT* __restrict__ rho;
     const O* __restrict__ dxx;
-    R T, a, b, Rg, k2, kappa, cap;
+    EosC<R> e;
+    R k2, kappa, cap;
     int64_t cap_steps;
     bool capped;
     struct Ops {
@@ -709,14 +712,12 @@ struct EpiMu {
     __device__ __forceinline__ Ops fetch(size_t o) const { return Ops{__ldg(rho + o), __ldg(dxx + o)}; }
     __device__ __forceinline__ bool operator()(size_t o, O d1, O d2, const Ops& op) {
         dyr[o] = d1;
-        const R r = (R)op.r;
-        const R eta = R(0.25) * b * r;
-        const R om = R(1) - eta;
-        const R mu0 = Rg * T * ((R(3) - eta) / (om * om * om) + log(r) + R(1)) - R(2) * a * r;
-        R m = k2 * mu0 - kappa * ((R)op.xx + (R)d2);
+        bool bad = false;
+        const R mu0 = eos_mu0(e, (R)op.r, bad);
+        R m = rn_fma(k2, mu0, -rn_mul(kappa, rn_add((R)op.xx, (R)d2)));
         if (capped) m = m < cap ? m : cap;
         mu[o] = (O)m;
-        return !(r > R(0) && eta < R(1) && m > -R(1e30) && m < R(1e30));
+        return bad || !(m > -R(1e30) && m < R(1e30));
     }
 };
 
@@ -940,7 +941,7 @@ cudaError_t lines_fp64_rho_x(const double* rho, double* dxr, double* dxx, int nx
 cudaError_t lines_fp64_rho_y_mu(const double* rho, const double* dxx, double* dyr, double* mu,
                                 int nx, int ny, int order, const PhysParams& p, DevState* st,
                                 cudaStream_t s) {
-    EpiMu<double, double, double> epi{dyr, mu, rho, dxx, p.T, p.a, p.b, p.R, p.k2, p.kappa,
+    EpiMu<double, double, double> epi{dyr, mu, rho, dxx, eos_const<double>(p), p.k2, p.kappa,
                                       p.mu_cap, p.cap_steps, false};
     return launch_lines<PolD, PolD, true>(InD{rho}, nx, ny, 1, order, kEpsD, kEpsD, epi, st, 0, s);
 }

@@ -25,6 +25,7 @@
 
 #include "cplbm_internal.cuh"
 #include "df.cuh"
+#include "eos.cuh"
 #include "lattice.cuh"
 
 namespace cplbm {
@@ -198,23 +199,17 @@ __global__ void k_macro_mixed(const float* __restrict__ f, const float* __restri
 }
 
 // Chemical potential of the mixed path, pointwise after the line solves of rho:
-// mu-hat = k^2 mu0(rho) - kappa (d_xx + d_yy) rho (Eqs. 21, 33) in FP32, limited
+// mu-hat = k^2 mu0(rho) - kappa (d_xx + d_yy) rho (Eq. 33 with the mu0 of
+// Eqs. 15, 17, 19 or 21) in FP32, limited
 // from above while the time level t < cap_steps (Sec. 5.6; t read on the device
 // so that graph replays stay correct).  Written over d_xx rho, which nothing
 // needs afterwards.
 __device__ __forceinline__ float mu_node(float r, float xx, float yy, const MuConstF& p,
                                          bool capped, bool& bad) {
-    // explicit rounding: the body is inlined in the lone and batched kernels
-    const float eta = rn_mul(rn_mul(0.25f, p.b), r);
-    const float om = rn_sub(1.0f, eta);
-    const float rt = rn_mul(p.R, p.T);
-    const float cs = rn_add(rn_add(rn_div(rn_sub(3.0f, eta), rn_mul(rn_mul(om, om), om)),
-                                   logf(r)),
-                            1.0f);
-    const float mu0 = rn_fma(rt, cs, -rn_mul(rn_mul(2.0f, p.a), r));
+    const float mu0 = eos_mu0(p.e, r, bad);
     float m = rn_fma(p.k2, mu0, -rn_mul(p.kappa, rn_add(xx, yy)));
     if (capped) m = fminf(m, p.cap);
-    bad |= !(r > 0.0f && eta < 1.0f && fabsf(m) < 1e30f);
+    bad |= !(fabsf(m) < 1e30f);
     return m;
 }
 
@@ -374,8 +369,8 @@ cudaError_t launch_macro_mixed(const float* f, const float* rh, const float* rl,
 }
 
 MuConstF mu_mixed_const(const PhysParams& p) {
-    return MuConstF{(float)p.T, (float)p.a, (float)p.b, (float)p.R, (float)p.k2,
-                    (float)p.kappa, (float)fmin(p.mu_cap, (double)FLT_MAX), p.cap_steps};
+    return MuConstF{eos_const<float>(p), (float)p.k2, (float)p.kappa,
+                    (float)fmin(p.mu_cap, (double)FLT_MAX), p.cap_steps};
 }
 
 cudaError_t launch_mu_mixed(const float* rh, float* dxx_mu, const float* dyy, int nx, int ny,

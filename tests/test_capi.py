@@ -49,6 +49,27 @@ def test_maxwell_agrees_with_oracle(T_r):
     assert g == pytest.approx(og, rel=1e-9)
 
 
+@pytest.mark.parametrize("kind", ["vdw", "rk", "rks", "pr", "cs"])
+def test_other_eos_thermodynamics_agree_with_oracle(kind):
+    """The library's critical point (maximum of the closed-form spinodal
+    temperature, refined on B'A'' = B''A') and Maxwell pair (nested bisection)
+    against the oracle's generic solver (brentq on the spinodal, bounded
+    maximisation, brentq on log p_sat)."""
+    from oracle import eos as E
+    omega = 0.344 if kind in ("rks", "pr") else 0.0
+    e = P.make_eos(kind, omega=omega)
+    o = E.Eos(kind, omega=omega)
+    tc, rc = P.lbm_critical(e)
+    otc, orc = o.critical_point()
+    assert tc == pytest.approx(otc, rel=1e-12)
+    assert rc == pytest.approx(orc, rel=1e-7)
+    for t_r in (0.9, 0.7, 0.5, 0.35):
+        g, l = P.lbm_maxwell(t_r, e)
+        og, ol = o.maxwell(t_r)
+        assert l == pytest.approx(ol, rel=1e-11)
+        assert g == pytest.approx(og, rel=1e-9)
+
+
 def test_workspace_bytes_validation():
     assert P.lbm_workspace_bytes(1024, 1024, P.LBM_PREC_MIXED, 6) > 9 * 1024 * 1024 * 4 * 2
     assert P.lbm_workspace_bytes(1024, 1024, P.LBM_PREC_FP64, 6) > 9 * 1024 * 1024 * 8 * 2
