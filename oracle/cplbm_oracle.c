@@ -47,6 +47,8 @@ typedef struct {
     int64_t mu_cap_steps;   /* the limit acts while the time level t < mu_cap_steps */
     int32_t eos;            /* EOS kind, see the header comment (0: CS) */
     double eos_alpha;       /* alpha(T) of Eqs. 16-19 */
+    int32_t mrt;            /* 0: BGK collision (Eq. 1); 1: MRT collision (Eq. 4) */
+    double s[9];            /* MRT relaxation rates, the diagonal of S in Eq. 4 */
 } orc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -284,6 +286,72 @@ int orc_force_stage(const orc_params *p, int64_t t, const double *rho, double *m
     return err ? -1 : 0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* MRT collision, Eq. 4                                                      */
+/* ------------------------------------------------------------------------ */
+
+/* The D2Q9 moment basis of the MRT model the paper cites (Lallemand and Luo):
+ * rows rho, e, epsilon, j_x, q_x, j_y, q_y, p_xx, p_xy over the velocity order
+ * of Sec. 2.  The paper does not print M; this is the standard basis its S =
+ * diag(0, s_e, s_eps, 0, s_q, 0, s_q, s_v, s_v) is written for. */
+static const double MRT_M[9][9] = {
+    {1, 1, 1, 1, 1, 1, 1, 1, 1},
+    {-4, -1, -1, -1, -1, 2, 2, 2, 2},
+    {4, -2, -2, -2, -2, 1, 1, 1, 1},
+    {0, 1, 0, -1, 0, 1, -1, -1, 1},
+    {0, -2, 0, 2, 0, 1, -1, -1, 1},
+    {0, 0, 1, 0, -1, 1, 1, -1, -1},
+    {0, 0, -2, 0, 2, 1, 1, -1, -1},
+    {0, 1, -1, 1, -1, 0, 0, 0, 0},
+    {0, 0, 0, 0, 0, 1, -1, 1, -1}};
+
+/* Inverse of a 9 x 9 matrix by Gauss-Jordan elimination with partial pivoting. */
+static int invert9(const double a_in[9][9], double inv[9][9])
+{
+    double a[9][18];
+    for (int i = 0; i < 9; ++i)
+        for (int j = 0; j < 18; ++j)
+            a[i][j] = j < 9 ? a_in[i][j] : (j - 9 == i ? 1.0 : 0.0);
+    for (int c = 0; c < 9; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < 9; ++r)
+            if (fabs(a[r][c]) > fabs(a[piv][c]))
+                piv = r;
+        if (a[piv][c] == 0.0)
+            return -1;
+        for (int j = 0; j < 18; ++j) {
+            double t = a[c][j];
+            a[c][j] = a[piv][j];
+            a[piv][j] = t;
+        }
+        double d = a[c][c];
+        for (int j = 0; j < 18; ++j)
+            a[c][j] /= d;
+        for (int r = 0; r < 9; ++r)
+            if (r != c) {
+                double m = a[r][c];
+                for (int j = 0; j < 18; ++j)
+                    a[r][j] -= m * a[c][j];
+            }
+    }
+    for (int i = 0; i < 9; ++i)
+        for (int j = 0; j < 9; ++j)
+            inv[i][j] = a[i][9 + j];
+    return 0;
+}
+
+/* Exported for the tests: M and its inverse. */
+void orc_mrt_matrices(double *m_out, double *minv_out)
+{
+    double inv[9][9];
+    invert9(MRT_M, inv);
+    for (int i = 0; i < 9; ++i)
+        for (int j = 0; j < 9; ++j) {
+            m_out[9 * i + j] = MRT_M[i][j];
+            minv_out[9 * i + j] = inv[i][j];
+        }
+}
+
 /* Advance the post-streaming populations f (time level t0) by nsteps steps:
  * moments (Eq. 3), force stage, BGK collision with exact-difference forcing
  * (Eqs. 1, 2, 5), then streaming f_i(x + e_i, t + 1) = f_i*(x, t) on the
@@ -298,17 +366,39 @@ int orc_run(const orc_params *p, double *f, int64_t t0, int64_t nsteps)
     double *rho = buf, *ux = buf + N, *uy = buf + 2 * N, *Fx = buf + 3 * N,
            *Fy = buf + 4 * N, *fs = buf + 5 * N;
     int err = 0;
+    double minv[9][9];
+    if (p->mrt && invert9(MRT_M, minv))
+        err = 1;
     for (int64_t s = 0; s < nsteps && !err; ++s) {
         int64_t t = t0 + s;
         moments(p, f, rho, ux, uy);
         err |= orc_force_stage(p, t, rho, NULL, Fx, Fy);
-        /* collision, Eq. 1 right-hand side */
+        /* collision: the right-hand side of Eq. 1 (BGK) or Eq. 4 (MRT,
+         * f* = f - M^-1 S M (f - f^eq) + F_i) */
         for (size_t n = 0; n < N; ++n) {
             double Fi[9];
             orc_forcing_terms(rho[n], ux[n], uy[n], Fx[n], Fy[n], Fi);
+            if (!p->mrt) {
+                for (int i = 0; i < 9; ++i) {
+                    double fi = f[i * N + n];
+                    fs[i * N + n] = fi - (fi - feq(i, rho[n], ux[n], uy[n])) / p->tau + Fi[i];
+                }
+                continue;
+            }
+            double dev[9], m[9];
+            for (int i = 0; i < 9; ++i)
+                dev[i] = f[i * N + n] - feq(i, rho[n], ux[n], uy[n]);
+            for (int r = 0; r < 9; ++r) {
+                m[r] = 0.0;
+                for (int i = 0; i < 9; ++i)
+                    m[r] += MRT_M[r][i] * dev[i];
+                m[r] *= p->s[r];
+            }
             for (int i = 0; i < 9; ++i) {
-                double fi = f[i * N + n];
-                fs[i * N + n] = fi - (fi - feq(i, rho[n], ux[n], uy[n])) / p->tau + Fi[i];
+                double d = 0.0;
+                for (int r = 0; r < 9; ++r)
+                    d += minv[i][r] * m[r];
+                fs[i * N + n] = f[i * N + n] - d + Fi[i];
             }
         }
         /* streaming, Eq. 1 left-hand side, periodic in x and y */

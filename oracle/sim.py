@@ -23,7 +23,11 @@ class OrcParams(C.Structure):
                 ("kappa", C.c_double), ("tau", C.c_double), ("k", C.c_double),
                 ("alpha", C.c_double),
                 ("mu_max", C.c_double), ("mu_cap_steps", C.c_int64),
-                ("eos", C.c_int32), ("eos_alpha", C.c_double)]
+                ("eos", C.c_int32), ("eos_alpha", C.c_double),
+                ("mrt", C.c_int32), ("s", C.c_double * 9)]
+
+# MRT relaxation rates of Sec. 2 (after Eq. 4): s_e, s_eps, s_q; s_v = 1/tau
+PAPER_MRT = (1.64, 1.54, 1.9)
 
 # EOS kinds of the C oracle (its header comment)
 EOS_KIND = {"cs": 0, "vdw": 1, "rk": 2, "rks": 3, "pr": 4}
@@ -38,6 +42,8 @@ def lib():
         L.orc_cs_p0.argtypes = [C.c_double] * 5
         L.orc_cs_mu0.restype = C.c_double
         L.orc_cs_mu0.argtypes = [C.c_double] * 5
+        L.orc_mrt_matrices.restype = None
+        L.orc_mrt_matrices.argtypes = [dp, dp]
         L.orc_p0.restype = C.c_double
         L.orc_p0.argtypes = [C.c_int] + [C.c_double] * 6
         L.orc_mu0.restype = C.c_double
@@ -81,6 +87,13 @@ def eos_mu0(kind, rho, T, a, b, R, alpha):
     return lib().orc_mu0(EOS_KIND[kind], rho, T, a, b, R, alpha)
 
 
+def mrt_matrices():
+    """(M, M^-1) of the C oracle's MRT collision, 9 x 9 arrays."""
+    m, mi = np.zeros((9, 9)), np.zeros((9, 9))
+    lib().orc_mrt_matrices(_ptr(m), _ptr(mi))
+    return m, mi
+
+
 def cs_mu0(rho, T, a=1.0, b=4.0, R=1.0):
     """Carnahan-Starling chemical potential without the gradient term, Eq. 21."""
     return lib().orc_cs_mu0(rho, T, a, b, R)
@@ -116,14 +129,22 @@ class OracleSim:
     """One periodic D2Q9 simulation advanced by the C oracle, FP64."""
 
     def __init__(self, nx, ny, T, kappa, tau, k, fd_order, mu_max=math.inf,
-                 mu_cap_steps=0, a=1.0, b=4.0, R=1.0, eos=None):
+                 mu_cap_steps=0, a=1.0, b=4.0, R=1.0, eos=None, mrt=None):
         """`eos`: an oracle.eos.Eos (its kind, a, b, R and alpha(T) replace the
-        Carnahan-Starling defaults)."""
+        Carnahan-Starling defaults).  `mrt`: None for BGK (Eq. 1), else the rates
+        (s_e, s_eps, s_q) of the MRT collision (Eq. 4), with s_v = 1/tau and the
+        conserved moments' rates 0."""
         kind, al = 0, 1.0
         if eos is not None:
             kind, a, b, R, al = EOS_KIND[eos.kind], eos.a, eos.b, eos.R, eos.alpha(T)
         self.p = OrcParams(nx, ny, T, a, b, R, kappa, tau, k, cfd_alpha(fd_order),
                            mu_max, mu_cap_steps, kind, al)
+        if mrt is not None:
+            se, seps, sq = mrt
+            sv = 1.0 / tau
+            self.p.mrt = 1
+            for i, v in enumerate((0.0, se, seps, 0.0, sq, 0.0, sq, sv, sv)):
+                self.p.s[i] = v
         self.nx, self.ny = nx, ny
         self.t = 0
         self.f = np.zeros((9, ny, nx))

@@ -108,7 +108,7 @@ def test_batch_coexistence(cuda, kind):
     """Sec. 5.1 / Fig. 4 for the other EOSs: flat interfaces (height 400, k = 0.1,
     kappa-hat = 0.005) at T_r = 0.6 and 0.8, run as one batch for 150 000 steps.
     Liquid within 1e-4 of Maxwell.  The gas sits above Maxwell by the scheme's
-    offset, as for CS, and is bounded by 5%.  Measured at 200 000 steps: +1.4% to
+    offset, as for CS, and is bounded by 5%.  Measured at 200 000 steps: +0.4% to
     +1.8% at 0.6, +2e-4 to +2e-3 at 0.8 (VDW the least, PR the most), and the mixed
     path agrees with FP64 within 2e-4."""
     from paper_1906_09530_gb300 import Batch
