@@ -81,12 +81,21 @@ typedef struct {
                               (all > 0); omega: acentric factor (RKS and PR only) */
 } lbm_eos;
 
+/* Collision.  BGK: Eq. 1 (single relaxation time tau).  MRT: Eq. 4 on the
+ * standard D2Q9 moment basis (rho, e, epsilon, j_x, q_x, j_y, q_y, p_xx, p_xy),
+ * S = diag(0, s_e, s_eps, 0, s_q, 0, s_q, s_v, s_v) with s_v = 1/tau; the paper
+ * uses s_e = 1.64, s_eps = 1.54, s_q = 1.9.  Both with the exact-difference
+ * forcing of Eq. 5. */
+enum { LBM_COLLIDE_BGK = 0, LBM_COLLIDE_MRT = 1 };
+
 typedef struct {
-    int32_t prec;         /* LBM_PREC_FP64 or LBM_PREC_MIXED */
+    int32_t prec;         /* LBM_PREC_FP64, LBM_PREC_MIXED or LBM_PREC_MIXED_DF */
     int32_t fd_order;     /* 4 (alpha = 1/4) or 6 (alpha = 1/3, Eq. 39) */
     double mu_max;        /* chemical-potential upper limit in momentum-space
                              units (Sec. 5.6); +INFINITY switches it off */
     int64_t mu_cap_steps; /* the limit acts while the time level t < mu_cap_steps */
+    int32_t collision;    /* LBM_COLLIDE_BGK (0) or LBM_COLLIDE_MRT */
+    double s_e, s_eps, s_q; /* MRT rates, each in (0, 2); unused by BGK */
 } lbm_opts;
 
 /* Bytes of device workspace lbm_init needs for this grid and options, or 0

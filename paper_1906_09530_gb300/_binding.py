@@ -31,7 +31,23 @@ class LbmEos(C.Structure):
 
 class LbmOpts(C.Structure):
     _fields_ = [("prec", C.c_int32), ("fd_order", C.c_int32), ("mu_max", C.c_double),
-                ("mu_cap_steps", C.c_int64)]
+                ("mu_cap_steps", C.c_int64), ("collision", C.c_int32), ("s_e", C.c_double),
+                ("s_eps", C.c_double), ("s_q", C.c_double)]
+
+
+LBM_COLLIDE_BGK, LBM_COLLIDE_MRT = 0, 1
+# MRT rates s_e, s_eps, s_q of Sec. 2 (after Eq. 4); s_v = 1/tau
+PAPER_MRT = (1.64, 1.54, 1.9)
+
+
+def _opts(prec, fd_order, mu_max, mu_cap_steps, collision, mrt_rates):
+    if collision not in ("bgk", "mrt"):
+        raise ValueError(collision)
+    o = LbmOpts(prec, fd_order, mu_max, mu_cap_steps)
+    if collision == "mrt":
+        o.collision = LBM_COLLIDE_MRT
+        o.s_e, o.s_eps, o.s_q = mrt_rates
+    return o
 
 
 class LbmInstance(C.Structure):
@@ -215,13 +231,13 @@ class Simulation:
 
     def __init__(self, nx, ny, T_r, kappa, tau, mesh_coeff, fd_order=6,
                  precision="fp64", mu_max=math.inf, mu_cap_steps=0, eos=None,
-                 device=None, stream=None):
+                 device=None, stream=None, collision="bgk", mrt_rates=PAPER_MRT):
         import torch
         self.nx, self.ny = nx, ny
         self.device = torch.device(device if device is not None else "cuda")
         prec = _PRECISIONS[precision]
         self.grid = LbmGrid(nx, ny, 1, 1)
-        self.opts = LbmOpts(prec, fd_order, mu_max, mu_cap_steps)
+        self.opts = _opts(prec, fd_order, mu_max, mu_cap_steps, collision, mrt_rates)
         self.eos = eos or cs_eos()
         nbytes = lib().lbm_workspace_bytes(C.byref(self.grid), C.byref(self.opts))
         if nbytes == 0:
@@ -328,7 +344,7 @@ class Batch:
     """
 
     def __init__(self, instances, fd_order=6, precision="mixed", eos=None, device=None,
-                 stream=None):
+                 stream=None, collision="bgk", mrt_rates=PAPER_MRT):
         import torch
         self.n = len(instances)
         arr = (LbmInstance * self.n)()
@@ -339,7 +355,7 @@ class Batch:
                                  d.get("mu_max", math.inf), d.get("mu_cap_steps", 0))
             self.shapes.append((d["ny"], d["nx"]))
         self._inst = arr
-        self.opts = LbmOpts(_PRECISIONS[precision], fd_order, math.inf, 0)
+        self.opts = _opts(_PRECISIONS[precision], fd_order, math.inf, 0, collision, mrt_rates)
         self.eos = eos or cs_eos()
         nbytes = lib().lbm_batch_workspace_bytes(arr, self.n, C.byref(self.opts))
         if nbytes == 0:

@@ -32,6 +32,8 @@ struct lbm_ctx {
     size_t N, plane;
     int prec, fd_order;
     bool rho_df;  // mixed: density lines in double-float (else FP32)
+    bool mrt;     // MRT collision (Eq. 4) with the rates below
+    MrtRates rates;
     double T, Tc, rhoc, kappa, tau, k;
     double mu_max;
     int64_t mu_cap_steps;
@@ -71,10 +73,14 @@ struct Layout {
 };
 
 bool grid_ok(const lbm_grid* g) { return g && g->nx >= 8 && g->ny >= 8; }
+bool rate_ok(double s) { return s > 0 && s < 2; }
 bool opts_ok(const lbm_opts* o) {
     return o &&
            (o->prec == LBM_PREC_FP64 || o->prec == LBM_PREC_MIXED ||
             o->prec == LBM_PREC_MIXED_DF) &&
+           (o->collision == LBM_COLLIDE_BGK ||
+            (o->collision == LBM_COLLIDE_MRT && rate_ok(o->s_e) && rate_ok(o->s_eps) &&
+             rate_ok(o->s_q))) &&
            (o->fd_order == 4 || o->fd_order == 6) && !std::isnan(o->mu_max);
 }
 
@@ -148,10 +154,12 @@ lbm_status enqueue_collide(lbm_ctx* c, cudaStream_t s, int from) {
     if (is_fp64(c))
         CK(launch_collide_stream<double>((const double*)c->f[from], (double*)c->f[to], c->Fx,
                                          c->Fy, c->rho, c->nx, c->ny, c->plane,
-                                         c->phys.omega, c->dst, s));
+                                         c->phys.omega, c->mrt ? &c->rates : nullptr, c->dst,
+                                         s));
     else
         CK(launch_cs_mixed((const float*)c->f[from], (float*)c->f[to], c->m_Fx, c->m_Fy,
-                           c->m_rh, c->m_rl, c->nx, c->ny, c->plane, c->phys.omega, c->dst, s));
+                           c->m_rh, c->m_rl, c->nx, c->ny, c->plane, c->phys.omega,
+                           c->mrt ? &c->rates : nullptr, c->dst, s));
     return LBM_OK;
 }
 
@@ -304,6 +312,8 @@ lbm_status lbm_init(lbm_ctx** out, const lbm_grid* grid, const lbm_eos* eos, dou
     c->prec = opts->prec;
     c->fd_order = opts->fd_order;
     c->rho_df = opts->prec == LBM_PREC_MIXED_DF;
+    c->mrt = opts->collision == LBM_COLLIDE_MRT;
+    c->rates = MrtRates{opts->s_e, opts->s_eps, opts->s_q};
     if (opts->prec == LBM_PREC_MIXED) {
         double rg, rl;
         c->rho_df = eos_maxwell(eos->kind, eos->a, eos->b, eos->R, eos->omega, T_r * Tc, &rg,

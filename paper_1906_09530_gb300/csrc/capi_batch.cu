@@ -65,7 +65,7 @@ Region region(int nx, int ny) {
 // Block counts of each pass for one instance.
 int cs_blocks_for(int nx, int ny, int rows) {
     return cs_mixed_blocks(cs_mixed_args(nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-                                         nx, ny, 0, 1.0, nullptr, rows));
+                                         nx, ny, 0, 1.0, nullptr, nullptr, rows));
 }
 int mu_blocks_for(size_t N) { return (int)(((N + 3) / 4 + kMuBatchT - 1) / kMuBatchT); }
 
@@ -128,6 +128,8 @@ bool instance_ok(const lbm_instance& in) {
 
 struct lbm_batch {
     int dev, n, order;
+    bool mrt;  // MRT collision (Eq. 4) for every instance
+    MrtRates rates;
     cudaStream_t stream, cap_stream;
     cudaEvent_t ev, tev[5];
     char* ws;
@@ -189,7 +191,7 @@ lbm_status upload_tables(lbm_batch* b) {
         DevState* st = b->dst + i;
         CsBatchInst c;
         c.a = cs_mixed_args(h.f[0], h.f[1], h.Fx, h.Fy, h.rh, h.rl, h.nx, h.ny, h.plane,
-                            h.phys.omega, st, h.rows);
+                            h.phys.omega, b->mrt ? &b->rates : nullptr, st, h.rows);
         c.f[0] = h.f[0];
         c.f[1] = h.f[1];
         c.blk0 = (int)mcs.size();
@@ -247,7 +249,8 @@ const T* at(const lbm_batch* b, size_t off) {
 lbm_status enqueue_step(lbm_batch* b, cudaStream_t s, int from, cudaEvent_t* ev = nullptr) {
     const Tables& t = b->tb;
     auto mark = [&](int i) { return ev ? cudaEventRecord(ev[i], s) : cudaSuccess; };
-    CK(launch_cs_mixed_batch(at<CsBatchInst>(b, t.cs), at<int>(b, t.map_cs), t.nb_cs, from, s));
+    CK(launch_cs_mixed_batch(at<CsBatchInst>(b, t.cs), at<int>(b, t.map_cs), t.nb_cs, from,
+                             b->mrt, s));
     CK(mark(1));
     // every instance is in exactly one of the two density launches
     CK(lines_batch_launch(LineBatchKind::kRhoF32, b->ws + t.rho_f32, at<int>(b, t.map_rho_f32),
@@ -367,6 +370,11 @@ lbm_status lbm_batch_init(lbm_batch** out, const lbm_instance* inst, int32_t n,
     if (!inst || n < 1 || !opts || !eos) return LBM_EINVAL;
     if (opts->fd_order != 4 && opts->fd_order != 6) return LBM_EINVAL;
     if (opts->prec != LBM_PREC_MIXED && opts->prec != LBM_PREC_MIXED_DF) return LBM_ENOTIMPL;
+    auto rate_ok = [](double r) { return r > 0 && r < 2; };
+    if (!(opts->collision == LBM_COLLIDE_BGK ||
+          (opts->collision == LBM_COLLIDE_MRT && rate_ok(opts->s_e) && rate_ok(opts->s_eps) &&
+           rate_ok(opts->s_q))))
+        return LBM_EINVAL;
     if (!(eos->kind >= LBM_EOS_CS && eos->kind <= LBM_EOS_PR && eos->a > 0 && eos->b > 0 &&
           eos->R > 0 && std::isfinite(eos->omega)))
         return LBM_EINVAL;
@@ -385,6 +393,8 @@ lbm_status lbm_batch_init(lbm_batch** out, const lbm_instance* inst, int32_t n,
     if (!b) return LBM_ENOMEM;
     b->n = n;
     b->order = opts->fd_order;
+    b->mrt = opts->collision == LBM_COLLIDE_MRT;
+    b->rates = MrtRates{opts->s_e, opts->s_eps, opts->s_q};
     b->stream = (cudaStream_t)cuda_stream;
     b->ws = (char*)d_workspace;
     b->timeout_s = 600.0;
@@ -499,7 +509,7 @@ int32_t lbm_batch_tile_rows(const lbm_batch* b, int32_t i) {
     if (!b || i < 0 || i >= b->n) return -1;
     const InstHost& h = b->inst[i];
     return cs_mixed_args(nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, h.nx, h.ny, 0,
-                         1.0, nullptr, h.rows)
+                         1.0, nullptr, nullptr, h.rows)
         .rows;
 }
 
@@ -631,8 +641,9 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int32_t reps) {
         float best = 0.0f;
         int best_rows = 0;
         for (int rows : kRowChoices) {
-            const CsArgs a = cs_mixed_args(h.f[b->cur], h.f[1 - b->cur], h.Fx, h.Fy, h.rh, h.rl,
-                                           h.nx, h.ny, h.plane, h.phys.omega, dst, rows);
+            const CsArgs a =
+                cs_mixed_args(h.f[b->cur], h.f[1 - b->cur], h.Fx, h.Fy, h.rh, h.rl, h.nx, h.ny,
+                              h.plane, h.phys.omega, b->mrt ? &b->rates : nullptr, dst, rows);
             CK(launch_cs_mixed_args(a, s));  // warm-up
             CK(cudaEventRecord(b->tev[0], s));
             for (int r = 0; r < reps; ++r) CK(launch_cs_mixed_args(a, s));

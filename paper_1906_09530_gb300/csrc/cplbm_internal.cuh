@@ -36,12 +36,17 @@ struct PhysParams {
     int64_t cap_steps;   // limit active while t < cap_steps
 };
 
+// MRT relaxation rates of Eq. 4 other than s_v = 1/tau (NULL pointer: BGK).
+struct MrtRates {
+    double se, seps, sq;
+};
+
 // Launchers (all asynchronous on `s`).  Fields are FP64 [ny][nx]; populations
 // are [9][plane] of TF with plane >= nx*ny.
 template <typename TF>
 cudaError_t launch_collide_stream(const TF* fin, TF* fout, const double* Fx, const double* Fy,
                                   double* rho_out, int nx, int ny, size_t plane, double omega,
-                                  DevState* st, cudaStream_t s);
+                                  const MrtRates* mrt, DevState* st, cudaStream_t s);
 
 template <typename TF>
 cudaError_t launch_init_feq(const double* rho, const double* ux, const double* uy, TF* f,
@@ -70,7 +75,7 @@ cudaError_t launch_diag_final(const double* partials, int nparts, DevState* st, 
 // ---- mixed precision path (kernels_mixed.cu) ------------------------------
 cudaError_t launch_cs_mixed(const float* fin, float* fout, const float* Fx, const float* Fy,
                             float* rh, float* rl, int nx, int ny, size_t plane, double omega,
-                            DevState* st, cudaStream_t s);
+                            const MrtRates* mrt, DevState* st, cudaStream_t s);
 cudaError_t launch_init_mixed(const double* rho, const double* ux, const double* uy, float* f,
                               float* rh, float* rl, int nx, int ny, size_t plane,
                               cudaStream_t s);
@@ -103,6 +108,8 @@ struct CsArgs {
     float omega;
     int nstrips, nseg, rows;  // warp strips of 30 columns x `rows` rows
     DevState* st;
+    int mrt;                  // 0: BGK (Eq. 1); 1: MRT (Eq. 4) with the rates below
+    float se, seps, sq;
 };
 struct CsBatchInst {
     CsArgs a;      // fin / fout are taken from f[] by the launch's `from`
@@ -161,11 +168,12 @@ struct MixedLinesView {
 
 CsArgs cs_mixed_args(const float* fin, float* fout, const float* Fx, const float* Fy,
                      float* rh, float* rl, int nx, int ny, size_t plane, double omega,
-                     DevState* st, int rows);  // rows <= 0: the default choice
+                     const MrtRates* mrt, DevState* st,
+                     int rows);  // rows <= 0: the default choice
 int cs_mixed_blocks(const CsArgs& a);
 cudaError_t launch_cs_mixed_args(const CsArgs& a, cudaStream_t s);
 cudaError_t launch_cs_mixed_batch(const CsBatchInst* d, const int* map, int nblocks, int from,
-                                  cudaStream_t s);
+                                  bool mrt, cudaStream_t s);
 MuConstF mu_mixed_const(const PhysParams& p);
 cudaError_t launch_mu_mixed_batch(const MuBatchInst* d, const int* map, int nblocks,
                                   cudaStream_t s);

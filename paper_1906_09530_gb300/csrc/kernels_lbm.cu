@@ -53,12 +53,12 @@ __device__ __forceinline__ void raise_flag(DevState* st, unsigned bits, int64_t 
 // then every destination node gathers f_i*(x - e_i) from shared memory, writes
 // its nine populations once (coalesced, aligned) and its new density.
 // ---------------------------------------------------------------------------
-template <typename TF, int BX, int BY>
+template <typename TF, int BX, int BY, bool MRT>
 __global__ void __launch_bounds__(BX* BY)
     k_collide_stream(const TF* __restrict__ fin, TF* __restrict__ fout,
                      const double* __restrict__ Fx, const double* __restrict__ Fy,
                      double* __restrict__ rho_out, int nx, int ny, size_t plane, TF omega,
-                     DevState* __restrict__ st) {
+                     TF se, TF seps, TF sq, DevState* __restrict__ st) {
     constexpr int HX = BX + 2, HY = BY + 2, HN = HX * HY;
     __shared__ TF sf[9][HN];
     const int tid = threadIdx.x + BX * threadIdx.y;
@@ -71,7 +71,10 @@ __global__ void __launch_bounds__(BX* BY)
         TF f[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i] = fin[i * plane + n];
-        ok &= collide_pairs<TF>(f, (TF)Fx[n], (TF)Fy[n], omega, (TF)FLT_MAX);
+        if constexpr (MRT)
+            ok &= collide_mrt<TF>(f, (TF)Fx[n], (TF)Fy[n], omega, (TF)FLT_MAX, se, seps, sq);
+        else
+            ok &= collide_pairs<TF>(f, (TF)Fx[n], (TF)Fy[n], omega, (TF)FLT_MAX);
 #pragma unroll
         for (int i = 0; i < 9; ++i) sf[i][k] = f[i];
     }
@@ -247,11 +250,16 @@ constexpr int kCsBX = 32, kCsBY = 16;
 template <typename TF>
 cudaError_t launch_collide_stream(const TF* fin, TF* fout, const double* Fx, const double* Fy,
                                   double* rho_out, int nx, int ny, size_t plane, double omega,
-                                  DevState* st, cudaStream_t s) {
+                                  const MrtRates* mrt, DevState* st, cudaStream_t s) {
     dim3 block(kCsBX, kCsBY);
     dim3 grid((nx + kCsBX - 1) / kCsBX, (ny + kCsBY - 1) / kCsBY);
-    k_collide_stream<TF, kCsBX, kCsBY>
-        <<<grid, block, 0, s>>>(fin, fout, Fx, Fy, rho_out, nx, ny, plane, (TF)omega, st);
+    if (mrt)
+        k_collide_stream<TF, kCsBX, kCsBY, true><<<grid, block, 0, s>>>(
+            fin, fout, Fx, Fy, rho_out, nx, ny, plane, (TF)omega, (TF)mrt->se, (TF)mrt->seps,
+            (TF)mrt->sq, st);
+    else
+        k_collide_stream<TF, kCsBX, kCsBY, false><<<grid, block, 0, s>>>(
+            fin, fout, Fx, Fy, rho_out, nx, ny, plane, (TF)omega, TF(0), TF(0), TF(0), st);
     return cudaGetLastError();
 }
 
@@ -311,7 +319,8 @@ cudaError_t launch_f_from_double(const double* in, TF* f, size_t n, cudaStream_t
 #define CPLBM_INST(TF)                                                                       \
     template cudaError_t launch_collide_stream<TF>(const TF*, TF*, const double*,            \
                                                    const double*, double*, int, int, size_t, \
-                                                   double, DevState*, cudaStream_t);         \
+                                                   double, const MrtRates*, DevState*,       \
+                                                   cudaStream_t);                            \
     template cudaError_t launch_init_feq<TF>(const double*, const double*, const double*,    \
                                              TF*, double*, int, int, size_t, cudaStream_t);  \
     template cudaError_t launch_rho_from_f<TF>(const TF*, double*, int, int, size_t,         \

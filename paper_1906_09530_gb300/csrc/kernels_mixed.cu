@@ -58,6 +58,7 @@ __device__ __forceinline__ void raise_flag(DevState* st, unsigned bits, int64_t 
 // ---------------------------------------------------------------------------
 constexpr int kSwWarps = 4;  // warps per block
 
+template <bool MRT>
 __device__ __forceinline__ void cs_mixed_body(const CsArgs& a, int wid) {
     const float* __restrict__ fin = a.fin;
     float* __restrict__ fout = a.fout;
@@ -88,7 +89,10 @@ __device__ __forceinline__ void cs_mixed_body(const CsArgs& a, int wid) {
     auto collide_raw = [&](float out[9]) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) out[i] = raw[i];
-        ok &= collide_pairs<float>(out, raw[9], raw[10], omega, FLT_MAX);
+        if constexpr (MRT)
+            ok &= collide_mrt<float>(out, raw[9], raw[10], omega, FLT_MAX, a.se, a.seps, a.sq);
+        else
+            ok &= collide_pairs<float>(out, raw[9], raw[10], omega, FLT_MAX);
     };
     float A[9], B[9], C[9];
     fetch(y0 - 1);
@@ -127,19 +131,21 @@ __device__ __forceinline__ void cs_mixed_body(const CsArgs& a, int wid) {
     if (!ok) raise_flag(a.st, FLAG_RHO, a.st->t);
 }
 
+template <bool MRT>
 __global__ void __launch_bounds__(kSwWarps * 32) k_cs_mixed_sw(CsArgs a) {
-    cs_mixed_body(a, blockIdx.x * kSwWarps + (threadIdx.x >> 5));
+    cs_mixed_body<MRT>(a, blockIdx.x * kSwWarps + (threadIdx.x >> 5));
 }
 
 // Batched: block b belongs to instance map[b]; its warps continue that
 // instance's warp numbering from the instance's first block.
+template <bool MRT>
 __global__ void __launch_bounds__(kSwWarps * 32)
     k_cs_mixed_batch(const CsBatchInst* __restrict__ d, const int* __restrict__ map, int from) {
     const CsBatchInst& D = d[map[blockIdx.x]];
     CsArgs a = D.a;
     a.fin = D.f[from];
     a.fout = D.f[1 - from];
-    cs_mixed_body(a, ((int)blockIdx.x - D.blk0) * kSwWarps + (threadIdx.x >> 5));
+    cs_mixed_body<MRT>(a, ((int)blockIdx.x - D.blk0) * kSwWarps + (threadIdx.x >> 5));
 }
 
 // f = f^eq(rho, u) in FP64, stored as FP32; rho = DF sum of the stored floats.
@@ -308,7 +314,7 @@ inline unsigned grid_for(size_t n, int threads) {
 
 CsArgs cs_mixed_args(const float* fin, float* fout, const float* Fx, const float* Fy,
                      float* rh, float* rl, int nx, int ny, size_t plane, double omega,
-                     DevState* st, int rows) {
+                     const MrtRates* mrt, DevState* st, int rows) {
     // rows per warp: 32 on large grids, fewer on small ones to keep >= ~4k warps
     const int nstrips = (nx + 29) / 30;
     if (rows <= 0) {
@@ -316,7 +322,9 @@ CsArgs cs_mixed_args(const float* fin, float* fout, const float* Fx, const float
         while (rows > 8 && (long long)nstrips * ((ny + rows - 1) / rows) < 4096) rows /= 2;
     }
     CsArgs a{fin, fout, Fx, Fy, rh, rl, nx, ny, plane, (float)omega, nstrips,
-             (ny + rows - 1) / rows, rows, st};
+             (ny + rows - 1) / rows, rows, st, mrt ? 1 : 0,
+             mrt ? (float)mrt->se : 0.0f, mrt ? (float)mrt->seps : 0.0f,
+             mrt ? (float)mrt->sq : 0.0f};
     return a;
 }
 
@@ -325,23 +333,28 @@ int cs_mixed_blocks(const CsArgs& a) {
     return (int)((warps + kSwWarps - 1) / kSwWarps);
 }
 
-cudaError_t launch_cs_mixed(const float* fin, float* fout, const float* Fx, const float* Fy,
-                            float* rh, float* rl, int nx, int ny, size_t plane, double omega,
-                            DevState* st, cudaStream_t s) {
-    const CsArgs a = cs_mixed_args(fin, fout, Fx, Fy, rh, rl, nx, ny, plane, omega, st, 0);
-    k_cs_mixed_sw<<<cs_mixed_blocks(a), kSwWarps * 32, 0, s>>>(a);
+cudaError_t launch_cs_mixed_args(const CsArgs& a, cudaStream_t s) {
+    if (a.mrt)
+        k_cs_mixed_sw<true><<<cs_mixed_blocks(a), kSwWarps * 32, 0, s>>>(a);
+    else
+        k_cs_mixed_sw<false><<<cs_mixed_blocks(a), kSwWarps * 32, 0, s>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_cs_mixed_args(const CsArgs& a, cudaStream_t s) {
-    k_cs_mixed_sw<<<cs_mixed_blocks(a), kSwWarps * 32, 0, s>>>(a);
-    return cudaGetLastError();
+cudaError_t launch_cs_mixed(const float* fin, float* fout, const float* Fx, const float* Fy,
+                            float* rh, float* rl, int nx, int ny, size_t plane, double omega,
+                            const MrtRates* mrt, DevState* st, cudaStream_t s) {
+    return launch_cs_mixed_args(
+        cs_mixed_args(fin, fout, Fx, Fy, rh, rl, nx, ny, plane, omega, mrt, st, 0), s);
 }
 
 cudaError_t launch_cs_mixed_batch(const CsBatchInst* d, const int* map, int nblocks, int from,
-                                  cudaStream_t s) {
+                                  bool mrt, cudaStream_t s) {
     if (nblocks <= 0) return cudaSuccess;
-    k_cs_mixed_batch<<<nblocks, kSwWarps * 32, 0, s>>>(d, map, from);
+    if (mrt)
+        k_cs_mixed_batch<true><<<nblocks, kSwWarps * 32, 0, s>>>(d, map, from);
+    else
+        k_cs_mixed_batch<false><<<nblocks, kSwWarps * 32, 0, s>>>(d, map, from);
     return cudaGetLastError();
 }
 

@@ -78,6 +78,17 @@ def test_workspace_bytes_validation():
     assert P.lbm_workspace_bytes(64, 64, 7, 6) == 0                    # bad precision
 
 
+def test_mrt_rates_validated():
+    g = B.LbmGrid(64, 64, 1, 1)
+    for rates, ok in (((1.64, 1.54, 1.9), True), ((0.0, 1.5, 1.5), False),
+                      ((1.5, 2.0, 1.5), False), ((1.5, 1.5, -1.0), False)):
+        o = B._opts(B.LBM_PREC_MIXED, 6, math.inf, 0, "mrt", rates)
+        assert (P.lib().lbm_workspace_bytes(C.byref(g), C.byref(o)) > 0) == ok
+    o = B.LbmOpts(B.LBM_PREC_MIXED, 6, math.inf, 0)
+    o.collision = 7
+    assert P.lib().lbm_workspace_bytes(C.byref(g), C.byref(o)) == 0
+
+
 def _init(**kw):
     args = dict(nx=64, ny=64, T_r=0.6, kappa=0.1, tau=1.0, k=0.5, order=6, ws=256, wsb=1 << 40)
     args.update(kw)

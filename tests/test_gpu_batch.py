@@ -204,3 +204,24 @@ def test_batch_step_timed_matches_step(cuda):
         assert np.array_equal(a.fields(i)[0], b.fields(i)[0])
     a.close()
     b.close()
+
+
+def test_batch_mrt_bitexact_vs_lone(cuda):
+    from paper_1906_09530_gb300 import Batch
+    spec, rhos = _instances()
+    spec, rhos = spec[:4], rhos[:4]
+    b = Batch(spec, collision="mrt")
+    for i, r in enumerate(rhos):
+        b.set_fields(i, r)
+    b.step(7)
+    for i, (d, r) in enumerate(zip(spec, rhos)):
+        from paper_1906_09530_gb300 import Simulation
+        s = Simulation(d["nx"], d["ny"], d["T_r"], d["kappa"], d["tau"], d["k"], fd_order=6,
+                       precision="mixed", mu_max=d.get("mu_max", math.inf),
+                       mu_cap_steps=d.get("mu_cap_steps", 0), collision="mrt")
+        s.set_fields(r)
+        s.step(7)
+        for x, y in zip(b.fields(i), s.fields()):
+            assert np.array_equal(x, y)
+        s.close()
+    b.close()

@@ -376,3 +376,38 @@ def test_step_timed_matches_step(cuda, precision):
     assert a.t == b.t == 5
     for x, y in zip(a.fields(), b.fields()):
         assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-4)])
+def test_mrt_steps_against_oracle(cuda, precision, tol):
+    """MRT collision (Eq. 4, the paper's rates s_e 1.64, s_eps 1.54, s_q 1.9,
+    s_v = 1/tau): the GPU's moment-space form against the oracle's literal
+    f - M^-1 S M (f - f^eq) + F_i, after 301 steps of a ragged drop at T_r 0.7,
+    k 0.3, tau 1 (with these rates the oracle itself blows up at T_r 0.6 for
+    k >= 0.3, and at tau 0.8 for every k tried)."""
+    from oracle import sim
+    c = dict(cases.ragged(nx=48, ny=40, T_r=0.7), k=0.3, tau=1.0)
+    g = cases.gpu_sim(c, precision=precision, collision="mrt")
+    g.set_fields(c["rho"])
+    g.step(301)
+    o = cases.oracle_sim(c, mrt=sim.PAPER_MRT)
+    o.set_fields(c["rho"])
+    o.step(301)
+    rho, vx, _, _ = g.fields()
+    orho, ovx, _, _, _, _ = o.fields()
+    assert rel_point(rho, orho) <= tol
+    assert np.abs(vx - ovx).max() <= 1e2 * tol * np.abs(ovx).max()
+
+
+def test_mrt_equal_rates_is_bgk_on_gpu(cuda):
+    """With s_e = s_eps = s_q = 1/tau the MRT kernel computes the BGK collision
+    (FP64, to rounding)."""
+    c = cases.ragged(nx=40, ny=32)
+    w = 1.0 / c["tau"]
+    a = cases.gpu_sim(c)
+    b = cases.gpu_sim(c, collision="mrt", mrt_rates=(w, w, w))
+    a.set_fields(c["rho"])
+    b.set_fields(c["rho"])
+    a.step(100)
+    b.step(100)
+    assert rel_point(b.fields()[0], a.fields()[0]) <= 1e-12
