@@ -1,0 +1,87 @@
+"""The surrogate network of the warm start, plain FP64 numpy: forward pass,
+backward pass and Adam step, written out layer by layer.
+
+TEST INFRASTRUCTURE ONLY (part of the oracle): only the tests and the
+benchmark's CPU legs use it.  Shares no code with the CUDA library.
+
+Network (4 layers, width 256): x[3] -> tanh(x W1 + b1) -> tanh(. W2 + b2) ->
+tanh(. W3 + b3) -> . W4 + b4 = y[256].  Row vectors; W_l is [fan_in, fan_out].
+Loss: mean squared error over the batch and the 256 outputs,
+L = sum((y - t)^2) / (B * 256).  Adam (Kingma and Ba, 2015) with bias
+correction: m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
+p -= lr (m / (1 - b1^s)) / (sqrt(v / (1 - b2^s)) + eps) at step s.
+
+Parameters travel as one flat float vector in the order W1, b1, W2, b2, W3,
+b3, W4, b4, each W row-major [fan_in][fan_out].
+"""
+import numpy as np
+
+SIZES = (3, 256, 256, 256, 256)
+N_LAYERS = len(SIZES) - 1
+
+
+def n_params():
+    return sum(a * b + b for a, b in zip(SIZES[:-1], SIZES[1:]))
+
+
+def unpack(p):
+    """List of (W, b) views of the flat parameter vector."""
+    out, o = [], 0
+    for a, b in zip(SIZES[:-1], SIZES[1:]):
+        W = p[o:o + a * b].reshape(a, b)
+        o += a * b
+        bias = p[o:o + b]
+        o += b
+        out.append((W, bias))
+    return out
+
+
+def init_params(seed):
+    """Glorot-uniform weights, zero biases, from numpy's seeded generator."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for a, b in zip(SIZES[:-1], SIZES[1:]):
+        lim = np.sqrt(6.0 / (a + b))
+        parts.append(rng.uniform(-lim, lim, size=a * b))
+        parts.append(np.zeros(b))
+    return np.concatenate(parts)
+
+
+def forward(p, x):
+    """Outputs y [B, 256] and the activations of every layer (for backward)."""
+    acts = [np.asarray(x, dtype=np.float64)]
+    layers = unpack(np.asarray(p, dtype=np.float64))
+    for l, (W, b) in enumerate(layers):
+        z = acts[-1] @ W + b
+        acts.append(np.tanh(z) if l < N_LAYERS - 1 else z)
+    return acts[-1], acts
+
+
+def loss_and_grad(p, x, t):
+    """Mean-squared-error loss and its gradient with respect to every parameter
+    (flat, the order of the parameter vector), by the chain rule."""
+    p = np.asarray(p, dtype=np.float64)
+    y, acts = forward(p, x)
+    B = y.shape[0]
+    diff = y - t
+    loss = float(np.sum(diff * diff) / (B * y.shape[1]))
+    layers = unpack(p)
+    grads = [None] * N_LAYERS
+    d = 2.0 * diff / (B * y.shape[1])  # dL/dy
+    for l in range(N_LAYERS - 1, -1, -1):
+        W, _ = layers[l]
+        if l < N_LAYERS - 1:
+            d = d * (1.0 - acts[l + 1] ** 2)  # through tanh
+        grads[l] = (acts[l].T @ d, d.sum(axis=0))
+        d = d @ W.T
+    g = np.concatenate([np.concatenate([gw.ravel(), gb]) for gw, gb in grads])
+    return loss, g
+
+
+def adam(p, g, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update (step counts from 1); returns new (p, m, v)."""
+    m = b1 * m + (1 - b1) * g
+    v = b2 * v + (1 - b2) * g * g
+    mh = m / (1 - b1**step)
+    vh = v / (1 - b2**step)
+    return p - lr * mh / (np.sqrt(vh) + eps), m, v
