@@ -312,6 +312,43 @@ lbm_status lbm_batch_set_timeout(lbm_batch *b, double seconds);
 /* Release the batch (not the workspace or the stream). */
 void lbm_batch_free(lbm_batch *b);
 
+/* ---- The surrogate network of the warm start ------------------------------
+ *
+ * A multilayer perceptron 3 -> 256 -> 256 -> 256 -> 256 (tanh on the three hidden
+ * layers, linear output) that maps (T_r, kappa-hat, k), scaled by the caller, to
+ * a 256-point equilibrium interface profile.  Every matrix product runs on the
+ * tensor cores in BF16 with FP32 accumulation; master weights, Adam moments,
+ * activations and the gradient are FP32.  Loss: mean squared error over the
+ * batch and the 256 outputs.  Training: Adam (beta1 0.9, beta2 0.999, eps 1e-8,
+ * with bias correction).  The parameters are one flat FP32 vector in the order
+ * W1, b1, W2, b2, W3, b3, W4, b4, each W row-major [fan_in][fan_out].
+ *
+ * Workspace: one caller-owned device buffer (256-byte aligned,
+ * lbm_mlp_workspace_bytes(max_batch) long).  Inputs d_x are device FP32
+ * [batch][3], targets and outputs device FP32 [batch][256], 1 <= batch <=
+ * max_batch.  All work is enqueued on the stream given to lbm_mlp_init. */
+typedef struct lbm_mlp lbm_mlp; /* opaque, owned by the library */
+
+int64_t lbm_mlp_param_count(void); /* 198 400 */
+size_t lbm_mlp_workspace_bytes(int32_t max_batch); /* 0 if max_batch is out of range */
+lbm_status lbm_mlp_init(lbm_mlp **out, int32_t max_batch, void *d_workspace, size_t ws_bytes,
+                        void *cuda_stream);
+/* Set the parameters from a host vector (and reset Adam's moments and step
+ * count); returns when copied. */
+lbm_status lbm_mlp_set_params(lbm_mlp *net, const float *h_params);
+lbm_status lbm_mlp_get_params(lbm_mlp *net, float *h_params);
+/* y = network(x), enqueued. */
+lbm_status lbm_mlp_forward(lbm_mlp *net, const float *d_x, int32_t batch, float *d_y);
+/* The loss of (x, t) and its gradient with respect to every parameter (into
+ * d_grad, a device FP32 vector of lbm_mlp_param_count() entries; NULL: kept
+ * inside).  h_loss, if not NULL, receives the loss and makes the call wait. */
+lbm_status lbm_mlp_loss_grad(lbm_mlp *net, const float *d_x, const float *d_t, int32_t batch,
+                             double *h_loss, float *d_grad);
+/* One Adam step with learning rate lr > 0 on the batch (x, t). */
+lbm_status lbm_mlp_train_step(lbm_mlp *net, const float *d_x, const float *d_t, int32_t batch,
+                              float lr, double *h_loss);
+void lbm_mlp_free(lbm_mlp *net);
+
 const char *lbm_strerror(lbm_status s);
 
 /* Release the context (not the workspace or the stream, which the caller owns). */

@@ -116,6 +116,15 @@ def lib():
             "lbm_batch_failed": (C.c_int, [_vp, C.POINTER(_i32), C.POINTER(C.c_int64)]),
             "lbm_batch_set_timeout": (C.c_int, [_vp, C.c_double]),
             "lbm_batch_free": (None, [_vp]),
+            "lbm_mlp_param_count": (C.c_int64, []),
+            "lbm_mlp_workspace_bytes": (C.c_size_t, [_i32]),
+            "lbm_mlp_init": (C.c_int, [C.POINTER(_vp), _i32, _vp, C.c_size_t, _vp]),
+            "lbm_mlp_set_params": (C.c_int, [_vp, _vp]),
+            "lbm_mlp_get_params": (C.c_int, [_vp, _vp]),
+            "lbm_mlp_forward": (C.c_int, [_vp, _vp, _i32, _vp]),
+            "lbm_mlp_loss_grad": (C.c_int, [_vp, _vp, _vp, _i32, _dp, _vp]),
+            "lbm_mlp_train_step": (C.c_int, [_vp, _vp, _vp, _i32, C.c_float, _dp]),
+            "lbm_mlp_free": (None, [_vp]),
             "lbm_strerror": (C.c_char_p, [C.c_int]),
             "lbm_free": (None, [_vp]),
         }
@@ -421,6 +430,77 @@ class Batch:
     def close(self):
         if getattr(self, "ctx", None):
             lib().lbm_batch_free(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Mlp:
+    """The surrogate network (lbm_mlp_* of the C ABI).  Inputs and targets are
+    CUDA float32 tensors [batch][3] and [batch][256]; parameters are numpy
+    float32 vectors in the library's order."""
+
+    def __init__(self, max_batch, device=None, stream=None):
+        import torch
+        self.max_batch = max_batch
+        self.n_params = lib().lbm_mlp_param_count()
+        nbytes = lib().lbm_mlp_workspace_bytes(max_batch)
+        if nbytes == 0:
+            raise LbmError(LBM_EINVAL, "lbm_mlp_workspace_bytes")
+        self.device = torch.device(device if device is not None else "cuda")
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream()
+            self.ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            self.ctx = C.c_void_p()
+            _check(lib().lbm_mlp_init(C.byref(self.ctx), max_batch, self.ws.data_ptr(), nbytes,
+                                      self.stream.cuda_stream), "lbm_mlp_init")
+
+    @staticmethod
+    def _f32(t, cols):
+        import torch
+        assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+        assert t.dim() == 2 and t.shape[1] == cols
+        return t.data_ptr()
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.n_params
+        _check(lib().lbm_mlp_set_params(self.ctx, p.ctypes.data), "lbm_mlp_set_params")
+
+    def get_params(self):
+        p = np.empty(self.n_params, dtype=np.float32)
+        _check(lib().lbm_mlp_get_params(self.ctx, p.ctypes.data), "lbm_mlp_get_params")
+        return p
+
+    def forward(self, x):
+        import torch
+        y = torch.empty((x.shape[0], 256), dtype=torch.float32, device=x.device)
+        _check(lib().lbm_mlp_forward(self.ctx, self._f32(x, 3), x.shape[0], y.data_ptr()),
+               "lbm_mlp_forward")
+        return y
+
+    def loss_grad(self, x, t):
+        import torch
+        g = torch.empty(self.n_params, dtype=torch.float32, device=x.device)
+        loss = C.c_double()
+        _check(lib().lbm_mlp_loss_grad(self.ctx, self._f32(x, 3), self._f32(t, 256), x.shape[0],
+                                       C.byref(loss), g.data_ptr()), "lbm_mlp_loss_grad")
+        return loss.value, g
+
+    def train_step(self, x, t, lr, want_loss=False):
+        loss = C.c_double()
+        _check(lib().lbm_mlp_train_step(self.ctx, self._f32(x, 3), self._f32(t, 256), x.shape[0],
+                                        lr, C.byref(loss) if want_loss else None),
+               "lbm_mlp_train_step")
+        return loss.value if want_loss else None
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lib().lbm_mlp_free(self.ctx)
             self.ctx = None
 
     def __del__(self):

@@ -1,0 +1,88 @@
+"""The surrogate network's kernels (lbm_mlp_* of the C ABI) against the FP64
+oracle (oracle/mlp.py, pinned by test_oracle_mlp.py), on the same float32
+parameters and inputs.
+
+Tolerances come from the arithmetic: every product takes BF16 operands (8
+significant bits, unit 2^-8 = 3.9e-3) with FP32 accumulation over K <= 256 terms
+whose rounding errors add up like a random walk, through four layers.  Relative
+L2 errors of about 1e-2 are expected, and the bounds are 2e-2 (outputs) and 5e-2
+(each layer's gradient), with the gradient's direction within 0.1% (cosine).
+"""
+import numpy as np
+import pytest
+
+from oracle import mlp as O
+
+pytestmark = pytest.mark.gpu
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _setup(cuda, B, seed=4):
+    from paper_1906_09530_gb300 import Mlp
+    torch = cuda
+    rng = np.random.default_rng(seed)
+    p = O.init_params(seed).astype(np.float32)
+    x = rng.uniform(-1, 1, (B, 3)).astype(np.float32)
+    t = (0.5 + 0.4 * np.sin(np.outer(x[:, 0] + 0.5 * x[:, 1] - x[:, 2], np.linspace(0, 3, 256)))
+         ).astype(np.float32)
+    net = Mlp(max_batch=512)
+    net.set_params(p)
+    return net, p, x, t, torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+
+
+def test_params_round_trip(cuda):
+    net, p, *_ = _setup(cuda, 8)
+    assert np.array_equal(net.get_params(), p)
+    assert net.n_params == O.n_params()
+
+
+@pytest.mark.parametrize("B", [1, 37, 300])
+def test_forward_matches_oracle(cuda, B):
+    net, p, x, t, dx, dt = _setup(cuda, B)
+    y = net.forward(dx).cpu().numpy()
+    y_ref, _ = O.forward(p.astype(np.float64), x.astype(np.float64))
+    assert _rel(y, y_ref) <= 2e-2
+
+
+def test_loss_and_gradient_match_oracle(cuda):
+    net, p, x, t, dx, dt = _setup(cuda, 200)
+    loss, g = net.loss_grad(dx, dt)
+    g = g.cpu().numpy().astype(np.float64)
+    loss_ref, g_ref = O.loss_and_grad(p.astype(np.float64), x, t)
+    assert loss == pytest.approx(loss_ref, rel=2e-2)
+    o = 0
+    for a, b in zip(O.SIZES[:-1], O.SIZES[1:]):
+        for n in (a * b, b):
+            gs, rs = g[o:o + n], g_ref[o:o + n]
+            assert _rel(gs, rs) <= 5e-2
+            assert gs @ rs / (np.linalg.norm(gs) * np.linalg.norm(rs)) >= 0.999
+            o += n
+
+
+def test_adam_steps_follow_oracle(cuda):
+    """Five Adam steps on the GPU against five on the oracle from the same
+    start: the parameters stay within a few hundredths of the step size."""
+    net, p, x, t, dx, dt = _setup(cuda, 128)
+    lr = 1e-3
+    for _ in range(5):
+        net.train_step(dx, dt, lr)
+    q = p.astype(np.float64)
+    m, v = np.zeros_like(q), np.zeros_like(q)
+    for s in range(1, 6):
+        _, g = O.loss_and_grad(q, x, t)
+        q, m, v = O.adam(q, g, m, v, s, lr)
+    got = net.get_params().astype(np.float64)
+    # each step moves a parameter by about lr; compare the displacements
+    assert _rel(got - p, q - p) <= 5e-2
+
+
+def test_training_reduces_loss(cuda):
+    net, p, x, t, dx, dt = _setup(cuda, 256)
+    l0 = net.train_step(dx, dt, 2e-3, want_loss=True)
+    for _ in range(300):
+        net.train_step(dx, dt, 2e-3)
+    l1 = net.loss_grad(dx, dt)[0]
+    assert l1 < 0.05 * l0
