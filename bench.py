@@ -310,6 +310,97 @@ def batch_config(steps, warmup, n=256):
             "l2": "working set above L2 (no flush)"}
 
 
+def surrogate_demo():
+    """The learned warm start: a surrogate trained on 256 equilibrium slabs
+    (T_r 0.33-0.5, kappa-hat 0.1, k 0.2) by the library's MLP kernels, then
+    steps and wall time to equilibrium (both bulks within the tolerance of a
+    1.5M-step run) from the tanh start and from the warm start, on a tall slab
+    (8 x 1536) where the gas offset relaxes by slow diffusion.  Also the
+    training step's tensor throughput (BF16 products, FP32 accumulation)."""
+    import numpy as np
+    import torch
+    from paper_1906_09530_gb300 import Simulation, lbm_maxwell, surrogate as SG
+    from paper_1906_09530_gb300 import workloads as W
+    ranges = {"T_r": (0.33, 0.5), "kappa": (0.1, 0.1), "k": (0.2, 0.2)}
+    n = 256
+    T = np.linspace(*ranges["T_r"], n)
+    K, k = np.full(n, 0.1), np.full(n, 0.2)
+    t0 = time.perf_counter()
+    G, L, P = SG.equilibrium_profiles(T, K, k, steps=200_000)
+    data_s = time.perf_counter() - t0
+    s = SG.Surrogate(seed=3, ranges=ranges)
+    t0 = time.perf_counter()
+    loss = s.fit(T, K, k, G, L, P, epochs=3000, lr=2e-3, batch=128)
+    fit_s = time.perf_counter() - t0
+    # training-step throughput at batch 256 (algorithmic flops: forward
+    # 2 (3*256 + 3*256^2) per sample, backward twice that less the input layer's
+    # input gradient)
+    # timed on a network of its own, so the trained one is left as it is
+    from paper_1906_09530_gb300 import Mlp
+    tnet = Mlp(256)
+    tnet.set_params(SG.glorot_params(0))
+    x = torch.rand((256, 3), device="cuda") * 2 - 1
+    y = torch.rand((256, 256), device="cuda")
+    for _ in range(10):
+        tnet.train_step(x, y, 1e-3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(200):
+        tnet.train_step(x, y, 1e-3)
+    e1.record()
+    torch.cuda.synchronize()
+    step_ms = e0.elapsed_time(e1) / 200
+    tnet.close()
+    fwd = 2 * (3 * 256 + 3 * 256 * 256)
+    flops = 256 * (fwd + 2 * fwd - 2 * 3 * 256)
+    peak, _ = load_bf16_peak()
+    tflops = flops / (step_ms / 1e3) / 1e12
+    ny = 1536
+
+    def bulk(sim):
+        r = sim.fields()[0][:, 0]
+        return (np.r_[r[: ny // 10], r[-ny // 10:]].mean(),
+                r[ny // 2 - ny // 10: ny // 2 + ny // 10].mean())
+    cases = []
+    for t_r in (0.35, 0.42):
+        rg, rl = lbm_maxwell(t_r)
+        ref = Simulation(8, ny, t_r, 0.1, 1.0, 0.2, fd_order=6, precision="mixed")
+        ref.set_fields(W.flat(8, ny, rg, rl, ny / 2, 20.0))
+        ref.step(1_500_000)
+        eq = bulk(ref)
+        ref.close()
+        g, l, w = s.predict([t_r], [0.1], [0.2])
+        row = {"T_r": t_r, "gas_offset_vs_maxwell": eq[0] / rg - 1,
+               "predicted_gas_rel_err": g[0] / eq[0] - 1, "predicted_liq_rel_err": l[0] / eq[1] - 1}
+        for name, field in (("tanh", W.flat(8, ny, rg, rl, ny / 2, 20.0)),
+                            ("warm", SG.flat_field(8, ny, g[0], l[0], w[0]))):
+            for tol in (1e-2, 1e-3):
+                sim = Simulation(8, ny, t_r, 0.1, 1.0, 0.2, fd_order=6, precision="mixed")
+                sim.set_fields(field)
+                c0 = time.perf_counter()
+                n_steps = SG.steps_to_equilibrium(sim, bulk, eq, tol, every=2000,
+                                                  max_steps=1_000_000)
+                row[f"{name}_steps_to_{tol:g}"] = n_steps
+                row[f"{name}_wall_s_to_{tol:g}"] = time.perf_counter() - c0
+                sim.close()
+        cases.append(row)
+    s.close()
+    return {"workload": "slab-8x1536-k0.2-kappa0.1, surrogate trained on 256 slabs T_r 0.33-0.5",
+            "training_data_s": data_s, "fit_s": fit_s, "fit_loss": loss,
+            "train_step_ms_batch256": step_ms,
+            "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
+                         "frac": tflops / peak,
+                         "note": "256-wide products: latency-bound, microseconds per step"},
+            "cases": cases}
+
+
+def load_bf16_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return float(json.load(open(p))["bf16_tflops"]), "measured"
+    return 1900.0, "fallback"
+
+
 def run_reference(args, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -361,6 +452,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-equilibrium", action="store_true")
+    ap.add_argument("--surrogate", action="store_true",
+                    help="add the learned warm start's measurement (several minutes)")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched-instances line")
     ap.add_argument("--no-large", action="store_true",
@@ -504,6 +597,8 @@ def main():
                                             k=0.3, width=4.0 / 0.3)
     if not args.no_batch and args.precision == "mixed":
         line["batch"] = batch_config(min(args.steps, 50), max(args.warmup // 10, 3))
+    if rank == 0 and args.surrogate:
+        line["surrogate"] = surrogate_demo()
     if rank == 0 and not args.no_equilibrium:
         line["equilibrium"] = equilibrium_time(args.precision)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
