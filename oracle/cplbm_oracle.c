@@ -37,6 +37,7 @@ static const double WQ[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,
                              1.0 / 9.0,  1.0 / 9.0,  1.0 / 36.0,
                              1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
 static const double CS2 = 1.0 / 3.0; /* c_s^2 with c = 1 */
+static const int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6}; /* e_OPP[i] = -e_i */
 
 typedef struct {
     int32_t nx, ny;
@@ -49,6 +50,7 @@ typedef struct {
     double eos_alpha;       /* alpha(T) of Eqs. 16-19 */
     int32_t mrt;            /* 0: BGK collision (Eq. 1); 1: MRT collision (Eq. 4) */
     double s[9];            /* MRT relaxation rates, the diagonal of S in Eq. 4 */
+    int32_t walls_y;        /* 1: solid walls below y = 0 and above y = ny - 1 (Sec. 5.5) */
 } orc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -188,12 +190,43 @@ static int cfd_x(const orc_params *p, const double *u, double *d)
 }
 
 /* d/dy of a [ny][nx] field: every y-line in turn. */
+/* y-lines.  With walls, every field is extended evenly about both walls
+ * (ghost y = -1 - j equals y = j, ghost y = ny + j equals y = ny - 1 - j): the
+ * first ghost takes the value of its fluid neighbour, the wall rule of Sec. 5.5,
+ * and the extended line is periodic with period 2 ny, so the same periodic
+ * compact scheme applies; the first ny results are the derivatives. */
 static int cfd_y(const orc_params *p, const double *u, double *d)
 {
-    for (int x = 0; x < p->nx; ++x)
-        if (orc_cfd_line(u + x, p->nx, d + x, p->nx, p->ny, p->alpha, 1.0))
-            return -1;
-    return 0;
+    int ny = p->ny;
+    if (!p->walls_y) {
+        for (int x = 0; x < p->nx; ++x)
+            if (orc_cfd_line(u + x, p->nx, d + x, p->nx, ny, p->alpha, 1.0))
+                return -1;
+        return 0;
+    }
+    double *line = (double *)malloc(sizeof(double) * 4 * ny);
+    if (!line)
+        return -1;
+    double *dl = line + 2 * ny;
+    int err = 0;
+    for (int x = 0; x < p->nx && !err; ++x) {
+        for (int y = 0; y < ny; ++y) {
+            line[y] = u[(size_t)y * p->nx + x];
+            line[2 * ny - 1 - y] = u[(size_t)y * p->nx + x];
+        }
+        err = orc_cfd_line(line, 1, dl, 1, 2 * ny, p->alpha, 1.0);
+        for (int y = 0; y < ny; ++y)
+            d[(size_t)y * p->nx + x] = dl[y];
+    }
+    free(line);
+    return err ? -1 : 0;
+}
+
+/* The compact derivative of a whole field along x (axis 0) or y (axis 1),
+ * with the run's boundaries; exported for the tests.  Returns 0 or -1. */
+int orc_cfd_field(const orc_params *p, int axis, const double *u, double *d)
+{
+    return axis == 0 ? cfd_x(p, u, d) : cfd_y(p, u, d);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -401,12 +434,21 @@ int orc_run(const orc_params *p, double *f, int64_t t0, int64_t nsteps)
                 fs[i * N + n] = f[i * N + n] - d + Fi[i];
             }
         }
-        /* streaming, Eq. 1 left-hand side, periodic in x and y */
+        /* streaming, Eq. 1 left-hand side, periodic in x; in y periodic, or with
+         * walls halfway bounce-back: a population that would leave the fluid
+         * through a wall returns to its node in the opposite direction */
         for (int i = 0; i < 9; ++i)
             for (int y = 0; y < ny; ++y)
                 for (int x = 0; x < nx; ++x) {
-                    int xd = (x + EX[i] + nx) % nx, yd = (y + EY[i] + ny) % ny;
-                    f[i * N + (size_t)yd * nx + xd] = fs[i * N + (size_t)y * nx + x];
+                    int xd = (x + EX[i] + nx) % nx, yd = y + EY[i];
+                    double v = fs[i * N + (size_t)y * nx + x];
+                    if (!p->walls_y) {
+                        yd = (yd + ny) % ny;
+                    } else if (yd < 0 || yd >= ny) {
+                        f[OPP[i] * N + (size_t)y * nx + x] = v;
+                        continue;
+                    }
+                    f[i * N + (size_t)yd * nx + xd] = v;
                 }
     }
     free(buf);

@@ -24,7 +24,7 @@ class OrcParams(C.Structure):
                 ("alpha", C.c_double),
                 ("mu_max", C.c_double), ("mu_cap_steps", C.c_int64),
                 ("eos", C.c_int32), ("eos_alpha", C.c_double),
-                ("mrt", C.c_int32), ("s", C.c_double * 9)]
+                ("mrt", C.c_int32), ("s", C.c_double * 9), ("walls_y", C.c_int32)]
 
 # MRT relaxation rates of Sec. 2 (after Eq. 4): s_e, s_eps, s_q; s_v = 1/tau
 PAPER_MRT = (1.64, 1.54, 1.9)
@@ -38,10 +38,13 @@ def lib():
     if _lib is None:
         L = C.CDLL(_build.build())
         dp = C.POINTER(C.c_double)
+        P = C.POINTER(OrcParams)
         L.orc_cs_p0.restype = C.c_double
         L.orc_cs_p0.argtypes = [C.c_double] * 5
         L.orc_cs_mu0.restype = C.c_double
         L.orc_cs_mu0.argtypes = [C.c_double] * 5
+        L.orc_cfd_field.restype = C.c_int
+        L.orc_cfd_field.argtypes = [P, C.c_int, dp, dp]
         L.orc_mrt_matrices.restype = None
         L.orc_mrt_matrices.argtypes = [dp, dp]
         L.orc_p0.restype = C.c_double
@@ -53,7 +56,6 @@ def lib():
                                    C.c_double, C.c_double]
         L.orc_forcing_terms.restype = None
         L.orc_forcing_terms.argtypes = [C.c_double] * 5 + [dp]
-        P = C.POINTER(OrcParams)
         L.orc_feq_field.restype = None
         L.orc_feq_field.argtypes = [P, dp, dp, dp, dp]
         L.orc_force_stage.restype = C.c_int
@@ -129,16 +131,19 @@ class OracleSim:
     """One periodic D2Q9 simulation advanced by the C oracle, FP64."""
 
     def __init__(self, nx, ny, T, kappa, tau, k, fd_order, mu_max=math.inf,
-                 mu_cap_steps=0, a=1.0, b=4.0, R=1.0, eos=None, mrt=None):
+                 mu_cap_steps=0, a=1.0, b=4.0, R=1.0, eos=None, mrt=None, walls_y=False):
         """`eos`: an oracle.eos.Eos (its kind, a, b, R and alpha(T) replace the
         Carnahan-Starling defaults).  `mrt`: None for BGK (Eq. 1), else the rates
         (s_e, s_eps, s_q) of the MRT collision (Eq. 4), with s_v = 1/tau and the
-        conserved moments' rates 0."""
+        conserved moments' rates 0.  `walls_y`: solid walls below the first and
+        above the last row (halfway bounce-back, fields extended evenly about
+        the walls for the y derivatives)."""
         kind, al = 0, 1.0
         if eos is not None:
             kind, a, b, R, al = EOS_KIND[eos.kind], eos.a, eos.b, eos.R, eos.alpha(T)
         self.p = OrcParams(nx, ny, T, a, b, R, kappa, tau, k, cfd_alpha(fd_order),
                            mu_max, mu_cap_steps, kind, al)
+        self.p.walls_y = 1 if walls_y else 0
         if mrt is not None:
             se, seps, sq = mrt
             sv = 1.0 / tau
@@ -174,6 +179,14 @@ class OracleSim:
                            _ptr(vy), _ptr(mu), _ptr(Fx), _ptr(Fy)):
             raise RuntimeError("oracle macro failed")
         return rho, vx, vy, mu, Fx, Fy
+
+    def cfd_field(self, u, axis):
+        """Compact derivative of a field along an axis, with this run's boundaries."""
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        d = np.empty_like(u)
+        if lib().orc_cfd_field(C.byref(self.p), axis, _ptr(u), _ptr(d)):
+            raise RuntimeError("oracle cfd failed")
+        return d
 
     def force_stage(self, rho, t=None):
         """(mu_hat, Fx, Fy) computed from a given density field."""

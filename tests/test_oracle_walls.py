@@ -1,0 +1,86 @@
+"""Pins of the oracle's walls (Sec. 5.5: periodic in x, solid top and bottom).
+
+Populations: halfway bounce-back, so the no-slip wall lies half a node outside
+the first and last rows.  Derivatives in y: every field is extended evenly
+about both walls, so the first ghost takes its fluid neighbour's value (the
+paper's wall rule for the chemical potential) and each y-line becomes periodic
+with period 2 ny.
+
+  * the y-derivative of cos(m pi (y + 1/2)/ny), even about both walls, is the
+    compact scheme's modified wavenumber times -sin(...), exactly (Eqs. 37-39);
+    a ghost reflected about the wrong point, or an odd extension, fails;
+  * the no-slip shear mode u_x = U sin(pi (y + 1/2)/ny) between the walls decays
+    as exp(-nu (pi/ny)^2 t), nu = (tau - 1/2)/3: this fixes the wall position;
+  * bounce-back conserves mass to rounding;
+  * without walls the same calls reduce to the periodic ones.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import OracleSim, cfd_alpha, thermo
+from paper_1906_09530_gb300 import workloads as W
+
+TC, _ = thermo.critical_point()
+
+
+def theta(order, w):
+    a = cfd_alpha(order)
+    A = 2.0 / 3.0 * (a + 2.0)
+    B = (4.0 * a - 1.0) / 3.0
+    return (A * math.sin(w) + B / 2 * math.sin(2 * w)) / (1 + 2 * a * math.cos(w))
+
+
+@pytest.mark.parametrize("order", [4, 6])
+@pytest.mark.parametrize("m", [1, 3, 7])
+def test_even_extension_derivative(order, m):
+    nx, ny = 3, 24
+    s = OracleSim(nx, ny, 0.7 * TC, 0.1, 1.0, 0.5, order, walls_y=True)
+    y = np.arange(ny)[:, None] * np.ones((1, nx))
+    w = m * math.pi / ny
+    u = np.cos(w * (y + 0.5))
+    d = s.cfd_field(u, 1)
+    assert np.abs(d + theta(order, w) * np.sin(w * (y + 0.5))).max() <= 1e-13
+    # x stays periodic
+    x = np.arange(nx)[None, :] * np.ones((ny, 1))
+    ux = np.sin(2 * math.pi * x / nx)
+    assert np.abs(s.cfd_field(ux, 0) - theta(order, 2 * math.pi / nx) *
+                  np.cos(2 * math.pi * x / nx)).max() <= 1e-13
+
+
+def test_channel_shear_mode_decay():
+    nx, ny, tau, U = 4, 32, 1.0, 1e-5
+    s = OracleSim(nx, ny, 1.5 * TC, 0.1, tau, 1.0, 6, walls_y=True)
+    y = np.arange(ny)[:, None] * np.ones((1, nx))
+    ux = U * np.sin(math.pi * (y + 0.5) / ny)
+    s.set_fields(np.full((ny, nx), 0.2), ux, np.zeros_like(ux))
+    s.step(2000)
+    vx = s.fields()[1]
+    prof = np.sin(math.pi * (np.arange(ny) + 0.5) / ny)
+    amp = (vx[:, 0] @ prof) / (prof @ prof)
+    nu = -math.log(amp / U) / ((math.pi / ny) ** 2 * 2000)
+    assert nu == pytest.approx((tau - 0.5) / 3, rel=1e-2)
+
+
+def test_mass_conserved_with_walls():
+    rg, rl = thermo.maxwell(0.6)
+    rho = W.with_noise(W.drop(40, 32, rg, rl, 8, 4, center=(20, 10)), 7, 1e-6)
+    s = OracleSim(40, 32, 0.6 * TC, 0.1, 1.0, 0.5, 6, walls_y=True)
+    s.set_fields(rho, np.zeros_like(rho), np.full_like(rho, -0.02))
+    m0 = s.f.sum()
+    s.step(200)
+    assert abs(s.f.sum() - m0) / m0 < 1e-13
+    assert np.isfinite(s.f).all()
+
+
+def test_no_walls_is_periodic():
+    rg, rl = thermo.maxwell(0.7)
+    rho = W.with_noise(W.drop(24, 20, rg, rl, 6, 4), 3, 1e-5)
+    a = OracleSim(24, 20, 0.7 * TC, 0.1, 1.0, 0.5, 6)
+    b = OracleSim(24, 20, 0.7 * TC, 0.1, 1.0, 0.5, 6, walls_y=False)
+    a.set_fields(rho)
+    b.set_fields(rho)
+    a.step(20)
+    b.step(20)
+    assert np.array_equal(a.f, b.f)
