@@ -222,11 +222,47 @@ static int cfd_y(const orc_params *p, const double *u, double *d)
     return err ? -1 : 0;
 }
 
-/* The compact derivative of a whole field along x (axis 0) or y (axis 1),
- * with the run's boundaries; exported for the tests.  Returns 0 or -1. */
+/* d2/dy2 of a [ny][nx] field, "applying CFM twice" (Sec. 4.3) along the
+ * line the field is extended to.  Periodic: cfd_y twice.  With walls the
+ * density is what is extended evenly; the scheme is applied twice over the
+ * whole period 2 ny, so the intermediate first derivative keeps the odd
+ * symmetry the derivative of an even line has (it is not extended again). */
+static int cfd_yy(const orc_params *p, const double *u, double *d)
+{
+    int ny = p->ny;
+    if (!p->walls_y) {
+        double *tmp = (double *)malloc(sizeof(double) * (size_t)p->nx * ny);
+        if (!tmp)
+            return -1;
+        int err = cfd_y(p, u, tmp) | cfd_y(p, tmp, d);
+        free(tmp);
+        return err ? -1 : 0;
+    }
+    double *line = (double *)malloc(sizeof(double) * 6 * ny);
+    if (!line)
+        return -1;
+    double *dl = line + 2 * ny, *ddl = line + 4 * ny;
+    int err = 0;
+    for (int x = 0; x < p->nx && !err; ++x) {
+        for (int y = 0; y < ny; ++y) {
+            line[y] = u[(size_t)y * p->nx + x];
+            line[2 * ny - 1 - y] = u[(size_t)y * p->nx + x];
+        }
+        err = orc_cfd_line(line, 1, dl, 1, 2 * ny, p->alpha, 1.0);
+        err |= orc_cfd_line(dl, 1, ddl, 1, 2 * ny, p->alpha, 1.0);
+        for (int y = 0; y < ny; ++y)
+            d[(size_t)y * p->nx + x] = ddl[y];
+    }
+    free(line);
+    return err ? -1 : 0;
+}
+
+/* The compact derivative of a whole field along x (axis 0) or y (axis 1), or
+ * the second derivative along y (axis 2) as the force stage takes it, with the
+ * run's boundaries; exported for the tests.  Returns 0 or -1. */
 int orc_cfd_field(const orc_params *p, int axis, const double *u, double *d)
 {
-    return axis == 0 ? cfd_x(p, u, d) : cfd_y(p, u, d);
+    return axis == 0 ? cfd_x(p, u, d) : axis == 1 ? cfd_y(p, u, d) : cfd_yy(p, u, d);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -281,6 +317,7 @@ static void moments(const orc_params *p, const double *f, double *rho, double *u
 /* The force stage at time level t, from rho alone:
  *   d_x rho, d_y rho                      compact FD, Eq. 39 (or its alpha family)
  *   d_xx rho = D_x(D_x rho), likewise y   "applying CFM twice", Sec. 4.3
+ *                                         (with walls: along the extended line)
  *   mu-hat = k^2 mu0(rho) - kappa (d_xx rho + d_yy rho)          Eq. 33
  *   mu-hat <- min(mu-hat, k^2 mu_max) while t < mu_cap_steps    Sec. 5.6
  *   F = -rho grad(mu-hat) + c_s^2 grad(rho)                     Eq. 12
@@ -298,7 +335,7 @@ int orc_force_stage(const orc_params *p, int64_t t, const double *rho, double *m
     err |= cfd_x(p, rho, dxr);
     err |= cfd_y(p, rho, dyr);
     err |= cfd_x(p, dxr, dxxr);
-    err |= cfd_y(p, dyr, dyyr);
+    err |= cfd_yy(p, rho, dyyr);
     double k2 = p->k * p->k;
     for (size_t n = 0; n < N; ++n) {
         double m = k2 * orc_mu0(p->eos, rho[n], p->T, p->a, p->b, p->R, p->eos_alpha) -

@@ -181,7 +181,9 @@ class OracleSim:
         return rho, vx, vy, mu, Fx, Fy
 
     def cfd_field(self, u, axis):
-        """Compact derivative of a field along an axis, with this run's boundaries."""
+        """Compact derivative of a field along an axis (0: x, 1: y), or its second
+        derivative along y (axis 2) as the force stage takes it, with this run's
+        boundaries."""
         u = np.ascontiguousarray(u, dtype=np.float64)
         d = np.empty_like(u)
         if lib().orc_cfd_field(C.byref(self.p), axis, _ptr(u), _ptr(d)):

@@ -9,6 +9,10 @@ with period 2 ny.
   * the y-derivative of cos(m pi (y + 1/2)/ny), even about both walls, is the
     compact scheme's modified wavenumber times -sin(...), exactly (Eqs. 37-39);
     a ghost reflected about the wrong point, or an odd extension, fails;
+  * the second y-derivative of the force stage (the scheme applied twice along
+    the extended density line) of that mode is -theta^2 times it, exactly, and
+    mu-hat of a small such ripple is k^2 mu0(rho) + kappa theta^2 times the
+    ripple; re-extending the intermediate first derivative evenly fails;
   * the no-slip shear mode u_x = U sin(pi (y + 1/2)/ny) between the walls decays
     as exp(-nu (pi/ny)^2 t), nu = (tau - 1/2)/3: this fixes the wall position;
   * bounce-back conserves mass to rounding;
@@ -47,6 +51,31 @@ def test_even_extension_derivative(order, m):
     ux = np.sin(2 * math.pi * x / nx)
     assert np.abs(s.cfd_field(ux, 0) - theta(order, 2 * math.pi / nx) *
                   np.cos(2 * math.pi * x / nx)).max() <= 1e-13
+
+
+@pytest.mark.parametrize("order", [4, 6])
+@pytest.mark.parametrize("m", [1, 4, 9])
+def test_second_derivative_along_extended_line(order, m):
+    nx, ny = 3, 24
+    s = OracleSim(nx, ny, 0.7 * TC, 0.1, 1.0, 0.5, order, walls_y=True)
+    y = np.arange(ny)[:, None] * np.ones((1, nx))
+    w = m * math.pi / ny
+    u = np.cos(w * (y + 0.5))
+    assert np.abs(s.cfd_field(u, 2) + theta(order, w) ** 2 * u).max() <= 1e-13
+
+
+@pytest.mark.parametrize("order", [4, 6])
+def test_mu_hat_of_a_wall_ripple(order):
+    nx, ny, T_r, kappa, k, eps = 4, 30, 0.8, 0.1, 0.5, 1e-3
+    T = T_r * TC
+    s = OracleSim(nx, ny, T, kappa, 1.0, k, order, walls_y=True)
+    y = np.arange(ny)[:, None] * np.ones((1, nx))
+    w = 2 * math.pi / ny
+    ripple = eps * np.cos(w * (y + 0.5))
+    rho = 0.3 + ripple
+    mu, _, _ = s.force_stage(rho)
+    want = k * k * thermo.mu0(rho, T) + kappa * theta(order, w) ** 2 * ripple
+    assert np.abs(mu - want).max() <= 1e-13
 
 
 def test_channel_shear_mode_decay():
