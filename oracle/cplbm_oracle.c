@@ -51,6 +51,7 @@ typedef struct {
     int32_t mrt;            /* 0: BGK collision (Eq. 1); 1: MRT collision (Eq. 4) */
     double s[9];            /* MRT relaxation rates, the diagonal of S in Eq. 4 */
     int32_t walls_y;        /* 1: solid walls below y = 0 and above y = ny - 1 (Sec. 5.5) */
+    double wall_ux[2];      /* x-velocity of the bottom and the top wall (0: at rest) */
 } orc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -473,7 +474,12 @@ int orc_run(const orc_params *p, double *f, int64_t t0, int64_t nsteps)
         }
         /* streaming, Eq. 1 left-hand side, periodic in x; in y periodic, or with
          * walls halfway bounce-back: a population that would leave the fluid
-         * through a wall returns to its node in the opposite direction */
+         * through a wall returns to its node in the opposite direction.  A wall
+         * moving along x at U (a moving reference frame, Sec. 5.5) adds the
+         * momentum of Ladd's moving-wall rule,
+         *   f_opp(i)(x, t+1) = f*_i(x, t) - 2 w_i rho(x, t) (e_i . U) / c_s^2,
+         * with rho the node's own density: mass is conserved, since the two
+         * diagonals it changes cancel. */
         for (int i = 0; i < 9; ++i)
             for (int y = 0; y < ny; ++y)
                 for (int x = 0; x < nx; ++x) {
@@ -482,7 +488,9 @@ int orc_run(const orc_params *p, double *f, int64_t t0, int64_t nsteps)
                     if (!p->walls_y) {
                         yd = (yd + ny) % ny;
                     } else if (yd < 0 || yd >= ny) {
-                        f[OPP[i] * N + (size_t)y * nx + x] = v;
+                        double U = p->wall_ux[yd < 0 ? 0 : 1];
+                        size_t n = (size_t)y * nx + x;
+                        f[OPP[i] * N + n] = v - 2.0 * WQ[i] * rho[n] * EX[i] * U / CS2;
                         continue;
                     }
                     f[i * N + (size_t)yd * nx + xd] = v;

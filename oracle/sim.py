@@ -24,7 +24,8 @@ class OrcParams(C.Structure):
                 ("alpha", C.c_double),
                 ("mu_max", C.c_double), ("mu_cap_steps", C.c_int64),
                 ("eos", C.c_int32), ("eos_alpha", C.c_double),
-                ("mrt", C.c_int32), ("s", C.c_double * 9), ("walls_y", C.c_int32)]
+                ("mrt", C.c_int32), ("s", C.c_double * 9), ("walls_y", C.c_int32),
+                ("wall_ux", C.c_double * 2)]
 
 # MRT relaxation rates of Sec. 2 (after Eq. 4): s_e, s_eps, s_q; s_v = 1/tau
 PAPER_MRT = (1.64, 1.54, 1.9)
@@ -131,19 +132,22 @@ class OracleSim:
     """One periodic D2Q9 simulation advanced by the C oracle, FP64."""
 
     def __init__(self, nx, ny, T, kappa, tau, k, fd_order, mu_max=math.inf,
-                 mu_cap_steps=0, a=1.0, b=4.0, R=1.0, eos=None, mrt=None, walls_y=False):
+                 mu_cap_steps=0, a=1.0, b=4.0, R=1.0, eos=None, mrt=None, walls_y=False,
+                 wall_ux=(0.0, 0.0)):
         """`eos`: an oracle.eos.Eos (its kind, a, b, R and alpha(T) replace the
         Carnahan-Starling defaults).  `mrt`: None for BGK (Eq. 1), else the rates
         (s_e, s_eps, s_q) of the MRT collision (Eq. 4), with s_v = 1/tau and the
         conserved moments' rates 0.  `walls_y`: solid walls below the first and
         above the last row (halfway bounce-back, fields extended evenly about
-        the walls for the y derivatives)."""
+        the walls for the y derivatives); `wall_ux`: the x-velocities of the
+        bottom and the top wall (Ladd's moving-wall bounce-back)."""
         kind, al = 0, 1.0
         if eos is not None:
             kind, a, b, R, al = EOS_KIND[eos.kind], eos.a, eos.b, eos.R, eos.alpha(T)
         self.p = OrcParams(nx, ny, T, a, b, R, kappa, tau, k, cfd_alpha(fd_order),
                            mu_max, mu_cap_steps, kind, al)
         self.p.walls_y = 1 if walls_y else 0
+        self.p.wall_ux[0], self.p.wall_ux[1] = wall_ux
         if mrt is not None:
             se, seps, sq = mrt
             sv = 1.0 / tau

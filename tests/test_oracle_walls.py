@@ -15,7 +15,10 @@ with period 2 ny.
     ripple; re-extending the intermediate first derivative evenly fails;
   * the no-slip shear mode u_x = U sin(pi (y + 1/2)/ny) between the walls decays
     as exp(-nu (pi/ny)^2 t), nu = (tau - 1/2)/3: this fixes the wall position;
-  * bounce-back conserves mass to rounding;
+  * with the walls moving along x at U_b and U_t (Ladd's moving-wall rule),
+    steady Couette flow is u_x = U_b + (U_t - U_b)(y + 1/2)/ny to rounding,
+    for any tau: this fixes the sign and the weight of the wall momentum;
+  * bounce-back conserves mass to rounding, moving walls too;
   * without walls the same calls reduce to the periodic ones.
 """
 import math
@@ -90,6 +93,29 @@ def test_channel_shear_mode_decay():
     amp = (vx[:, 0] @ prof) / (prof @ prof)
     nu = -math.log(amp / U) / ((math.pi / ny) ** 2 * 2000)
     assert nu == pytest.approx((tau - 0.5) / 3, rel=1e-2)
+
+
+@pytest.mark.parametrize("tau", [0.7, 1.0, 1.6])
+def test_couette_flow_between_moving_walls(tau):
+    nx, ny, ub, ut = 4, 16, -0.01, 0.03
+    s = OracleSim(nx, ny, 1.5 * TC, 0.1, tau, 1.0, 6, walls_y=True, wall_ux=(ub, ut))
+    s.set_fields(np.full((ny, nx), 0.2))
+    s.step(int(6 * ny * ny / ((tau - 0.5) / 3)))  # many viscous times
+    rho, vx, vy, *_ = s.fields()
+    y = np.arange(ny)[:, None]
+    assert np.abs(vx - (ub + (ut - ub) * (y + 0.5) / ny)).max() <= 1e-12
+    assert np.abs(vy).max() <= 1e-13
+    assert np.abs(rho - 0.2).max() <= 1e-12
+
+
+def test_mass_conserved_with_moving_walls():
+    rg, rl = thermo.maxwell(0.6)
+    rho = W.with_noise(W.drop(40, 32, rg, rl, 8, 4, center=(20, 10)), 7, 1e-6)
+    s = OracleSim(40, 32, 0.6 * TC, 0.1, 1.0, 0.5, 6, walls_y=True, wall_ux=(0.05, 0.05))
+    s.set_fields(rho, np.full_like(rho, 0.05), np.full_like(rho, -0.02))
+    m0 = s.f.sum()
+    s.step(200)
+    assert abs(s.f.sum() - m0) / m0 < 1e-13
 
 
 def test_mass_conserved_with_walls():
