@@ -310,6 +310,125 @@ def batch_config(steps, warmup, n=256):
             "l2": "working set above L2 (no flush)"}
 
 
+SPLASH = dict(nx=2048, ny=1024, T_r=0.55, k=0.5, kappa=0.1, tau=1.0, order=6, film=100,
+              radius=100.0, height=200.0, width=8.0, u_drop=-0.1, u_shift=0.05)
+
+
+def spreading_radius(rho, y, xc, mid):
+    """Spreading radius of an impact at column xc, read on row y: from xc go
+    each way across any gas (the crater) to the outer edge of the first liquid
+    run (the rim); half the distance between the two edges, 0 if the row holds
+    no liquid within half the width."""
+    import numpy as np
+    row = np.asarray(rho[y]) > mid
+    n = row.size
+
+    def edge(step):
+        d = 0
+        while d < n // 2 and not row[(xc + step * d) % n]:
+            d += 1
+        if d >= n // 2:
+            return None
+        while d < n // 2 and row[(xc + step * d) % n]:
+            d += 1
+        return d - 1
+
+    r, l = edge(1), edge(-1)
+    return 0.0 if r is None or l is None else (r + l + 1) / 2.0
+
+
+def phase_mismatch(a, b, mid):
+    """Nodes on different sides of the midpoint density in a and b, and the
+    interface links of a (the mean outline displacement is their ratio)."""
+    import numpy as np
+    pa, pb = a > mid, b > mid
+    links = int((np.diff(pa.astype(np.int8), axis=1) != 0).sum() +
+                (np.diff(pa.astype(np.int8), axis=0) != 0).sum())
+    return int((pa != pb).sum()), links
+
+
+def splash_config(precision="mixed", steps=10_000, every=100):
+    """Drop splashing (Sec. 5.5): a drop of diameter 200 falling at 0.1 onto a
+    film of thickness 100 on the bottom wall of a 2048 x 1024 channel (periodic
+    in x, walls in y), CS T_r 0.55, k 0.5, tau 1 (Re = U D / nu = 120); once in
+    a static frame and once in a frame moving at 0.05 (fluid and walls), run
+    side by side.  Reports throughput (CUDA events around the stepping only),
+    mass drift, the spreading radius r(t) on the row four nodes above the film
+    against r/D = C sqrt(U t / D) shortly after impact (t* = U t / D from 0.3 to
+    1.3, t from the nominal contact, (height - radius) / U), and the outline
+    mismatch between the two frames over time."""
+    import numpy as np
+    import torch
+    import paper_1906_09530_gb300 as P
+    from paper_1906_09530_gb300 import workloads as W
+    c = SPLASH
+    nx, ny = c["nx"], c["ny"]
+    rg, rl = P.lbm_maxwell(c["T_r"])
+    mid = 0.5 * (rg + rl)
+    D, U = 2 * c["radius"], -c["u_drop"]
+    t_c = (c["height"] - c["radius"]) / U
+    yprobe = c["film"] + 4
+    frames = (("static", 0.0), ("moving_frame", c["u_shift"]))
+    sims, m0 = {}, {}
+    for name, us in frames:
+        sims[name] = P.Simulation(nx, ny, c["T_r"], c["kappa"], c["tau"], c["k"],
+                                  fd_order=c["order"], precision=precision, walls_y=True,
+                                  wall_ux=(us, us))
+        sims[name].set_fields(*W.splash(nx, ny, rg, rl, c["film"], c["radius"], c["height"],
+                                        c["width"], c["u_drop"], us))
+        m0[name] = sims[name].diag()[0]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ms = {n: 0.0 for n, _ in frames}
+    rs = {n: [] for n, _ in frames}
+    ts, gal = [], {}
+    for k in range(steps // every):
+        rho = {}
+        for name, us in frames:
+            sim = sims[name]
+            torch.cuda.synchronize()
+            ev[0].record()
+            sim.step(every)
+            ev[1].record()
+            torch.cuda.synchronize()
+            ms[name] += ev[0].elapsed_time(ev[1])
+            rho[name] = sim.fields()[0]
+            xc = int(round(nx / 2 + us * sim.t)) % nx
+            rs[name].append(spreading_radius(rho[name], yprobe, xc, mid))
+        t = sims["static"].t
+        ts.append(t)
+        tstar = U * (t - t_c) / D
+        if (k + 1) % 10 == 0:
+            shifted = np.roll(rho["moving_frame"], -int(round(c["u_shift"] * t)), axis=1)
+            bad, links = phase_mismatch(rho["static"], shifted, mid)
+            gal[f"{tstar:.2f}"] = {"mismatch_nodes": bad, "interface_links": links}
+    ts = np.array(ts, dtype=np.float64)
+    tstar = U * (ts - t_c) / D
+    res = {}
+    for name, _ in frames:
+        sim = sims[name]
+        m1, vmax = sim.diag()[:2]
+        sim.close()
+        r = np.array(rs[name])
+        sel = (tstar >= 0.3) & (tstar <= 1.3) & (r > 0)  # shortly after impact
+        sq = np.sqrt(tstar[sel])
+        C = float((r[sel] / D) @ sq / (sq @ sq)) if sel.any() else None
+        expo = (float(np.polyfit(np.log(tstar[sel]), np.log(r[sel] / D), 1)[0])
+                if sel.sum() > 2 else None)
+        res[name] = {"mlups": nx * ny * steps / (ms[name] / 1e3) / 1e6,
+                     "ms_per_step": ms[name] / steps,
+                     "mass_rel_drift": abs(m1 - m0[name]) / m0[name], "max_v_end": vmax,
+                     "spread_C": C, "spread_exponent": expo,
+                     "r_over_D": {f"{a:.2f}": round(float(b / D), 4)
+                                  for a, b in zip(tstar[4::5], r[4::5]) if a > 0}}
+    return {"workload": f"splash-{nx}x{ny}-D{int(D)}-U{U}-film{c['film']}-Tr{c['T_r']}"
+                        f"-k{c['k']}-{precision}",
+            "steps": steps, "density_ratio": rl / rg, "reynolds": U * D / ((c["tau"] - 0.5) / 3),
+            **res,
+            "galilean": {"frame_speed": c["u_shift"], "by_tstar": gal},
+            "timing": "CUDA events around lbm_step chunks of 100 steps; fields read "
+                      "between chunks (not timed)"}
+
+
 def surrogate_demo():
     """The learned warm start: a surrogate trained on 256 equilibrium slabs
     (T_r 0.33-0.5, kappa-hat 0.1, k 0.2) by the library's MLP kernels, then
@@ -458,6 +577,8 @@ def main():
                     help="skip the batched-instances line")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the 4096^2 line (default: measured after the main one)")
+    ap.add_argument("--no-splash", action="store_true",
+                    help="skip the drop-splashing line (walls, 2048 x 1024, 2 x 10 000 steps)")
     args = ap.parse_args()
     w = dict(WORKLOAD)
     if args.size != 1024:
@@ -597,6 +718,8 @@ def main():
                                             k=0.3, width=4.0 / 0.3)
     if not args.no_batch and args.precision == "mixed":
         line["batch"] = batch_config(min(args.steps, 50), max(args.warmup // 10, 3))
+    if rank == 0 and not args.no_splash:
+        line["splash"] = splash_config(args.precision)
     if rank == 0 and args.surrogate:
         line["surrogate"] = surrogate_demo()
     if rank == 0 and not args.no_equilibrium:

@@ -72,7 +72,17 @@ enum { LBM_PREC_FP64 = 0, LBM_PREC_MIXED = 1, LBM_PREC_MIXED_DF = 2 };
 
 typedef struct {
     int32_t nx, ny;                 /* lattice size, each >= 8 */
-    int32_t periodic_x, periodic_y; /* must both be 1 (walls: LBM_ENOTIMPL) */
+    int32_t periodic_x, periodic_y; /* periodic_x must be 1 (LBM_ENOTIMPL otherwise);
+                                       periodic_y = 0 puts solid walls below row 0 and
+                                       above row ny-1: halfway bounce-back for the
+                                       populations (walls at rest unless
+                                       lbm_set_wall_velocity moves them), and the
+                                       density and mu-hat extended evenly about the
+                                       walls for their y-derivatives (the first ghost
+                                       takes its fluid neighbour's value, Sec. 5.5;
+                                       d_yy rho is the compact scheme applied twice
+                                       along the extended line).  Batches are
+                                       periodic only. */
 } lbm_grid;
 
 typedef struct {
@@ -220,6 +230,14 @@ int64_t lbm_failed_step(const lbm_ctx *ctx);
 
 /* Host wait limit, in seconds, for lbm_step / lbm_check / copies (default 600). */
 lbm_status lbm_set_timeout(lbm_ctx *ctx, double seconds);
+
+/* Walls moving along x, as seen from a moving reference frame (Sec. 5.5):
+ * u_bottom, u_top are the x-velocities of the wall below row 0 and above row
+ * ny-1, lattice units.  The population reflected at a wall moving at U gains
+ * -2 w_i rho (e_i . U) / c_s^2 (Ladd's moving-wall bounce-back), rho the node's
+ * own density; mass is conserved.  Takes effect from the next step.
+ * LBM_EINVAL if the grid has no walls or |u| >= 0.5. */
+lbm_status lbm_set_wall_velocity(lbm_ctx *ctx, double u_bottom, double u_top);
 
 /* ---- Batches: many independent instances advanced together -------------
  *

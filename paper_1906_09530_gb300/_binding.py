@@ -100,6 +100,7 @@ def lib():
             "lbm_time": (C.c_int64, [_vp]),
             "lbm_failed_step": (C.c_int64, [_vp]),
             "lbm_set_timeout": (C.c_int, [_vp, C.c_double]),
+            "lbm_set_wall_velocity": (C.c_int, [_vp, C.c_double, C.c_double]),
             "lbm_batch_workspace_bytes": (C.c_size_t, [C.POINTER(LbmInstance), _i32,
                                                         C.POINTER(LbmOpts)]),
             "lbm_batch_init": (C.c_int, [C.POINTER(_vp), C.POINTER(LbmInstance), _i32,
@@ -240,12 +241,15 @@ class Simulation:
 
     def __init__(self, nx, ny, T_r, kappa, tau, mesh_coeff, fd_order=6,
                  precision="fp64", mu_max=math.inf, mu_cap_steps=0, eos=None,
-                 device=None, stream=None, collision="bgk", mrt_rates=PAPER_MRT):
+                 device=None, stream=None, collision="bgk", mrt_rates=PAPER_MRT,
+                 walls_y=False, wall_ux=(0.0, 0.0)):
+        """`walls_y`: solid walls below the first and above the last row (else
+        periodic in y); `wall_ux`: their x-velocities (bottom, top)."""
         import torch
         self.nx, self.ny = nx, ny
         self.device = torch.device(device if device is not None else "cuda")
         prec = _PRECISIONS[precision]
-        self.grid = LbmGrid(nx, ny, 1, 1)
+        self.grid = LbmGrid(nx, ny, 1, 0 if walls_y else 1)
         self.opts = _opts(prec, fd_order, mu_max, mu_cap_steps, collision, mrt_rates)
         self.eos = eos or cs_eos()
         nbytes = lib().lbm_workspace_bytes(C.byref(self.grid), C.byref(self.opts))
@@ -259,6 +263,8 @@ class Simulation:
                                   T_r, kappa, tau, mesh_coeff, C.byref(self.opts),
                                   self.ws.data_ptr(), nbytes, self.stream.cuda_stream),
                    "lbm_init")
+        if walls_y and any(wall_ux):
+            self.set_wall_velocity(*wall_ux)
 
     # -- state ------------------------------------------------------------
     def set_fields(self, rho, ux=None, uy=None):
@@ -327,6 +333,9 @@ class Simulation:
         v = [C.c_double() for _ in range(4)]
         _check(lib().lbm_diag(self.ctx, *[C.byref(x) for x in v]), "lbm_diag")
         return tuple(x.value for x in v)
+
+    def set_wall_velocity(self, u_bottom, u_top):
+        _check(lib().lbm_set_wall_velocity(self.ctx, u_bottom, u_top), "lbm_set_wall_velocity")
 
     def set_timeout(self, seconds):
         _check(lib().lbm_set_timeout(self.ctx, seconds), "lbm_set_timeout")

@@ -32,6 +32,8 @@ struct lbm_ctx {
     size_t N, plane;
     int prec, fd_order;
     bool rho_df;  // mixed: density lines in double-float (else FP32)
+    bool walls_y; // solid walls below row 0 and above row ny-1 (Sec. 5.5)
+    Walls walls;  // the same, with the walls' x-velocities, for the collide pass
     bool mrt;     // MRT collision (Eq. 4) with the rates below
     MrtRates rates;
     double T, Tc, rhoc, kappa, tau, k;
@@ -124,26 +126,27 @@ lbm_status enqueue_force(lbm_ctx* c, cudaStream_t s, int bump, cudaEvent_t* ev =
         // x|y lines of rho together, mu-hat pointwise, x|y lines of mu-hat + force
         if (c->rho_df)
             CK(lines_mixed_rho_xy(c->m_rh, c->m_rl, c->m_dxr, c->m_dxx, c->m_dyr, c->m_dyy, nx,
-                                  ny, o, c->dst, bump, s));
+                                  ny, o, c->dst, bump, s, c->walls_y));
         else
             CK(lines_mixed_rho_xy_f32(c->m_rh, c->m_dxr, c->m_dxx, c->m_dyr, c->m_dyy, nx, ny, o,
-                                      c->dst, bump, s));
+                                      c->dst, bump, s, c->walls_y));
         CK(mark(0));
         CK(launch_mu_mixed(c->m_rh, c->m_dxx, c->m_dyy, nx, ny, c->phys, c->dst, s));
         CK(mark(1));
         CK(lines_mixed_force_xy(c->m_dxx, c->m_rh, c->m_dxr, c->m_dyr, c->m_Fx, c->m_Fy, nx, ny,
-                                o, s));
+                                o, s, c->walls_y));
         CK(mark(2));
         CK(mark(3));
         return LBM_OK;
     }
     CK(lines_fp64_rho_x(c->rho, c->dxr, c->dxx, nx, ny, o, c->dst, bump, s));
     CK(mark(0));
-    CK(lines_fp64_rho_y_mu(c->rho, c->dxx, c->dyr, c->mu, nx, ny, o, c->phys, c->dst, s));
+    CK(lines_fp64_rho_y_mu(c->rho, c->dxx, c->dyr, c->mu, nx, ny, o, c->phys, c->dst, s,
+                           c->walls_y));
     CK(mark(1));
     CK(lines_fp64_force(c->mu, c->rho, c->dxr, c->Fx, nx, ny, 0, o, s));
     CK(mark(2));
-    CK(lines_fp64_force(c->mu, c->rho, c->dyr, c->Fy, nx, ny, 1, o, s));
+    CK(lines_fp64_force(c->mu, c->rho, c->dyr, c->Fy, nx, ny, 1, o, s, c->walls_y));
     CK(mark(3));
     return LBM_OK;
 }
@@ -155,11 +158,11 @@ lbm_status enqueue_collide(lbm_ctx* c, cudaStream_t s, int from) {
         CK(launch_collide_stream<double>((const double*)c->f[from], (double*)c->f[to], c->Fx,
                                          c->Fy, c->rho, c->nx, c->ny, c->plane,
                                          c->phys.omega, c->mrt ? &c->rates : nullptr, c->dst,
-                                         s));
+                                         s, c->walls));
     else
         CK(launch_cs_mixed((const float*)c->f[from], (float*)c->f[to], c->m_Fx, c->m_Fy,
                            c->m_rh, c->m_rl, c->nx, c->ny, c->plane, c->phys.omega,
-                           c->mrt ? &c->rates : nullptr, c->dst, s));
+                           c->mrt ? &c->rates : nullptr, c->dst, s, c->walls));
     return LBM_OK;
 }
 
@@ -287,7 +290,7 @@ lbm_status lbm_init(lbm_ctx** out, const lbm_grid* grid, const lbm_eos* eos, dou
     if (!out) return LBM_EINVAL;
     *out = nullptr;
     if (!grid_ok(grid) || !opts_ok(opts) || !eos) return LBM_EINVAL;
-    if (!grid->periodic_x || !grid->periodic_y) return LBM_ENOTIMPL;
+    if (!grid->periodic_x) return LBM_ENOTIMPL;  // walls are built in y only
     if (!eos_valid(eos)) return LBM_EINVAL;
     if (!(T_r > 0 && T_r < 1) || !(kappa > 0) || !(tau > 0.5) ||
         !(mesh_coeff > 0 && mesh_coeff <= 1))
@@ -313,6 +316,8 @@ lbm_status lbm_init(lbm_ctx** out, const lbm_grid* grid, const lbm_eos* eos, dou
     c->fd_order = opts->fd_order;
     c->rho_df = opts->prec == LBM_PREC_MIXED_DF;
     c->mrt = opts->collision == LBM_COLLIDE_MRT;
+    c->walls_y = !grid->periodic_y;
+    c->walls.on = c->walls_y;
     c->rates = MrtRates{opts->s_e, opts->s_eps, opts->s_q};
     if (opts->prec == LBM_PREC_MIXED) {
         double rg, rl;
@@ -398,6 +403,15 @@ void lbm_free(lbm_ctx* c) {
 lbm_status lbm_set_timeout(lbm_ctx* c, double seconds) {
     if (!c || !(seconds > 0)) return LBM_EINVAL;
     c->timeout_s = seconds;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_wall_velocity(lbm_ctx* c, double u_bottom, double u_top) {
+    if (!c || !c->walls_y || !(std::fabs(u_bottom) < 0.5) || !(std::fabs(u_top) < 0.5))
+        return LBM_EINVAL;
+    c->walls.u[0] = u_bottom;
+    c->walls.u[1] = u_top;
+    drop_graphs(c);  // the captured collide launches hold the old velocities
     return LBM_OK;
 }
 

@@ -41,12 +41,20 @@ struct MrtRates {
     double se, seps, sq;
 };
 
+// Solid walls below row 0 and above row ny-1 (Sec. 5.5), halfway bounce-back;
+// u: the x-velocities of the bottom and the top wall (a moving frame).
+struct Walls {
+    bool on = false;
+    double u[2] = {0.0, 0.0};
+};
+
 // Launchers (all asynchronous on `s`).  Fields are FP64 [ny][nx]; populations
 // are [9][plane] of TF with plane >= nx*ny.
 template <typename TF>
 cudaError_t launch_collide_stream(const TF* fin, TF* fout, const double* Fx, const double* Fy,
                                   double* rho_out, int nx, int ny, size_t plane, double omega,
-                                  const MrtRates* mrt, DevState* st, cudaStream_t s);
+                                  const MrtRates* mrt, DevState* st, cudaStream_t s,
+                                  const Walls& walls = Walls());
 
 template <typename TF>
 cudaError_t launch_init_feq(const double* rho, const double* ux, const double* uy, TF* f,
@@ -75,7 +83,8 @@ cudaError_t launch_diag_final(const double* partials, int nparts, DevState* st, 
 // ---- mixed precision path (kernels_mixed.cu) ------------------------------
 cudaError_t launch_cs_mixed(const float* fin, float* fout, const float* Fx, const float* Fy,
                             float* rh, float* rl, int nx, int ny, size_t plane, double omega,
-                            const MrtRates* mrt, DevState* st, cudaStream_t s);
+                            const MrtRates* mrt, DevState* st, cudaStream_t s,
+                            const Walls& walls = Walls());
 cudaError_t launch_init_mixed(const double* rho, const double* ux, const double* uy, float* f,
                               float* rh, float* rl, int nx, int ny, size_t plane,
                               cudaStream_t s);
@@ -110,6 +119,8 @@ struct CsArgs {
     DevState* st;
     int mrt;                  // 0: BGK (Eq. 1); 1: MRT (Eq. 4) with the rates below
     float se, seps, sq;
+    int walls;                // 1: halfway bounce-back below row 0 and above row ny-1
+    float uw6[2];             // bottom / top wall x-velocity over 6 (moving walls)
 };
 struct CsBatchInst {
     CsArgs a;      // fin / fout are taken from f[] by the launch's `from`
@@ -169,7 +180,8 @@ struct MixedLinesView {
 CsArgs cs_mixed_args(const float* fin, float* fout, const float* Fx, const float* Fy,
                      float* rh, float* rl, int nx, int ny, size_t plane, double omega,
                      const MrtRates* mrt, DevState* st,
-                     int rows);  // rows <= 0: the default choice
+                     int rows,  // rows <= 0: the default choice
+                     const Walls& walls = Walls());
 int cs_mixed_blocks(const CsArgs& a);
 cudaError_t launch_cs_mixed_args(const CsArgs& a, cudaStream_t s);
 cudaError_t launch_cs_mixed_batch(const CsBatchInst* d, const int* map, int nblocks, int from,
@@ -196,16 +208,19 @@ cudaError_t lines_batch_launch(LineBatchKind kind, const void* d_desc, const int
 // above it, in double-float wherever a window spans more than a factor 32.
 constexpr double kDfRatio = 1e4;
 
-// Warp-cooperative compact-FD line solves (kernels_lines.cu).  axis 0: lines
+// Warp-cooperative compact-FD line solves (kernels_lines.cu).  With walls_y the
+// y-lines are extended evenly about both walls (a periodic line of period
+// 2 ny, the first ghost equal to its fluid neighbour, Sec. 5.5).  axis 0: lines
 // along x, 1: along y.  Passes 2-5 of the FP64 path and of the mixed path, and
 // the stand-alone derivatives.
 cudaError_t lines_fp64_rho_x(const double* rho, double* dxr, double* dxx, int nx, int ny,
                              int order, DevState* st, int bump, cudaStream_t s);
 cudaError_t lines_fp64_rho_y_mu(const double* rho, const double* dxx, double* dyr, double* mu,
                                 int nx, int ny, int order, const PhysParams& p, DevState* st,
-                                cudaStream_t s);
+                                cudaStream_t s, bool walls_y = false);
 cudaError_t lines_fp64_force(const double* mu, const double* rho, const double* dr, double* F,
-                             int nx, int ny, int axis, int order, cudaStream_t s);
+                             int nx, int ny, int axis, int order, cudaStream_t s,
+                             bool walls_y = false);
 cudaError_t lines_fp64_plain(const double* u, double* d1, double* d2, int nx, int ny, int axis,
                              int order, cudaStream_t s);
 // Mixed path, merged launches: the x- and y-lines of rho together (first and
@@ -213,14 +228,14 @@ cudaError_t lines_fp64_plain(const double* u, double* d1, double* d2, int nx, in
 // mu-hat together with the force epilogue.
 cudaError_t lines_mixed_rho_xy(const float* rh, const float* rl, float* dxr, float* dxx,
                                float* dyr, float* dyy, int nx, int ny, int order, DevState* st,
-                               int bump, cudaStream_t s);
+                               int bump, cudaStream_t s, bool walls_y = false);
 // The same in FP32 on the hi part of the density (below kDfRatio).
 cudaError_t lines_mixed_rho_xy_f32(const float* rh, float* dxr, float* dxx, float* dyr,
                                    float* dyy, int nx, int ny, int order, DevState* st, int bump,
-                                   cudaStream_t s);
+                                   cudaStream_t s, bool walls_y = false);
 cudaError_t lines_mixed_force_xy(const float* mu, const float* rh, const float* dxr,
                                  const float* dyr, float* Fx, float* Fy, int nx, int ny,
-                                 int order, cudaStream_t s);
+                                 int order, cudaStream_t s, bool walls_y = false);
 // mu-hat = k^2 mu0(rho) - kappa (d_xx + d_yy) rho (Eqs. 21, 33, Sec. 5.6), FP32,
 // written over d_xx rho (`dxx_mu`); flags bad values.
 cudaError_t launch_mu_mixed(const float* rh, float* dxx_mu, const float* dyy, int nx, int ny,

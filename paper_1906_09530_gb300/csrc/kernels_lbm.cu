@@ -53,12 +53,13 @@ __device__ __forceinline__ void raise_flag(DevState* st, unsigned bits, int64_t 
 // then every destination node gathers f_i*(x - e_i) from shared memory, writes
 // its nine populations once (coalesced, aligned) and its new density.
 // ---------------------------------------------------------------------------
-template <typename TF, int BX, int BY, bool MRT>
+template <typename TF, int BX, int BY, bool MRT, bool WALLS>
 __global__ void __launch_bounds__(BX* BY)
     k_collide_stream(const TF* __restrict__ fin, TF* __restrict__ fout,
                      const double* __restrict__ Fx, const double* __restrict__ Fy,
                      double* __restrict__ rho_out, int nx, int ny, size_t plane, TF omega,
-                     TF se, TF seps, TF sq, DevState* __restrict__ st) {
+                     TF se, TF seps, TF sq, TF uwb6, TF uwt6,
+                     DevState* __restrict__ st) {
     constexpr int HX = BX + 2, HY = BY + 2, HN = HX * HY;
     __shared__ TF sf[9][HN];
     const int tid = threadIdx.x + BX * threadIdx.y;
@@ -84,9 +85,21 @@ __global__ void __launch_bounds__(BX* BY)
         const int lx = threadIdx.x + 1, ly = threadIdx.y + 1;
         const size_t n = (size_t)y * nx + x;
         TF g[9];
+        // the node's density, for the momentum a moving wall gives
+        TF rw = TF(0);
+        if (WALLS && (y == 0 || y == ny - 1)) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) rw += sf[i][ly * HX + lx];
+        }
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            g[i] = sf[i][(ly - q_ey(i)) * HX + (lx - q_ex(i))];
+            const int ys = y - q_ey(i);
+            // halfway bounce-back at walls: the node's own opposite population,
+            // plus e_x rho U / 6 on the diagonals from a wall moving at U (Ladd)
+            if (WALLS && (ys < 0 || ys >= ny))
+                g[i] = sf[q_opp(i)][ly * HX + lx] + TF(q_ex(i)) * rw * (ys < 0 ? uwb6 : uwt6);
+            else
+                g[i] = sf[i][(ly - q_ey(i)) * HX + (lx - q_ex(i))];
             fout[i * plane + n] = g[i];
         }
         rho_out[n] = (double)sum9(g);
@@ -250,16 +263,25 @@ constexpr int kCsBX = 32, kCsBY = 16;
 template <typename TF>
 cudaError_t launch_collide_stream(const TF* fin, TF* fout, const double* Fx, const double* Fy,
                                   double* rho_out, int nx, int ny, size_t plane, double omega,
-                                  const MrtRates* mrt, DevState* st, cudaStream_t s) {
+                                  const MrtRates* mrt, DevState* st, cudaStream_t s,
+                                  const Walls& walls) {
+    const TF ub = (TF)(walls.u[0] / 6.0), ut = (TF)(walls.u[1] / 6.0);
     dim3 block(kCsBX, kCsBY);
     dim3 grid((nx + kCsBX - 1) / kCsBX, (ny + kCsBY - 1) / kCsBY);
-    if (mrt)
-        k_collide_stream<TF, kCsBX, kCsBY, true><<<grid, block, 0, s>>>(
-            fin, fout, Fx, Fy, rho_out, nx, ny, plane, (TF)omega, (TF)mrt->se, (TF)mrt->seps,
-            (TF)mrt->sq, st);
+    const TF se = mrt ? (TF)mrt->se : TF(0), seps = mrt ? (TF)mrt->seps : TF(0),
+             sq = mrt ? (TF)mrt->sq : TF(0);
+#define CPLBM_CS(M, W)                                                                    \
+    k_collide_stream<TF, kCsBX, kCsBY, M, W><<<grid, block, 0, s>>>(                      \
+        fin, fout, Fx, Fy, rho_out, nx, ny, plane, (TF)omega, se, seps, sq, ub, ut, st)
+    if (mrt && walls.on)
+        CPLBM_CS(true, true);
+    else if (mrt)
+        CPLBM_CS(true, false);
+    else if (walls.on)
+        CPLBM_CS(false, true);
     else
-        k_collide_stream<TF, kCsBX, kCsBY, false><<<grid, block, 0, s>>>(
-            fin, fout, Fx, Fy, rho_out, nx, ny, plane, (TF)omega, TF(0), TF(0), TF(0), st);
+        CPLBM_CS(false, false);
+#undef CPLBM_CS
     return cudaGetLastError();
 }
 
@@ -320,7 +342,7 @@ cudaError_t launch_f_from_double(const double* in, TF* f, size_t n, cudaStream_t
     template cudaError_t launch_collide_stream<TF>(const TF*, TF*, const double*,            \
                                                    const double*, double*, int, int, size_t, \
                                                    double, const MrtRates*, DevState*,       \
-                                                   cudaStream_t);                            \
+                                                   cudaStream_t, const Walls&);              \
     template cudaError_t launch_init_feq<TF>(const double*, const double*, const double*,    \
                                              TF*, double*, int, int, size_t, cudaStream_t);  \
     template cudaError_t launch_rho_from_f<TF>(const TF*, double*, int, int, size_t,         \

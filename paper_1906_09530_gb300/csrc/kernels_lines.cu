@@ -151,6 +151,8 @@ struct LineGeo {
     int nwin;       // windows per line
     int ngroups;    // line groups of kNL
     int vec;        // nx % 4 == 0: 16-byte staging (x-lines) and epilogue (float fields)
+    int period;     // n (periodic line), or 2 n (y-line between walls, extended evenly)
+    int mirror;     // positions n .. 2n-1 of the period read position 2n-1-p
 };
 
 // Asynchronous global -> shared copies (cp.async): the staging loads need no
@@ -413,8 +415,8 @@ __device__ __forceinline__ void lines_body(In& in, const LineGeo& g, const LineC
 
     // ---- stage the window: positions s-H-4 .. s-H+kW+3 of kNL lines ----
     constexpr int LWIN = kW + 8;
-    const int p0 = wrapi((long long)s - g.H - 4, g.n);  // line position of window slot 0
-    const bool short_line = g.n < LWIN;
+    const int p0 = wrapi((long long)s - g.H - 4, g.period);  // period position of slot 0
+    const bool short_line = g.period < LWIN;
     if (AXIS == 0 && g.vec) {
         // rows: 16-byte chunks (p0, H and own are multiples of 4, and so is the
         // line length, so no chunk straddles the periodic wrap)
@@ -425,8 +427,8 @@ __device__ __forceinline__ void lines_body(In& in, const LineGeo& g, const LineC
             const int line = line0 + l;
             if (line < g.nlines) {
                 int p = p0 + q;
-                if (short_line) p %= g.n;
-                else if (p >= g.n) p -= g.n;
+                if (short_line) p %= g.period;
+                else if (p >= g.period) p -= g.period;
                 in.stage4(tin, l * kLW + q, kPS, (size_t)line * g.ls + (size_t)p);
             } else {
 #pragma unroll
@@ -446,8 +448,9 @@ __device__ __forceinline__ void lines_body(In& in, const LineGeo& g, const LineC
             const int line = line0 + l;
             if (line < g.nlines) {
                 int p = p0 + q;
-                if (short_line) p %= g.n;
-                else if (p >= g.n) p -= g.n;
+                if (short_line) p %= g.period;
+                else if (p >= g.period) p -= g.period;
+                if (g.mirror && p >= g.n) p = 2 * g.n - 1 - p;
                 in.stage(tin, l * kLW + q, kPS, (size_t)line * g.ls + (size_t)p * g.ps);
             } else {
                 P1::sput(tin, l * kLW + q, kPS, P1::zero());
@@ -807,7 +810,10 @@ int halo(int order, double eps1, bool second, double eps2) {
     return (h1 > h2 ? h1 : h2) + 1;
 }
 
-LineGeo make_geo(int nx, int ny, int axis, int H) {
+// Walls in y (walls_y): the y-lines are extended evenly about both walls, a
+// periodic line of period 2 ny whose first ghost equals its fluid neighbour
+// (the wall rule of Sec. 5.5); only the ny fluid positions are owned.
+LineGeo make_geo(int nx, int ny, int axis, int H, bool walls_y = false) {
     LineGeo g;
     if (axis == 0) {
         g.n = nx; g.nlines = ny; g.ps = 1; g.ls = nx;
@@ -823,6 +829,8 @@ LineGeo make_geo(int nx, int ny, int axis, int H) {
     g.nwin = (g.n + g.own - 1) / g.own;
     g.ngroups = (g.nlines + kNL - 1) / kNL;
     g.vec = nx % 4 == 0;
+    g.mirror = axis == 1 && walls_y;
+    g.period = g.mirror ? 2 * g.n : g.n;
     return g;
 }
 
@@ -854,7 +862,7 @@ cudaError_t launch_lines_t(In in, const LineGeo& g, int order, Epi epi, DevState
 template <class P1, class P2, bool SIXTH, bool SECOND, class InX, class EpiX, class InY,
           class EpiY>
 cudaError_t launch_xy_t(InX inx, EpiX ex, InY iny, EpiY ey, int nx, int ny, int order, int H,
-                        DevState* st, int bump, cudaStream_t s) {
+                        DevState* st, int bump, bool walls_y, cudaStream_t s) {
     auto kern = k_lines_xy<P1, P2, SIXTH, SECOND, InX, EpiX, InY, EpiY>;
     const size_t smem = smem_bytes<P1, P2, SECOND>();
     static bool attr = false;  // one flag per kernel instantiation
@@ -864,7 +872,7 @@ cudaError_t launch_xy_t(InX inx, EpiX ex, InY iny, EpiY ey, int nx, int ny, int 
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    const LineGeo gx = make_geo(nx, ny, 0, H), gy = make_geo(nx, ny, 1, H);
+    const LineGeo gx = make_geo(nx, ny, 0, H), gy = make_geo(nx, ny, 1, H, walls_y);
     const int nbx = gx.ngroups * gx.nwin;
     const unsigned blocks = (unsigned)(nbx + gy.ngroups * gy.nwin);
     kern<<<blocks, kNL * 32, smem, s>>>(inx, gx, ex, iny, gy, ey, make_const<P1>(order),
@@ -875,18 +883,21 @@ cudaError_t launch_xy_t(InX inx, EpiX ex, InY iny, EpiY ey, int nx, int ny, int 
 
 template <class P1, class P2, bool SECOND, class InX, class EpiX, class InY, class EpiY>
 cudaError_t launch_xy(InX inx, EpiX ex, InY iny, EpiY ey, int nx, int ny, int order,
-                      double eps1, double eps2, DevState* st, int bump, cudaStream_t s) {
+                      double eps1, double eps2, DevState* st, int bump, cudaStream_t s,
+                      bool walls_y = false) {
     const int H = halo(order, eps1, SECOND, eps2);
     if (order == 6)
-        return launch_xy_t<P1, P2, true, SECOND>(inx, ex, iny, ey, nx, ny, order, H, st, bump, s);
-    return launch_xy_t<P1, P2, false, SECOND>(inx, ex, iny, ey, nx, ny, order, H, st, bump, s);
+        return launch_xy_t<P1, P2, true, SECOND>(inx, ex, iny, ey, nx, ny, order, H, st, bump,
+                                                 walls_y, s);
+    return launch_xy_t<P1, P2, false, SECOND>(inx, ex, iny, ey, nx, ny, order, H, st, bump,
+                                              walls_y, s);
 }
 
 // dispatch on axis and scheme order
 template <class P1, class P2, bool SECOND, class In, class Epi>
 cudaError_t launch_lines(In in, int nx, int ny, int axis, int order, double eps1, double eps2,
-                         Epi epi, DevState* st, int bump, cudaStream_t s) {
-    const LineGeo g = make_geo(nx, ny, axis, halo(order, eps1, SECOND, eps2));
+                         Epi epi, DevState* st, int bump, cudaStream_t s, bool walls_y = false) {
+    const LineGeo g = make_geo(nx, ny, axis, halo(order, eps1, SECOND, eps2), walls_y);
     if (axis == 0) {
         if (order == 6)
             return launch_lines_t<0, P1, P2, true, SECOND>(in, g, order, epi, st, bump, s);
@@ -940,15 +951,17 @@ cudaError_t lines_fp64_rho_x(const double* rho, double* dxr, double* dxx, int nx
 }
 cudaError_t lines_fp64_rho_y_mu(const double* rho, const double* dxx, double* dyr, double* mu,
                                 int nx, int ny, int order, const PhysParams& p, DevState* st,
-                                cudaStream_t s) {
+                                cudaStream_t s, bool walls_y) {
     EpiMu<double, double, double> epi{dyr, mu, rho, dxx, eos_const<double>(p), p.k2, p.kappa,
                                       p.mu_cap, p.cap_steps, false};
-    return launch_lines<PolD, PolD, true>(InD{rho}, nx, ny, 1, order, kEpsD, kEpsD, epi, st, 0, s);
+    return launch_lines<PolD, PolD, true>(InD{rho}, nx, ny, 1, order, kEpsD, kEpsD, epi, st, 0, s,
+                                          walls_y);
 }
 cudaError_t lines_fp64_force(const double* mu, const double* rho, const double* dr, double* F,
-                             int nx, int ny, int axis, int order, cudaStream_t s) {
+                             int nx, int ny, int axis, int order, cudaStream_t s, bool walls_y) {
     return launch_lines<PolD, PolD, false>(InD{mu}, nx, ny, axis, order, kEpsD, kEpsD,
-                                           EpiForce<double, double>{F, rho, dr}, nullptr, 0, s);
+                                           EpiForce<double, double>{F, rho, dr}, nullptr, 0, s,
+                                           walls_y);
 }
 cudaError_t lines_fp64_plain(const double* u, double* d1, double* d2, int nx, int ny, int axis,
                              int order, cudaStream_t s) {
@@ -962,24 +975,24 @@ cudaError_t lines_fp64_plain(const double* u, double* d1, double* d2, int nx, in
 // ---- mixed path ----
 cudaError_t lines_mixed_rho_xy(const float* rh, const float* rl, float* dxr, float* dxx,
                                float* dyr, float* dyy, int nx, int ny, int order, DevState* st,
-                               int bump, cudaStream_t s) {
+                               int bump, cudaStream_t s, bool walls_y) {
     return launch_xy<PolDF, PolF, true>(InDF{rh, rl}, EpiStore<float, float>{dxr, dxx},
                                         InDF{rh, rl}, EpiStore<float, float>{dyr, dyy}, nx, ny,
-                                        order, kEpsDF, kEpsF, st, bump, s);
+                                        order, kEpsDF, kEpsF, st, bump, s, walls_y);
 }
 cudaError_t lines_mixed_rho_xy_f32(const float* rh, float* dxr, float* dxx, float* dyr,
                                    float* dyy, int nx, int ny, int order, DevState* st, int bump,
-                                   cudaStream_t s) {
+                                   cudaStream_t s, bool walls_y) {
     return launch_xy<PolF, PolF, true>(InF{rh}, EpiStore<float, float>{dxr, dxx}, InF{rh},
                                        EpiStore<float, float>{dyr, dyy}, nx, ny, order, kEpsF,
-                                       kEpsF, st, bump, s);
+                                       kEpsF, st, bump, s, walls_y);
 }
 cudaError_t lines_mixed_force_xy(const float* mu, const float* rh, const float* dxr,
                                  const float* dyr, float* Fx, float* Fy, int nx, int ny,
-                                 int order, cudaStream_t s) {
+                                 int order, cudaStream_t s, bool walls_y) {
     return launch_xy<PolF, PolF, false>(InF{mu}, EpiForce<float, float>{Fx, rh, dxr}, InF{mu},
                                         EpiForce<float, float>{Fy, rh, dyr}, nx, ny, order,
-                                        kEpsF, kEpsF, nullptr, 0, s);
+                                        kEpsF, kEpsF, nullptr, 0, s, walls_y);
 }
 cudaError_t lines_mixed_plain(const float* uh, const float* ul, float* d1, float* d2, int nx,
                               int ny, int axis, int order, cudaStream_t s) {

@@ -58,7 +58,9 @@ __device__ __forceinline__ void raise_flag(DevState* st, unsigned bits, int64_t 
 // ---------------------------------------------------------------------------
 constexpr int kSwWarps = 4;  // warps per block
 
-template <bool MRT>
+// WALLS: the bounce-back rows are compiled only into the walled variant, so
+// the periodic kernel keeps its register count.
+template <bool MRT, bool WALLS>
 __device__ __forceinline__ void cs_mixed_body(const CsArgs& a, int wid) {
     const float* __restrict__ fin = a.fin;
     float* __restrict__ fout = a.fout;
@@ -114,6 +116,23 @@ __device__ __forceinline__ void cs_mixed_body(const CsArgs& a, int wid) {
         g[6] = __shfl_down_sync(0xffffffffu, A[6], 1);
         g[7] = __shfl_down_sync(0xffffffffu, C[7], 1);
         g[8] = __shfl_up_sync(0xffffffffu, C[8], 1);
+        if (WALLS && (y == 0 || y == ny - 1)) {
+            // halfway bounce-back: what would come from a solid row is the
+            // node's own population that left toward it, reversed; a wall
+            // moving along x at U adds e_x rho U / 6 to the reflected
+            // diagonals (Ladd), rho the node's density
+            const float c = __fmul_rn(sum9_exact(B).hi, a.uw6[y == 0 ? 0 : 1]);
+            if (y == 0) {
+                g[2] = B[4];
+                g[5] = __fadd_rn(B[7], c);
+                g[6] = __fsub_rn(B[8], c);
+            }
+            if (y == ny - 1) {
+                g[4] = B[2];
+                g[7] = __fsub_rn(B[5], c);
+                g[8] = __fadd_rn(B[6], c);
+            }
+        }
         if (writer) {
             const size_t n = (size_t)y * nx + xo;
 #pragma unroll
@@ -131,9 +150,9 @@ __device__ __forceinline__ void cs_mixed_body(const CsArgs& a, int wid) {
     if (!ok) raise_flag(a.st, FLAG_RHO, a.st->t);
 }
 
-template <bool MRT>
+template <bool MRT, bool WALLS>
 __global__ void __launch_bounds__(kSwWarps * 32) k_cs_mixed_sw(CsArgs a) {
-    cs_mixed_body<MRT>(a, blockIdx.x * kSwWarps + (threadIdx.x >> 5));
+    cs_mixed_body<MRT, WALLS>(a, blockIdx.x * kSwWarps + (threadIdx.x >> 5));
 }
 
 // Batched: block b belongs to instance map[b]; its warps continue that
@@ -145,7 +164,7 @@ __global__ void __launch_bounds__(kSwWarps * 32)
     CsArgs a = D.a;
     a.fin = D.f[from];
     a.fout = D.f[1 - from];
-    cs_mixed_body<MRT>(a, ((int)blockIdx.x - D.blk0) * kSwWarps + (threadIdx.x >> 5));
+    cs_mixed_body<MRT, false>(a, ((int)blockIdx.x - D.blk0) * kSwWarps + (threadIdx.x >> 5));
 }
 
 // f = f^eq(rho, u) in FP64, stored as FP32; rho = DF sum of the stored floats.
@@ -314,7 +333,7 @@ inline unsigned grid_for(size_t n, int threads) {
 
 CsArgs cs_mixed_args(const float* fin, float* fout, const float* Fx, const float* Fy,
                      float* rh, float* rl, int nx, int ny, size_t plane, double omega,
-                     const MrtRates* mrt, DevState* st, int rows) {
+                     const MrtRates* mrt, DevState* st, int rows, const Walls& walls) {
     // rows per warp: 32 on large grids, fewer on small ones to keep >= ~4k warps
     const int nstrips = (nx + 29) / 30;
     if (rows <= 0) {
@@ -324,7 +343,8 @@ CsArgs cs_mixed_args(const float* fin, float* fout, const float* Fx, const float
     CsArgs a{fin, fout, Fx, Fy, rh, rl, nx, ny, plane, (float)omega, nstrips,
              (ny + rows - 1) / rows, rows, st, mrt ? 1 : 0,
              mrt ? (float)mrt->se : 0.0f, mrt ? (float)mrt->seps : 0.0f,
-             mrt ? (float)mrt->sq : 0.0f};
+             mrt ? (float)mrt->sq : 0.0f, walls.on ? 1 : 0,
+             {(float)(walls.u[0] / 6.0), (float)(walls.u[1] / 6.0)}};
     return a;
 }
 
@@ -334,18 +354,24 @@ int cs_mixed_blocks(const CsArgs& a) {
 }
 
 cudaError_t launch_cs_mixed_args(const CsArgs& a, cudaStream_t s) {
-    if (a.mrt)
-        k_cs_mixed_sw<true><<<cs_mixed_blocks(a), kSwWarps * 32, 0, s>>>(a);
+    const int nb = cs_mixed_blocks(a);
+    if (a.mrt && a.walls)
+        k_cs_mixed_sw<true, true><<<nb, kSwWarps * 32, 0, s>>>(a);
+    else if (a.mrt)
+        k_cs_mixed_sw<true, false><<<nb, kSwWarps * 32, 0, s>>>(a);
+    else if (a.walls)
+        k_cs_mixed_sw<false, true><<<nb, kSwWarps * 32, 0, s>>>(a);
     else
-        k_cs_mixed_sw<false><<<cs_mixed_blocks(a), kSwWarps * 32, 0, s>>>(a);
+        k_cs_mixed_sw<false, false><<<nb, kSwWarps * 32, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_cs_mixed(const float* fin, float* fout, const float* Fx, const float* Fy,
                             float* rh, float* rl, int nx, int ny, size_t plane, double omega,
-                            const MrtRates* mrt, DevState* st, cudaStream_t s) {
+                            const MrtRates* mrt, DevState* st, cudaStream_t s,
+                            const Walls& walls) {
     return launch_cs_mixed_args(
-        cs_mixed_args(fin, fout, Fx, Fy, rh, rl, nx, ny, plane, omega, mrt, st, 0), s);
+        cs_mixed_args(fin, fout, Fx, Fy, rh, rl, nx, ny, plane, omega, mrt, st, 0, walls), s);
 }
 
 cudaError_t launch_cs_mixed_batch(const CsBatchInst* d, const int* map, int nblocks, int from,

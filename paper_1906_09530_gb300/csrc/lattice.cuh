@@ -14,6 +14,11 @@ __host__ __device__ __forceinline__ constexpr int q_ey(int i) {
     return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
 }
 
+// Opposite direction: e_opp(i) = -e_i.
+__host__ __device__ __forceinline__ constexpr int q_opp(int i) {
+    return i == 0 ? 0 : (i <= 4 ? ((i + 1) % 4) + 1 : ((i - 3) % 4) + 5);
+}
+
 // Periodic index for v in [-1, n + 33), n >= 8 (tile halos): at most 5 steps.
 __device__ __forceinline__ int wrap_near(int v, int n) {
     if (v < 0) v += n;

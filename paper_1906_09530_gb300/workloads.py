@@ -12,6 +12,8 @@ fed from here, so their inputs are bit-identical.
               generator, so any node's value can be recomputed on its own.
   * batch     a seeded set of many independent instances (uneven grid sides and
               temperatures, drops and flat interfaces) for the batched path.
+  * splash    a liquid film on the bottom wall and a drop falling onto it
+              (Sec. 5.5), with an optional uniform shift of the reference frame.
 """
 import numpy as np
 
@@ -94,3 +96,17 @@ def batch_field(spec, rho_g, rho_l):
     if spec["kind"] == "drop":
         return drop(spec["nx"], spec["ny"], rho_g, rho_l, 0.25 * n, spec["width"])
     return flat(spec["nx"], spec["ny"], rho_g, rho_l, 0.5 * spec["ny"], spec["width"])
+
+
+def splash(nx, ny, rho_g, rho_l, film, radius, height, width, u_drop, u_shift=0.0):
+    """(rho, ux, uy): a film of thickness `film` on the bottom wall (rows 0 ..)
+    and a drop of the given radius whose centre is `height` above the film's
+    surface, at x = nx/2, moving at uy = u_drop; tanh edges of width W (Eq. 41).
+    u_shift adds a uniform ux everywhere (a moving reference frame)."""
+    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    film_phi = 0.5 * (1.0 - np.tanh(2.0 * (y - film) / width))
+    r = np.sqrt((x - nx / 2.0) ** 2 + (y - film - height) ** 2)
+    drop_phi = 0.5 * (1.0 - np.tanh(2.0 * (r - radius) / width))
+    phi = np.maximum(film_phi, drop_phi)
+    rho = rho_g + (rho_l - rho_g) * phi
+    return rho, np.full_like(rho, u_shift), u_drop * drop_phi

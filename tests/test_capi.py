@@ -130,6 +130,7 @@ def test_strerror_and_null_ctx():
     assert lib.lbm_step(None, 1) == B.LBM_EINVAL
     assert lib.lbm_time(None) == -1
     lib.lbm_free(None)
+    assert lib.lbm_set_wall_velocity(None, 0.0, 0.0) == B.LBM_EINVAL
 
 
 def test_oracle_and_library_share_nothing():

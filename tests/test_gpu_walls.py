@@ -1,0 +1,156 @@
+"""Walls in y on the GPU (periodic x; Sec. 5.5): halfway bounce-back and the
+evenly extended y-lines, against the oracle (pinned by test_oracle_walls.py).
+
+Case: a drop of radius 8 near the bottom wall of a 48 x 40 grid, falling at
+u_y = -0.02, CS T_r 0.6, k 0.5, kappa-hat 0.1, tau 1; in the moving-frame
+variant everything (fluid and walls) also moves at u_x = 0.05.  Tolerances
+are those of the periodic parity tests.  Then two properties at sizes the
+oracle does not reach: Couette flow between moving walls (exact for the
+method), and Sec. 5.5's Galilean check of a drop impact, whose outlines in a
+static and in a moving frame agree.
+"""
+import numpy as np
+import pytest
+
+from oracle import OracleSim, sim as S, thermo
+from paper_1906_09530_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+TC, _ = thermo.critical_point()
+NX, NY, TR, K = 48, 40, 0.6, 0.5
+
+
+def _fields(shift=0.0):
+    rg, rl = thermo.maxwell(TR)
+    rho = W.with_noise(W.drop(NX, NY, rg, rl, 8.0, 4.0, center=(NX / 2, 11.0)), 5, 1e-5)
+    return rho, np.full_like(rho, shift), np.full_like(rho, -0.02)
+
+
+def _pair(precision, collision="bgk", order=6, shift=0.0):
+    from paper_1906_09530_gb300 import Simulation
+    rho, ux, uy = _fields(shift)
+    g = Simulation(NX, NY, TR, 0.1, 1.0, K, fd_order=order, precision=precision,
+                   collision=collision, walls_y=True, wall_ux=(shift, shift))
+    g.set_fields(rho, ux, uy)
+    o = OracleSim(NX, NY, TR * TC, 0.1, 1.0, K, order, walls_y=True,
+                  mrt=S.PAPER_MRT if collision == "mrt" else None, wall_ux=(shift, shift))
+    o.set_fields(rho, ux, uy)
+    return g, o
+
+
+def rel_point(a, b):
+    return float(np.max(np.abs(a - b) / np.abs(b)))
+
+
+@pytest.mark.parametrize("order", [4, 6])
+def test_force_stage_t0_with_walls(cuda, order):
+    g, o = _pair("fp64", order=order)
+    rho, vx, vy, mu = g.fields()
+    orho, ovx, ovy, omu, _, _ = o.fields()
+    assert rel_point(rho, orho) <= 1e-14
+    assert np.abs(mu - omu).max() <= 1e-12 * np.abs(omu).max()
+    assert np.abs(vy - ovy).max() <= 1e-12 * np.abs(ovy).max()
+
+
+@pytest.mark.parametrize("collision", ["bgk", "mrt"])
+def test_fp64_steps_with_walls(cuda, collision):
+    g, o = _pair("fp64", collision)
+    g.step(301)
+    o.step(301)
+    rho, vx, vy, mu = g.fields()
+    orho, ovx, ovy, omu, _, _ = o.fields()
+    assert rel_point(rho, orho) <= 1e-10
+    assert np.abs(vy - ovy).max() <= 1e-8 * np.abs(ovy).max()
+    assert np.abs(mu - omu).max() <= 1e-8 * np.abs(omu).max()
+
+
+def test_fp64_steps_with_moving_walls(cuda):
+    g, o = _pair("fp64", shift=0.05)
+    g.step(301)
+    o.step(301)
+    rho, vx, vy, mu = g.fields()
+    orho, ovx, ovy, omu, _, _ = o.fields()
+    assert rel_point(rho, orho) <= 1e-10
+    assert np.abs(vx - ovx).max() <= 1e-8 * np.abs(ovx).max()
+    assert np.abs(vy - ovy).max() <= 1e-8 * np.abs(ovy).max()
+
+
+@pytest.mark.parametrize("precision,shift", [("mixed", 0.0), ("mixed_df", 0.0),
+                                             ("mixed", 0.05)])
+def test_mixed_steps_with_walls(cuda, precision, shift):
+    g, o = _pair(precision, shift=shift)
+    g.step(200)
+    o.step(200)
+    assert rel_point(g.fields()[0], o.fields()[0]) <= 1e-4
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
+def test_couette_flow(cuda, precision, tol):
+    """Steady Couette flow between walls at -0.01 and 0.03, with the walls half a
+    node outside the fluid: linear to rounding in FP64; FP32 populations leave
+    errors of order 1e-7 of the density."""
+    from paper_1906_09530_gb300 import Simulation
+    nx, ny, ub, ut = 64, 16, -0.01, 0.03
+    g = Simulation(nx, ny, 0.9, 0.1, 1.0, 1.0, fd_order=6, precision=precision,
+                   walls_y=True, wall_ux=(ub, ut))
+    g.set_fields(np.full((ny, nx), thermo.maxwell(0.9)[1]))  # uniform liquid
+    g.step(10_000)
+    rho, vx, vy, _ = g.fields()
+    y = np.arange(ny)[:, None]
+    assert np.abs(vx - (ub + (ut - ub) * (y + 0.5) / ny)).max() <= tol
+    assert np.abs(vy).max() <= tol
+
+
+def _phase_mismatch(a, b, mid):
+    """Nodes on different sides of the midpoint density in a and b, and the
+    number of interface links of a."""
+    pa, pb = a > mid, b > mid
+    links = (np.diff(pa.astype(np.int8), axis=1) != 0).sum() + \
+        (np.diff(pa.astype(np.int8), axis=0) != 0).sum()
+    return int((pa != pb).sum()), int(links)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_galilean_invariance_of_drop_impact(cuda, precision):
+    """Sec. 5.5: a drop (radius 24, u_y = -0.1) hits a film on the bottom wall
+    (320 x 160, CS T_r 0.55, density ratio 285); once in a static frame, once in
+    a frame moving at 0.05 (fluid and walls).  After 1600 steps the moving run,
+    shifted back by 80 nodes, has the static run's outline to within a mean
+    normal displacement of 0.2 node: fewer nodes change phase than a fifth of
+    the interface links.  The method's own figure (the oracle on this case)
+    is 46 nodes of 376 links."""
+    from paper_1906_09530_gb300 import Simulation
+    nx, ny, steps, us = 320, 160, 1600, 0.05
+    rg, rl = thermo.maxwell(0.55)
+    out = []
+    for u in (0.0, us):
+        g = Simulation(nx, ny, 0.55, 0.1, 1.0, 0.5, fd_order=6, precision=precision,
+                       walls_y=True, wall_ux=(u, u))
+        g.set_fields(*W.splash(nx, ny, rg, rl, 16, 24, 40, 8.0, -0.1, u))
+        g.step(steps)
+        out.append(g.fields())
+        g.close()
+    a = out[0][0]
+    b = np.roll(out[1][0], -int(round(us * steps)), axis=1)
+    bad, links = _phase_mismatch(a, b, 0.5 * (rg + rl))
+    assert links > 100 and bad <= 0.2 * links, (bad, links)
+
+
+def test_wall_velocity_needs_walls(cuda):
+    from paper_1906_09530_gb300 import LbmError, Simulation
+    g = Simulation(32, 32, 0.7, 0.1, 1.0, 0.5)
+    with pytest.raises(LbmError):
+        g.set_wall_velocity(0.01, 0.0)
+    g.close()
+    g = Simulation(32, 32, 0.7, 0.1, 1.0, 0.5, walls_y=True)
+    with pytest.raises(LbmError):
+        g.set_wall_velocity(0.5, 0.0)
+    g.set_wall_velocity(0.01, -0.01)
+    g.close()
+
+
+def test_mass_conserved_with_walls(cuda):
+    g, _ = _pair("fp64")
+    m0 = g.diag()[0]
+    g.step(500)
+    assert abs(g.diag()[0] - m0) / m0 <= 1e-12
