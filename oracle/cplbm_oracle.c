@@ -320,6 +320,7 @@ static void moments(const orc_params *p, const double *f, double *rho, double *u
  *   d_xx rho = D_x(D_x rho), likewise y   "applying CFM twice", Sec. 4.3
  *                                         (with walls: along the extended line)
  *   mu-hat = k^2 mu0(rho) - kappa (d_xx rho + d_yy rho)          Eq. 33
+ *            (mu0 = +infinity at or beyond the repulsive pole)
  *   mu-hat <- min(mu-hat, k^2 mu_max) while t < mu_cap_steps    Sec. 5.6
  *   F = -rho grad(mu-hat) + c_s^2 grad(rho)                     Eq. 12
  * Any output pointer may be NULL except Fx, Fy.  Returns 0 or -1. */
@@ -338,9 +339,18 @@ int orc_force_stage(const orc_params *p, int64_t t, const double *rho, double *m
     err |= cfd_x(p, dxr, dxxr);
     err |= cfd_yy(p, rho, dyyr);
     double k2 = p->k * p->k;
+    /* the repulsive pole: b rho / 4 = 1 (CS, Eq. 21) or b rho = 1 (Eqs. 15-19) */
+    double bpole = p->eos == 0 ? p->b / 4.0 : p->b;
     for (size_t n = 0; n < N; ++n) {
-        double m = k2 * orc_mu0(p->eos, rho[n], p->T, p->a, p->b, p->R, p->eos_alpha) -
-                   p->kappa * (dxxr[n] + dyyr[n]);
+        /* mu0 grows without bound as rho approaches the pole from below; at or
+         * beyond it mu0 is taken as that limit, +infinity (where the printed
+         * formula has no real value, or for CS turns negative).  With the upper
+         * limit active this gives k^2 mu_max (Sec. 5.6: the limit replaces the
+         * overflowing chemical potential); without it the run fails there. */
+        double m0 = rho[n] > 0.0 && bpole * rho[n] >= 1.0
+                        ? INFINITY
+                        : orc_mu0(p->eos, rho[n], p->T, p->a, p->b, p->R, p->eos_alpha);
+        double m = k2 * m0 - p->kappa * (dxxr[n] + dyyr[n]);
         if (t < p->mu_cap_steps && m > k2 * p->mu_max)
             m = k2 * p->mu_max;
         mu[n] = m;

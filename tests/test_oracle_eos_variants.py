@@ -118,3 +118,39 @@ def test_c_oracle_matches_python(kind):
                                                                          abs=1e-16)
         assert S.eos_mu0(kind, r, T, e.a, e.b, e.R, al) == pytest.approx(e.mu0(r, T),
                                                                           rel=1e-13, abs=1e-16)
+
+
+@pytest.mark.parametrize("kind", E.KINDS)
+def test_mu0_grows_without_bound_below_the_pole(kind):
+    """The repulsive pole (b rho = 1, or b rho / 4 = 1 for CS): approached from
+    below, mu0 rises past any bound, so +infinity is its value there."""
+    e = mk(kind)
+    T = 0.6 * e.critical_point()[0]
+    pole = 1.0 / (e.b / 4.0 if kind == "cs" else e.b)
+    vals = [e.mu0(pole * (1 - d), T) for d in (1e-2, 1e-4, 1e-6, 1e-8)]
+    assert all(np.diff(vals) > 0) and vals[-1] > 10 * abs(vals[0])
+
+
+@pytest.mark.parametrize("kind", ["cs", "pr"])
+def test_upper_limit_replaces_mu_at_the_pole(kind):
+    """Sec. 5.6: while the limit is active, a node at or beyond the pole (where
+    the chemical potential overflows) gets mu-hat = k^2 mu_max and its
+    neighbours stay finite; without the limit mu-hat is infinite there."""
+    from oracle import OracleSim
+    e = None if kind == "cs" else mk(kind)
+    ee = mk(kind)
+    tc = ee.critical_point()[0]
+    rg, rl = ee.maxwell(0.6)
+    pole = 1.0 / (ee.b / 4.0 if kind == "cs" else ee.b)
+    kappa, k, mu_max = (0.1, 0.5, 2.0) if kind == "cs" else (0.005, 0.2, 6.0)
+    rho = np.full((12, 16), rl)
+    rho[5, 7] = 1.02 * pole
+    rho[6, 7] = pole
+    capped = OracleSim(16, 12, 0.6 * tc, kappa, 1.0, k, 6, eos=e, mu_max=mu_max,
+                       mu_cap_steps=10)
+    mu, Fx, Fy = capped.force_stage(rho, t=0)
+    assert mu[5, 7] == k * k * mu_max and mu[6, 7] == k * k * mu_max
+    assert np.isfinite(mu).all() and np.isfinite(Fx).all() and np.isfinite(Fy).all()
+    free = OracleSim(16, 12, 0.6 * tc, kappa, 1.0, k, 6, eos=e)
+    mu, _, _ = free.force_stage(rho, t=0)
+    assert mu[5, 7] == np.inf and mu[6, 7] == np.inf
