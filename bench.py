@@ -347,6 +347,23 @@ def phase_mismatch(a, b, mid):
     return int((pa != pb).sum()), links
 
 
+def spread_fit(tstar, r, D, lo=0.5, hi=3.0):
+    """(C, exponent) of r/D = C (t*)^e over lo <= t* <= hi: C by least squares
+    with e = 1/2, e from the log-log slope.  A sample below 3/4 of the median
+    of its five neighbours is dropped (the probe row met a bubble or a drop
+    instead of the rim)."""
+    import numpy as np
+    tstar, r = np.asarray(tstar, dtype=np.float64), np.asarray(r, dtype=np.float64)
+    med = np.array([np.median(r[max(0, i - 2):i + 3]) for i in range(r.size)])
+    sel = (tstar >= lo) & (tstar <= hi) & (r > 0) & (r >= 0.75 * med)
+    if sel.sum() < 3:
+        return None, None
+    sq = np.sqrt(tstar[sel])
+    C = float((r[sel] / D) @ sq / (sq @ sq))
+    e = float(np.polyfit(np.log(tstar[sel]), np.log(r[sel] / D), 1)[0])
+    return C, e
+
+
 def splash_config(precision="mixed", steps=10_000, every=100):
     """Drop splashing (Sec. 5.5): a drop of diameter 200 falling at 0.1 onto a
     film of thickness 100 on the bottom wall of a 2048 x 1024 channel (periodic
@@ -354,8 +371,8 @@ def splash_config(precision="mixed", steps=10_000, every=100):
     a static frame and once in a frame moving at 0.05 (fluid and walls), run
     side by side.  Reports throughput (CUDA events around the stepping only),
     mass drift, the spreading radius r(t) on the row four nodes above the film
-    against r/D = C sqrt(U t / D) shortly after impact (t* = U t / D from 0.3 to
-    1.3, t from the nominal contact, (height - radius) / U), and the outline
+    against r/D = C sqrt(U t / D) after impact (spread_fit, t* = U t / D from 0.5
+    to 3, t from the nominal contact, (height - radius) / U), and the outline
     mismatch between the two frames over time."""
     import numpy as np
     import torch
@@ -409,11 +426,7 @@ def splash_config(precision="mixed", steps=10_000, every=100):
         m1, vmax = sim.diag()[:2]
         sim.close()
         r = np.array(rs[name])
-        sel = (tstar >= 0.3) & (tstar <= 1.3) & (r > 0)  # shortly after impact
-        sq = np.sqrt(tstar[sel])
-        C = float((r[sel] / D) @ sq / (sq @ sq)) if sel.any() else None
-        expo = (float(np.polyfit(np.log(tstar[sel]), np.log(r[sel] / D), 1)[0])
-                if sel.sum() > 2 else None)
+        C, expo = spread_fit(tstar, r, D)
         res[name] = {"mlups": nx * ny * steps / (ms[name] / 1e3) / 1e6,
                      "ms_per_step": ms[name] / steps,
                      "mass_rel_drift": abs(m1 - m0[name]) / m0[name], "max_v_end": vmax,
@@ -427,6 +440,83 @@ def splash_config(precision="mixed", steps=10_000, every=100):
             "galilean": {"frame_speed": c["u_shift"], "by_tstar": gal},
             "timing": "CUDA events around lbm_step chunks of 100 steps; fields read "
                       "between chunks (not timed)"}
+
+
+SPLASH_PAPER = dict(nx=1000, ny=300, T_r=0.6, k=0.1, kappa=0.005, order=6, film=30,
+                    radius=50.0, gap=25.0, u_drop=-0.1, omega=0.344, mu_max=6.0,
+                    mu_cap_steps=1000, frame=0.03)
+
+
+def splash_paper_config(t_end=7.6, every=100):
+    """The paper's own drop-splashing case (Sec. 5.5, Figs. 10-12): PR water
+    (omega 0.344) at T_r 0.6, 1000 x 300 (periodic x, walls in y), D = 100,
+    U = 0.1, film 30, k = 0.1, kappa-hat 0.005, mixed path; Re = U D / nu = 40
+    (tau 1.25) and 150 (tau 0.7), the upper limit mu_max = 6 for the first 1000
+    steps (Sec. 5.6), and Re 150 again in a frame moving at 0.03.  The drop
+    starts 25 nodes above the film.  Reports the spreading constant C and
+    exponent (spread_fit, t* 0.5-3), r/D at t* = 1..7, the outline mismatch of
+    the moving frame at the paper's snapshot times, and throughput."""
+    import numpy as np
+    import torch
+    import paper_1906_09530_gb300 as P
+    from paper_1906_09530_gb300 import workloads as W
+    c = SPLASH_PAPER
+    nx, ny = c["nx"], c["ny"]
+    eos = P.make_eos("pr", omega=c["omega"])
+    rg, rl = P.lbm_maxwell(c["T_r"], eos)
+    mid = 0.5 * (rg + rl)
+    D, U = 2 * c["radius"], -c["u_drop"]
+    t_c = c["gap"] / U
+    steps = int(round((t_c + t_end * D / U) / every)) * every
+    snap_t = [int(t_c + ts * D / U) // every * every for ts in (0.5, 2.0, 4.5, 7.6)]
+    res, snaps = {}, {}
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for name, tau, us in (("re40", 1.25, 0.0), ("re150", 0.7, 0.0),
+                          ("re150_frame", 0.7, c["frame"])):
+        sim = P.Simulation(nx, ny, c["T_r"], c["kappa"], tau, c["k"], fd_order=c["order"],
+                           precision="mixed", eos=eos, mu_max=c["mu_max"],
+                           mu_cap_steps=c["mu_cap_steps"], walls_y=True, wall_ux=(us, us))
+        sim.set_fields(*W.splash(nx, ny, rg, rl, c["film"], c["radius"],
+                                 c["radius"] + c["gap"], 2.0 / c["k"], c["u_drop"], us))
+        m0 = sim.diag()[0]
+        ms, ts, rs = 0.0, [], []
+        snaps[name] = {}
+        while sim.t < steps:
+            torch.cuda.synchronize()
+            ev[0].record()
+            sim.step(every)
+            ev[1].record()
+            torch.cuda.synchronize()
+            ms += ev[0].elapsed_time(ev[1])
+            rho = sim.fields()[0]
+            xc = int(round(nx / 2 + us * sim.t)) % nx
+            ts.append(sim.t)
+            rs.append(spreading_radius(rho, c["film"] + 5, xc, mid))
+            if sim.t in snap_t:
+                snaps[name][sim.t] = np.roll(rho, -int(round(us * sim.t)), axis=1) > mid
+        m1 = sim.diag()[0]
+        sim.close()
+        tstar = U * (np.array(ts, dtype=np.float64) - t_c) / D
+        r = np.array(rs)
+        C, e = spread_fit(tstar, r, D)
+        res[name] = {"reynolds": U * D / ((tau - 0.5) / 3), "tau": tau, "spread_C": C,
+                     "spread_exponent": e, "mass_rel_drift": abs(m1 - m0) / m0,
+                     "mlups": nx * ny * steps / (ms / 1e3) / 1e6,
+                     "r_over_D": {f"{a:.1f}": round(float(b / D), 3) for a, b in zip(tstar, r)
+                                  if a > 0.9 and abs(a - round(a)) < 0.051}}
+    gal = {}
+    for t in snap_t:
+        a, b = snaps["re150"].get(t), snaps["re150_frame"].get(t)
+        if a is not None and b is not None:
+            links = int((np.diff(a.astype(np.int8), axis=1) != 0).sum() +
+                        (np.diff(a.astype(np.int8), axis=0) != 0).sum())
+            gal[f"{U * (t - t_c) / D:.2f}"] = {"mismatch_nodes": int((a != b).sum()),
+                                               "interface_links": links}
+    return {"workload": f"splash-paper-{nx}x{ny}-D{int(D)}-U{U}-film{c['film']}-PR-Tr{c['T_r']}"
+                        f"-k{c['k']}-cap{c['mu_max']}x{c['mu_cap_steps']}-mixed",
+            "density_ratio": rl / rg, "steps": steps, **res,
+            "galilean_frame_0.03_re150": gal,
+            "paper_reference": "2-D spreading constant C about 1.3 (Sec. 5.5)"}
 
 
 def surrogate_demo():
@@ -578,7 +668,8 @@ def main():
     ap.add_argument("--no-large", action="store_true",
                     help="skip the 4096^2 line (default: measured after the main one)")
     ap.add_argument("--no-splash", action="store_true",
-                    help="skip the drop-splashing line (walls, 2048 x 1024, 2 x 10 000 steps)")
+                    help="skip the drop-splashing lines (walls; 2048 x 1024 and the "
+                         "paper's 1000 x 300)")
     args = ap.parse_args()
     w = dict(WORKLOAD)
     if args.size != 1024:
@@ -720,6 +811,7 @@ def main():
         line["batch"] = batch_config(min(args.steps, 50), max(args.warmup // 10, 3))
     if rank == 0 and not args.no_splash:
         line["splash"] = splash_config(args.precision)
+        line["splash_paper"] = splash_paper_config()
     if rank == 0 and args.surrogate:
         line["surrogate"] = surrogate_demo()
     if rank == 0 and not args.no_equilibrium:

@@ -45,7 +45,8 @@ typedef enum {
     LBM_ENOMEM = 2,    /* workspace too small, or host allocation failed */
     LBM_ECUDA = 3,     /* a CUDA runtime call failed */
     LBM_EUNSTABLE = 4, /* the device flagged rho <= 0, a non-finite value or the
-                          EOS pole (b rho / 4 >= 1); see lbm_failed_step() */
+                          EOS pole (b rho >= 1; b rho / 4 >= 1 for CS) while the
+                          upper limit is off; see lbm_failed_step() */
     LBM_ETIMEOUT = 5,  /* device work did not finish within the wait limit */
     LBM_ENOTIMPL = 6   /* option recognised but not built (e.g. non-periodic) */
 } lbm_status;
@@ -102,7 +103,9 @@ typedef struct {
     int32_t prec;         /* LBM_PREC_FP64, LBM_PREC_MIXED or LBM_PREC_MIXED_DF */
     int32_t fd_order;     /* 4 (alpha = 1/4) or 6 (alpha = 1/3, Eq. 39) */
     double mu_max;        /* chemical-potential upper limit in momentum-space
-                             units (Sec. 5.6); +INFINITY switches it off */
+                             units (Sec. 5.6); +INFINITY switches it off.  While
+                             it acts, a node at or beyond the EOS pole (where mu0
+                             grows without bound) gets mu-hat = k^2 mu_max */
     int64_t mu_cap_steps; /* the limit acts while the time level t < mu_cap_steps */
     int32_t collision;    /* LBM_COLLIDE_BGK (0) or LBM_COLLIDE_MRT */
     double s_e, s_eps, s_q; /* MRT rates, each in (0, 2); unused by BGK */

@@ -21,7 +21,8 @@ struct DevState {
 
 enum : unsigned int {
     FLAG_RHO = 1u,   // collide-stream: rho <= 0 or not finite
-    FLAG_EOS = 2u,   // EOS pass: b rho / 4 >= 1 (the CS pole) or mu not finite
+    FLAG_EOS = 2u,   // EOS pass: rho <= 0, the EOS pole with the upper limit off,
+                     // or mu not finite
 };
 
 // Physical parameters the kernels need.

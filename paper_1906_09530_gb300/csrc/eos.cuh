@@ -44,4 +44,13 @@ __device__ __forceinline__ T eos_mu0(const EosC<T>& e, T r, bool& bad) {
     return rn_sub(m, rn_div(rn_mul(e.aal, r), rn_add(T(1), br)));
 }
 
+// A positive density at or beyond the repulsive pole.  mu0 grows without bound
+// as rho approaches the pole from below, so there it is +infinity: while the
+// upper limit of Sec. 5.6 is active such a node takes the limit (the limit
+// replaces the overflowing chemical potential); otherwise it is an error.
+template <class T>
+__device__ __forceinline__ bool eos_at_pole(const EosC<T>& e, T r) {
+    return r > T(0) && rn_mul(e.b, r) >= T(1);  // e.b holds b/4 for CS
+}
+
 }  // namespace cplbm

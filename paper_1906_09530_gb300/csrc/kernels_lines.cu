@@ -718,7 +718,14 @@ struct EpiMu {
         bool bad = false;
         const R mu0 = eos_mu0(e, (R)op.r, bad);
         R m = rn_fma(k2, mu0, -rn_mul(kappa, rn_add((R)op.xx, (R)d2)));
-        if (capped) m = m < cap ? m : cap;
+        if (capped) {
+            if (eos_at_pole(e, (R)op.r)) {  // mu0 = +infinity: the limit takes the node
+                m = cap;
+                bad = false;
+            } else {
+                m = m < cap ? m : cap;
+            }
+        }
         mu[o] = (O)m;
         return bad || !(m > -R(1e30) && m < R(1e30));
     }

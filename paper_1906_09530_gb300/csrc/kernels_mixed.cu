@@ -231,10 +231,18 @@ __global__ void k_macro_mixed(const float* __restrict__ f, const float* __restri
 // needs afterwards.
 __device__ __forceinline__ float mu_node(float r, float xx, float yy, const MuConstF& p,
                                          bool capped, bool& bad) {
-    const float mu0 = eos_mu0(p.e, r, bad);
+    bool b0 = false;
+    const float mu0 = eos_mu0(p.e, r, b0);
     float m = rn_fma(p.k2, mu0, -rn_mul(p.kappa, rn_add(xx, yy)));
-    if (capped) m = fminf(m, p.cap);
-    bad |= !(fabsf(m) < 1e30f);
+    if (capped) {
+        if (eos_at_pole(p.e, r)) {  // mu0 = +infinity: the limit takes the node
+            m = p.cap;
+            b0 = false;
+        } else {
+            m = fminf(m, p.cap);
+        }
+    }
+    bad |= b0 || !(fabsf(m) < 1e30f);
     return m;
 }
 

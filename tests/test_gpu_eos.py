@@ -129,3 +129,48 @@ def test_batch_coexistence(cuda, kind):
         assert abs(l / rl - 1) <= 1e-4
         assert -1e-3 <= g / rg - 1 <= 0.05
     b.close()
+
+
+def _pole_field(ee, nx=48, ny=40):
+    """A PR (or CS) drop with two nodes at and beyond the repulsive pole."""
+    rg, rl = ee.maxwell(0.6)
+    pole = 1.0 / (ee.b / 4.0 if ee.kind == "cs" else ee.b)
+    rho = W.drop(nx, ny, rg, rl, 10.0, 4.0 / 0.2)
+    rho[20, 24] = 1.02 * pole
+    rho[21, 24] = pole
+    return rho, pole
+
+
+@pytest.mark.parametrize("kind,precision", [("pr", "fp64"), ("pr", "mixed"),
+                                            ("cs", "fp64"), ("cs", "mixed")])
+def test_upper_limit_takes_the_pole(cuda, kind, precision):
+    """Sec. 5.6: while the limit acts, nodes at or beyond the pole get
+    mu-hat = k^2 mu_max and the run goes on (FP64: as the oracle, step by
+    step); with the limit off the same state is flagged unstable."""
+    from paper_1906_09530_gb300 import LbmError, Simulation, make_eos
+    ee = E.Eos(kind, omega=0.344 if kind == "pr" else 0.0)
+    tc, _ = ee.critical_point()
+    kappa, k, mu_max = (0.005, 0.2, 6.0) if kind == "pr" else (0.1, 0.5, 2.0)
+    e = make_eos(kind, omega=0.344 if kind == "pr" else 0.0)
+    rho, pole = _pole_field(ee)
+    g = Simulation(48, 40, 0.6, kappa, 1.0, k, fd_order=6, precision=precision, eos=e,
+                   mu_max=mu_max, mu_cap_steps=50)
+    g.set_fields(rho)
+    mu = g.fields()[3]
+    cap = k * k * mu_max
+    if precision == "fp64":
+        assert mu[20, 24] == cap and mu[21, 24] == cap
+    else:
+        assert mu[20, 24] == pytest.approx(cap, rel=1e-7)
+    g.step(5)
+    if precision == "fp64":
+        o = OracleSim(48, 40, 0.6 * tc, kappa, 1.0, k, 6, eos=None if kind == "cs" else ee,
+                      mu_max=mu_max, mu_cap_steps=50)
+        o.set_fields(rho)
+        o.step(5)
+        assert rel_point(g.fields()[0], o.fields()[0]) <= 1e-10
+    g.close()
+    with pytest.raises(LbmError):
+        h = Simulation(48, 40, 0.6, kappa, 1.0, k, fd_order=6, precision=precision, eos=e)
+        h.set_fields(rho)
+        h.step(1)
