@@ -609,7 +609,7 @@ __global__ void __launch_bounds__(kNL * 32)
 // nbx take the x windows, the rest the y windows.
 template <class P1, class P2, bool SIXTH, bool SECOND, class InX, class EpiX, class InY,
           class EpiY>
-__global__ void __launch_bounds__(kNL * 32, 3)
+__global__ void __launch_bounds__(kNL * 32, 4)
     k_lines_xy(InX inx, LineGeo gx, EpiX ex, InY iny, LineGeo gy, EpiY ey, LineConst<P1> k1,
                LineConst<PolF> k1f, LineConst<P2> k2, DevState* st, int bump, int nbx) {
     if (bump && blockIdx.x == 0 && threadIdx.x == 0) st->t += 1;

@@ -58,6 +58,29 @@ __device__ __forceinline__ void raise_flag(DevState* st, unsigned bits, int64_t 
 // ---------------------------------------------------------------------------
 constexpr int kSwWarps = 4;  // warps per block
 
+// Halfway bounce-back at a wall, by the ordinary pull: the populations that the
+// pull takes from the solid row (H, the row beyond the wall) are replaced by the
+// wall row's own populations moving into the wall, reversed, so each node gets
+// its own reflected population.  A wall moving along x at U adds e_x rho U / 6
+// on the diagonals (Ladd), rho the node's density.  Diagonals are placed one
+// lane over, where the pull takes them from the neighbour lane.  Warp-uniform.
+template <bool BOTTOM>
+__device__ __forceinline__ void reflect_into(float (&H)[9], const float (&B)[9], float uw6) {
+    float r = B[0];
+#pragma unroll
+    for (int i = 1; i < 9; ++i) r = __fadd_rn(r, B[i]);
+    const float c = __fmul_rn(r, uw6);
+    if (BOTTOM) {  // H is row -1: directions 2, 5, 6 come from it
+        H[2] = B[4];
+        H[5] = __shfl_down_sync(0xffffffffu, __fadd_rn(B[7], c), 1);
+        H[6] = __shfl_up_sync(0xffffffffu, __fsub_rn(B[8], c), 1);
+    } else {  // H is row ny: directions 4, 7, 8 come from it
+        H[4] = B[2];
+        H[7] = __shfl_up_sync(0xffffffffu, __fsub_rn(B[5], c), 1);
+        H[8] = __shfl_down_sync(0xffffffffu, __fadd_rn(B[6], c), 1);
+    }
+}
+
 // WALLS: the bounce-back rows are compiled only into the walled variant, so
 // the periodic kernel keeps its register count.
 template <bool MRT, bool WALLS>
@@ -102,9 +125,15 @@ __device__ __forceinline__ void cs_mixed_body(const CsArgs& a, int wid) {
     fetch(y0);
     collide_raw(B);
     fetch(y0 + 1);
+    if (WALLS && y0 == 0) reflect_into<true>(A, B, a.uw6[0]);
     for (int y = y0; y < y1; ++y) {
-        collide_raw(C);  // row y+1
-        if (y + 1 < y1) fetch(y + 2);
+        if (WALLS && y == ny - 1) {
+            // row ny is solid: the pull takes only C[4], C[7], C[8] from it
+            reflect_into<false>(C, B, a.uw6[1]);
+        } else {
+            collide_raw(C);  // row y+1
+            if (y + 1 < y1 && !(WALLS && y + 2 == ny)) fetch(y + 2);
+        }
         // gather row y: e = (ex, ey) comes from row y - ey, column x - ex
         float g[9];
         g[0] = B[0];
@@ -116,23 +145,6 @@ __device__ __forceinline__ void cs_mixed_body(const CsArgs& a, int wid) {
         g[6] = __shfl_down_sync(0xffffffffu, A[6], 1);
         g[7] = __shfl_down_sync(0xffffffffu, C[7], 1);
         g[8] = __shfl_up_sync(0xffffffffu, C[8], 1);
-        if (WALLS && (y == 0 || y == ny - 1)) {
-            // halfway bounce-back: what would come from a solid row is the
-            // node's own population that left toward it, reversed; a wall
-            // moving along x at U adds e_x rho U / 6 to the reflected
-            // diagonals (Ladd), rho the node's density
-            const float c = __fmul_rn(sum9_exact(B).hi, a.uw6[y == 0 ? 0 : 1]);
-            if (y == 0) {
-                g[2] = B[4];
-                g[5] = __fadd_rn(B[7], c);
-                g[6] = __fsub_rn(B[8], c);
-            }
-            if (y == ny - 1) {
-                g[4] = B[2];
-                g[7] = __fsub_rn(B[5], c);
-                g[8] = __fadd_rn(B[6], c);
-            }
-        }
         if (writer) {
             const size_t n = (size_t)y * nx + xo;
 #pragma unroll
@@ -150,15 +162,25 @@ __device__ __forceinline__ void cs_mixed_body(const CsArgs& a, int wid) {
     if (!ok) raise_flag(a.st, FLAG_RHO, a.st->t);
 }
 
-template <bool MRT, bool WALLS>
+template <bool MRT>
 __global__ void __launch_bounds__(kSwWarps * 32) k_cs_mixed_sw(CsArgs a) {
-    cs_mixed_body<MRT, WALLS>(a, blockIdx.x * kSwWarps + (threadIdx.x >> 5));
+    cs_mixed_body<MRT, false>(a, blockIdx.x * kSwWarps + (threadIdx.x >> 5));
+}
+
+// With walls: held to the periodic kernel's 48 registers (10 blocks of 4 warps
+// per SM); unconstrained, the wall rows cost one more 8-register granule and
+// a tenth of the occupancy.
+template <bool MRT>
+__global__ void __launch_bounds__(kSwWarps * 32, 10) k_cs_mixed_sw_walls(CsArgs a) {
+    cs_mixed_body<MRT, true>(a, blockIdx.x * kSwWarps + (threadIdx.x >> 5));
 }
 
 // Batched: block b belongs to instance map[b]; its warps continue that
-// instance's warp numbering from the instance's first block.
+// instance's warp numbering from the instance's first block.  Held to 48
+// registers like the lone kernel (reading the instance's arguments took it to
+// 64, eight blocks per SM instead of ten).
 template <bool MRT>
-__global__ void __launch_bounds__(kSwWarps * 32)
+__global__ void __launch_bounds__(kSwWarps * 32, 10)
     k_cs_mixed_batch(const CsBatchInst* __restrict__ d, const int* __restrict__ map, int from) {
     const CsBatchInst& D = d[map[blockIdx.x]];
     CsArgs a = D.a;
@@ -364,13 +386,13 @@ int cs_mixed_blocks(const CsArgs& a) {
 cudaError_t launch_cs_mixed_args(const CsArgs& a, cudaStream_t s) {
     const int nb = cs_mixed_blocks(a);
     if (a.mrt && a.walls)
-        k_cs_mixed_sw<true, true><<<nb, kSwWarps * 32, 0, s>>>(a);
+        k_cs_mixed_sw_walls<true><<<nb, kSwWarps * 32, 0, s>>>(a);
     else if (a.mrt)
-        k_cs_mixed_sw<true, false><<<nb, kSwWarps * 32, 0, s>>>(a);
+        k_cs_mixed_sw<true><<<nb, kSwWarps * 32, 0, s>>>(a);
     else if (a.walls)
-        k_cs_mixed_sw<false, true><<<nb, kSwWarps * 32, 0, s>>>(a);
+        k_cs_mixed_sw_walls<false><<<nb, kSwWarps * 32, 0, s>>>(a);
     else
-        k_cs_mixed_sw<false, false><<<nb, kSwWarps * 32, 0, s>>>(a);
+        k_cs_mixed_sw<false><<<nb, kSwWarps * 32, 0, s>>>(a);
     return cudaGetLastError();
 }
 
