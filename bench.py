@@ -46,23 +46,27 @@ if ROOT not in sys.path:
 WORKLOAD = dict(nx=1024, ny=1024, T_r=0.5, k=0.5, kappa=0.1, tau=1.0, order=6, radius=200.0,
                 width=8.0)
 METRIC = "MLUPS (million lattice-node updates per second) of the full time step"
-# algorithmic bytes per node of each pass: [collide-stream, x rho, y rho + mu, x mu + F_x,
-# y mu + F_y]; populations 4 B (mixed) or 8 B (fp64), fields 8 B
-PASS_NAMES = {"fp64": ["collide_stream", "cfd_x_rho", "cfd_y_rho_mu", "cfd_x_force",
-                        "cfd_y_force"],
-              "mixed": ["collide_stream", "cfd_rho_xy", "mu_pointwise", "cfd_mu_force_xy"]}
+DF_RATIO = 1e4  # the mixed path's density lines are double-float from this Maxwell ratio
 
 
-def pass_bytes(precision):
-    """Algorithmic bytes per node of each pass: every field read or written once
-    per pass that needs it, in the precision the path stores it."""
-    if precision == "mixed":
-        # collide-stream: f 36 in + 36 out (FP32), F 8, rho hi/lo 8
-        # x|y lines of rho: rho hi/lo 8 read by each direction -> d_x, d_xx, d_y, d_yy 16
-        # mu-hat: rho_hi, d_xx, d_yy 12 -> mu 4
-        # x|y lines of mu-hat: mu 4 by each direction, rho_hi 4, d_x rho, d_y rho 8 -> F 8
-        return [88, 32, 16, 28]
-    return [168, 24, 32, 32, 32]  # all FP64
+def pass_layout(precision, flags=0):
+    """(names, algorithmic bytes per node) of the passes of one step (flags:
+    lbm_path_flags).  Every field is read or written once per pass that needs
+    it, in the precision the path stores it; x- and y-lines launched together
+    are one pass.
+      mixed, collide-stream: f 36 in + 36 out (FP32), F 8 in, rho hi/lo 8 out = 88
+      x|y lines of rho: rho as hi/lo (8, double-float lines) or hi only (4) ->
+        d_x, d_xx, d_y, d_yy 16
+      mu-hat: rho_hi, d_xx, d_yy 12 -> mu 4 = 16
+      x|y lines of mu-hat + force: mu 4, rho_hi 4, d_x, d_y 8 -> F 8 = 24
+      fp64: collide 72 + 72 + F 16 + rho 8; x rho 8 -> 16; y rho, d_xx 16 -> 16;
+      each force direction mu, rho, d rho 24 -> F 8."""
+    if precision != "mixed":
+        return (["collide_stream", "cfd_x_rho", "cfd_y_rho_mu", "cfd_x_force", "cfd_y_force"],
+                [168, 24, 32, 32, 32])
+    r = 8 if flags & 2 else 4
+    return (["collide_stream", "cfd_rho_xy", "mu_pointwise", "cfd_mu_force_xy"],
+            [88, r + 16, 16, 24])
 
 
 def measured_traffic(precision):
@@ -226,12 +230,11 @@ def large_grid(precision, steps, warmup, size=4096, collision="bgk", **over):
                        fd_order=w["order"], precision=precision, collision=collision)
     sim.set_fields(W.drop(w["nx"], w["ny"], rg, rl, w["radius"], w["width"]))
     sim.step(warmup)
-    names = PASS_NAMES[precision]
+    names, pb = pass_layout(precision, sim.path_flags)
     ms = np.array([sim.step_timed() for _ in range(steps)])[:, :len(names)]
     sim.close()
     N = w["nx"] * w["ny"]
     step_ms = float(ms.sum(axis=1).mean())
-    pb = pass_bytes(precision)
     peak, peak_kind = load_peaks()
     gbs = sum(pb) * N / (step_ms / 1e3) / 1e9
     return {"workload": workload_name(w, precision) + ("-mrt" if collision == "mrt" else ""),
@@ -294,7 +297,12 @@ def batch_config(steps, warmup, n=256):
     for s in sims:
         s.check()
         s.close()
-    pb = sum(pass_bytes("mixed"))
+    # batches run the merged passes; double-float density lines from DF_RATIO
+    alg = 0
+    for d in specs:
+        rg, rl = P.lbm_maxwell(d["T_r"])
+        alg += d["nx"] * d["ny"] * sum(pass_layout("mixed", 2 if rl >= DF_RATIO * rg else 0)[1])
+    pb = alg / N
     peak, peak_kind = load_peaks()
     return {"workload": f"batch-{n}-instances-sides64-512-Tr0.3-0.9-mixed", "instances": n,
             "nodes": N, "steps": steps,
@@ -302,7 +310,7 @@ def batch_config(steps, warmup, n=256):
             "graph_mlups": N / (graph_ms / 1e3) / 1e6,
             "lone_sequential_mlups": N / (lone_ms / 1e3) / 1e6,
             "passes_ms": {nm: round(float(ms[:, i].mean()), 5)
-                          for i, nm in enumerate(PASS_NAMES["mixed"])},
+                          for i, nm in enumerate(pass_layout("mixed")[0])},
             "step_roofline": {"alg_bytes_per_node": pb,
                               "frac": pb * N / (step_ms / 1e3) / 1e9 / peak,
                               "peak": peak, "peak_kind": f"{peak_kind} copy bandwidth"},
@@ -715,7 +723,7 @@ def main():
 
     clocks = ClockSampler(bus_id(local))
     barrier()
-    names = PASS_NAMES[args.precision]
+    names, pb = pass_layout(args.precision, sim.path_flags)
     pass_ms = np.zeros((args.steps, 5))
     for i in range(args.steps):
         flush.zero_()
@@ -766,7 +774,6 @@ def main():
                        "mu to host), wall clock; bytes per step = run totals / K"}
 
     mean_pass = pass_ms.mean(axis=0)
-    pb = pass_bytes(args.precision)
     peak, peak_kind = load_peaks()
     dom = int(np.argmax(mean_pass))
     passes = {}

@@ -166,6 +166,13 @@ lbm_status lbm_check(lbm_ctx *ctx);
  *       [3] x- and y-lines of mu-hat + F; [4] is 0. */
 lbm_status lbm_step_timed(lbm_ctx *ctx, float *pass_ms);
 
+/* How a mixed context runs its passes (chosen at lbm_init), as a bit set:
+ * LBM_PATH_RHO_DF: the density lines are double-float (density ratio at or
+ *   above 1e4, or LBM_PREC_MIXED_DF), else FP32 on the hi part.
+ * 0 for FP64, -1 for NULL. */
+enum { LBM_PATH_RHO_DF = 2 };
+int32_t lbm_path_flags(const lbm_ctx *ctx);
+
 /* Outputs of the current state to host FP64 [ny][nx] arrays, any may be NULL:
  * rho (Eq. 3), the velocity v = u + F/(2 rho) (Sec. 2, after Eq. 5) and the
  * mesh-space chemical potential mu-hat (Eq. 33).  Returns when copied. */

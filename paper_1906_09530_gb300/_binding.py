@@ -98,6 +98,7 @@ def lib():
             "lbm_cfd": (C.c_int, [_vp, _vp, _vp, _i32, _i32, _i32, _i32, _vp]),
             "lbm_cfd_df": (C.c_int, [_vp, _vp, _vp, _vp, _i32, _i32, _i32, _i32, _vp]),
             "lbm_time": (C.c_int64, [_vp]),
+            "lbm_path_flags": (C.c_int32, [_vp]),
             "lbm_failed_step": (C.c_int64, [_vp]),
             "lbm_set_timeout": (C.c_int, [_vp, C.c_double]),
             "lbm_set_wall_velocity": (C.c_int, [_vp, C.c_double, C.c_double]),
@@ -298,6 +299,11 @@ class Simulation:
     @property
     def t(self):
         return lib().lbm_time(self.ctx)
+
+    @property
+    def path_flags(self):
+        """Bit set: LBM_PATH_RHO_DF (2) for double-float density lines; 0 for FP64."""
+        return lib().lbm_path_flags(self.ctx)
 
     @property
     def failed_step(self):

@@ -415,6 +415,12 @@ lbm_status lbm_set_wall_velocity(lbm_ctx* c, double u_bottom, double u_top) {
     return LBM_OK;
 }
 
+int32_t lbm_path_flags(const lbm_ctx* c) {
+    if (!c) return -1;
+    if (c->prec == LBM_PREC_FP64) return 0;
+    return c->rho_df ? LBM_PATH_RHO_DF : 0;
+}
+
 int64_t lbm_time(const lbm_ctx* c) { return c ? c->t : -1; }
 int64_t lbm_failed_step(const lbm_ctx* c) { return c ? c->failed : -1; }
 

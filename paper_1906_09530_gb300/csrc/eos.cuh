@@ -7,6 +7,7 @@
 // b rho >= 1 for the cubic EOSs).
 #pragma once
 
+#include "cplbm_internal.cuh"
 #include "lattice.cuh"
 
 namespace cplbm {
@@ -51,6 +52,28 @@ __device__ __forceinline__ T eos_mu0(const EosC<T>& e, T r, bool& bad) {
 template <class T>
 __device__ __forceinline__ bool eos_at_pole(const EosC<T>& e, T r) {
     return r > T(0) && rn_mul(e.b, r) >= T(1);  // e.b holds b/4 for CS
+}
+
+// mu-hat of the mixed path at one node: k^2 mu0(rho) - kappa (d_xx + d_yy) rho
+// (Eq. 33 with the mu0 of Eqs. 15, 17, 19 or 21) in FP32, limited from above
+// while the time level t < cap_steps (Sec. 5.6; `capped` comes from the time
+// level read on the device, so that graph replays stay correct).  Shared by
+// the lone and the batched pointwise kernels.
+__device__ __forceinline__ float mu_node(float r, float xx, float yy, const MuConstF& p,
+                                         bool capped, bool& bad) {
+    bool b0 = false;
+    const float mu0 = eos_mu0(p.e, r, b0);
+    float m = rn_fma(p.k2, mu0, -rn_mul(p.kappa, rn_add(xx, yy)));
+    if (capped) {
+        if (eos_at_pole(p.e, r)) {  // mu0 = +infinity: the limit takes the node
+            m = p.cap;
+            b0 = false;
+        } else {
+            m = fminf(m, p.cap);
+        }
+    }
+    bad |= b0 || !(fabsf(m) < 1e30f);
+    return m;
 }
 
 }  // namespace cplbm

@@ -245,29 +245,8 @@ __global__ void k_macro_mixed(const float* __restrict__ f, const float* __restri
     }
 }
 
-// Chemical potential of the mixed path, pointwise after the line solves of rho:
-// mu-hat = k^2 mu0(rho) - kappa (d_xx + d_yy) rho (Eq. 33 with the mu0 of
-// Eqs. 15, 17, 19 or 21) in FP32, limited
-// from above while the time level t < cap_steps (Sec. 5.6; t read on the device
-// so that graph replays stay correct).  Written over d_xx rho, which nothing
-// needs afterwards.
-__device__ __forceinline__ float mu_node(float r, float xx, float yy, const MuConstF& p,
-                                         bool capped, bool& bad) {
-    bool b0 = false;
-    const float mu0 = eos_mu0(p.e, r, b0);
-    float m = rn_fma(p.k2, mu0, -rn_mul(p.kappa, rn_add(xx, yy)));
-    if (capped) {
-        if (eos_at_pole(p.e, r)) {  // mu0 = +infinity: the limit takes the node
-            m = p.cap;
-            b0 = false;
-        } else {
-            m = fminf(m, p.cap);
-        }
-    }
-    bad |= b0 || !(fabsf(m) < 1e30f);
-    return m;
-}
-
+// Chemical potential of the mixed path, pointwise after the line solves of rho
+// (mu_node, eos.cuh), written over d_xx rho, which nothing needs afterwards.
 // Chunks of four nodes (16-byte loads and stores: the planes are 256-byte
 // aligned), chunk c0, c0 + stride, ...; a short last chunk node by node.
 __device__ __forceinline__ void mu_mixed_body(const float* __restrict__ rh, float* dxx_mu,

@@ -131,6 +131,7 @@ def test_strerror_and_null_ctx():
     assert lib.lbm_time(None) == -1
     lib.lbm_free(None)
     assert lib.lbm_set_wall_velocity(None, 0.0, 0.0) == B.LBM_EINVAL
+    assert lib.lbm_path_flags(None) == -1
 
 
 def test_oracle_and_library_share_nothing():
