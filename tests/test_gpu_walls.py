@@ -154,3 +154,24 @@ def test_mass_conserved_with_walls(cuda):
     m0 = g.diag()[0]
     g.step(500)
     assert abs(g.diag()[0] - m0) / m0 <= 1e-12
+
+
+@pytest.mark.parametrize("nx,ny,order,precision", [(37, 29, 6, "fp64"), (37, 29, 4, "mixed"),
+                                                   (64, 19, 6, "mixed_df")])
+def test_ragged_grids_with_walls(cuda, nx, ny, order, precision):
+    """Sizes that are not multiples of 4 or of a strip (the scalar staging and
+    epilogue paths) and a short y-line (period 2 ny below a window), against the
+    oracle, with moving walls."""
+    from paper_1906_09530_gb300 import Simulation
+    rg, rl = thermo.maxwell(TR)
+    rho = W.with_noise(W.drop(nx, ny, rg, rl, 6.0, 4.0, center=(nx / 2, 8.0)), 9, 1e-5)
+    ux, uy = np.full_like(rho, 0.02), np.full_like(rho, -0.01)
+    g = Simulation(nx, ny, TR, 0.1, 1.0, K, fd_order=order, precision=precision, walls_y=True,
+                   wall_ux=(0.02, 0.02))
+    g.set_fields(rho, ux, uy)
+    o = OracleSim(nx, ny, TR * TC, 0.1, 1.0, K, order, walls_y=True, wall_ux=(0.02, 0.02))
+    o.set_fields(rho, ux, uy)
+    g.step(150)
+    o.step(150)
+    tol = 1e-10 if precision == "fp64" else 1e-4
+    assert rel_point(g.fields()[0], o.fields()[0]) <= tol
