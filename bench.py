@@ -618,6 +618,23 @@ def load_bf16_peak():
     return 1900.0, "fallback"
 
 
+def max_over_ranks(seconds, dist, device):
+    """The largest of every rank's elapsed time (seconds), on every rank; the
+    job's time is its slowest replica's.  dist: torch.distributed or None."""
+    if dist is None:
+        return float(seconds)
+    import torch
+    t = torch.tensor([float(seconds)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(units_per_rank, world, seconds):
+    """Whole-job throughput: the node updates of all ranks over the slowest
+    rank's time, in millions per second."""
+    return world * units_per_rank / seconds / 1e6
+
+
 def run_reference(args, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -733,12 +750,8 @@ def main():
     barrier()
     clk = clocks.stop()
     step_ms = pass_ms.sum(axis=1)
-    total_s = step_ms.sum() / 1e3
-    if dist is not None:
-        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = world * N * args.steps / total_s / 1e6
+    total_s = max_over_ranks(step_ms.sum() / 1e3, dist, "cuda")
+    value = whole_job_mlups(N * args.steps, world, total_s)
 
     # back-to-back CUDA-graph steps without flushing (context only)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -762,12 +775,8 @@ def main():
         _check(lib().lbm_set_fields(sim.ctx, _hptr(h_rho), None, None), "lbm_set_fields")
         _check(lib().lbm_step(sim.ctx, args.steps), "lbm_step")
         _check(lib().lbm_fields(sim.ctx, *[_hptr(a) for a in outs]), "lbm_fields")
-        dt = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": world * N * args.steps / dt / 1e6, "unit": "MLUPS",
+        dt = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+        e2e = {"value": whole_job_mlups(N * args.steps, world, dt), "unit": "MLUPS",
                "h2d_bytes_per_step": N * 8 / args.steps,
                "d2h_bytes_per_step": 4 * N * 8 / args.steps,
                "what": "lbm_set_fields(host rho) + lbm_step(K) + lbm_fields(rho, vx, vy, "
