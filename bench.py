@@ -532,8 +532,9 @@ def surrogate_demo():
     (T_r 0.33-0.5, kappa-hat 0.1, k 0.2) by the library's MLP kernels, then
     steps and wall time to equilibrium (both bulks within the tolerance of a
     1.5M-step run) from the tanh start and from the warm start, on a tall slab
-    (8 x 1536) where the gas offset relaxes by slow diffusion.  Also the
-    training step's tensor throughput (BF16 products, FP32 accumulation)."""
+    (8 x 1536) where the gas offset relaxes by slow diffusion; and at T_r 0.35
+    the 4096^2 drop of radius 1000 from both starts (warm_drop_case).  Also
+    the training step's tensor throughput (BF16 products, FP32 accumulation)."""
     import numpy as np
     import torch
     from paper_1906_09530_gb300 import Simulation, lbm_maxwell, surrogate as SG
@@ -601,6 +602,8 @@ def surrogate_demo():
                 row[f"{name}_wall_s_to_{tol:g}"] = time.perf_counter() - c0
                 sim.close()
         cases.append(row)
+        if t_r == 0.35:
+            cases.append(warm_drop_case(s, eq, t_r))
     s.close()
     return {"workload": "slab-8x1536-k0.2-kappa0.1, surrogate trained on 256 slabs T_r 0.33-0.5",
             "training_data_s": data_s, "fit_s": fit_s, "fit_loss": loss,
@@ -609,6 +612,55 @@ def surrogate_demo():
                          "frac": tflops / peak,
                          "note": "256-wide products: latency-bound, microseconds per step"},
             "cases": cases}
+
+
+def warm_drop_case(s, eq, t_r, n=4096, radius=1000.0, every=5000, max_steps=100_000):
+    """A 4096^2 drop of radius 1000 at T_r (k 0.2, kappa-hat 0.1, mixed), from the
+    tanh start between the Maxwell densities and from the surrogate's warm start
+    (its interface window mapped radially): steps until the bulk gas (the
+    outermost 256 nodes of every side) and the bulk liquid (r < radius / 2) are
+    both within 1e-3 of the long slab run's equilibrium eq, checked every
+    `every` steps up to max_steps, and the deviations where the count stops.
+    A drop of this size differs from the flat equilibrium by its Laplace
+    pressure, far below 1e-3 in density."""
+    import numpy as np
+    import torch
+    from paper_1906_09530_gb300 import LbmError, Simulation, lbm_maxwell, surrogate as SG
+    from paper_1906_09530_gb300 import workloads as W
+    rg, rl = lbm_maxwell(t_r)
+    g, l, w = s.predict([t_r], [0.1], [0.2])
+    yy, xx = torch.meshgrid(torch.arange(n, device="cuda", dtype=torch.float64),
+                            torch.arange(n, device="cuda", dtype=torch.float64), indexing="ij")
+    r = torch.hypot(xx - n / 2, yy - n / 2)
+    liq = r < radius / 2
+    b = 256
+    gas = torch.zeros_like(liq)
+    gas[:b, :] = gas[-b:, :] = gas[:, :b] = gas[:, -b:] = True
+
+    def probe(sim):
+        rho = sim.fields_device()[0]
+        return float(rho[gas].mean()), float(rho[liq].mean())
+    row = {"case": f"drop-{n}x{n}-R{int(radius)}-Tr{t_r}-k0.2-mixed", "checked_every": every,
+           "max_steps": max_steps}
+    for name, field in (("tanh", W.drop(n, n, rg, rl, radius, 20.0)),
+                        ("warm", SG.drop_field(n, n, radius, g[0], l[0], w[0]))):
+        sim = Simulation(n, n, t_r, 0.1, 1.0, 0.2, fd_order=6, precision="mixed")
+        sim.set_fields(field)
+        del field
+        c0 = time.perf_counter()
+        try:
+            steps = SG.steps_to_equilibrium(sim, probe, eq, 1e-3, every=every,
+                                            max_steps=max_steps)
+        except LbmError as e:
+            row[name] = {"error": str(e), "failed_step": sim.failed_step}
+            sim.close()
+            continue
+        wall = time.perf_counter() - c0
+        gv, lv = probe(sim)
+        row[name] = {"steps_to_1e-3": steps, "wall_s": wall, "at_step": sim.t,
+                     "gas_rel_dev": gv / eq[0] - 1, "liq_rel_dev": lv / eq[1] - 1}
+        sim.close()
+    return row
 
 
 def load_bf16_peak():

@@ -13,7 +13,7 @@ import math
 import numpy as np
 import pytest
 
-from oracle import thermo
+from oracle import OracleSim, thermo
 from paper_1906_09530_gb300 import workloads as W
 from tests import cases
 
@@ -224,4 +224,31 @@ def test_batch_mrt_bitexact_vs_lone(cuda):
         for x, y in zip(b.fields(i), s.fields()):
             assert np.array_equal(x, y)
         s.close()
+    b.close()
+
+
+def test_benchmark_batch_sampled_members_against_oracle(cuda):
+    """The batch the benchmark times (256 instances, sides 64-512, T_r 0.3-0.9,
+    drops and slabs, autotuned strip heights): after 3 steps, the smallest, the
+    largest, the coldest (ratio above 1e10, double-float density lines) and a
+    middle instance against the FP64 oracle, node by node."""
+    from paper_1906_09530_gb300 import Batch
+    specs = W.batch_instances(256)
+    keys = ("nx", "ny", "T_r", "k", "kappa", "tau")
+    b = Batch([{k: d[k] for k in keys} for d in specs])
+    fields = [W.batch_field(d, *thermo.maxwell(d["T_r"])) for d in specs]
+    for i, r in enumerate(fields):
+        b.set_fields(i, r)
+    b.autotune(3)
+    b.step(3)
+    sides = [d["nx"] for d in specs]
+    picks = {sides.index(min(sides)), sides.index(max(sides)), 0, 128}
+    tc = thermo.critical_point()[0]
+    for i in sorted(picks):
+        d = specs[i]
+        o = OracleSim(d["nx"], d["ny"], d["T_r"] * tc, d["kappa"], d["tau"], d["k"], 6)
+        o.set_fields(fields[i])
+        o.step(3)
+        got, want = b.fields(i)[0], o.fields()[0]
+        assert np.max(np.abs(got - want) / want) <= 1e-5, (i, d["T_r"], d["nx"])
     b.close()

@@ -411,3 +411,25 @@ def test_mrt_equal_rates_is_bgk_on_gpu(cuda):
     a.step(100)
     b.step(100)
     assert rel_point(b.fields()[0], a.fields()[0]) <= 1e-12
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-4)])
+def test_diagonal_slab_against_oracle(cuda, precision, tol):
+    """A slab at 45 degrees to the grid (density a function of (x + y) mod n,
+    periodic in both directions): both line directions cross the same
+    interface.  200 steps against the oracle."""
+    from oracle import OracleSim, thermo
+    from paper_1906_09530_gb300 import Simulation
+    n, tr, k = 64, 0.6, 0.5
+    tc, _ = thermo.critical_point()
+    rg, rl = thermo.maxwell(tr)
+    y, x = np.mgrid[0:n, 0:n].astype(np.float64)
+    s = (x + y) % n
+    rho = rg + (rl - rg) * 0.5 * (1 - np.tanh(2 * ((np.abs(s - n / 2) - n / 4) / np.sqrt(2)) / 8.0))
+    g = Simulation(n, n, tr, 0.1, 1.0, k, fd_order=6, precision=precision)
+    g.set_fields(rho)
+    g.step(200)
+    o = OracleSim(n, n, tr * tc, 0.1, 1.0, k, 6)
+    o.set_fields(rho)
+    o.step(200)
+    assert rel_point(g.fields()[0], o.fields()[0]) <= tol

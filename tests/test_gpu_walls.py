@@ -175,3 +175,24 @@ def test_ragged_grids_with_walls(cuda, nx, ny, order, precision):
     o.step(150)
     tol = 1e-10 if precision == "fp64" else 1e-4
     assert rel_point(g.fields()[0], o.fields()[0]) <= tol
+
+
+@pytest.mark.parametrize("precision,shift,tol", [("fp64", 0.0, 1e-12), ("mixed", 0.0, 2e-6),
+                                                 ("mixed", 0.05, 2e-6)])
+def test_splash_full_size_against_oracle(cuda, precision, shift, tol):
+    """The drop-splash workload the benchmark times (2048 x 1024, film 100, drop
+    radius 100 centred 200 above it, u_y = -0.1, CS T_r 0.55, k 0.5, tau 1, 6th
+    order), in the static and the moving frame: every node after 4 steps."""
+    from paper_1906_09530_gb300 import Simulation
+    nx, ny = 2048, 1024
+    rg, rl = thermo.maxwell(0.55)
+    fields = W.splash(nx, ny, rg, rl, 100, 100.0, 200.0, 8.0, -0.1, shift)
+    g = Simulation(nx, ny, 0.55, 0.1, 1.0, 0.5, fd_order=6, precision=precision, walls_y=True,
+                   wall_ux=(shift, shift))
+    g.set_fields(*fields)
+    g.step(4)
+    o = OracleSim(nx, ny, 0.55 * TC, 0.1, 1.0, 0.5, 6, walls_y=True, wall_ux=(shift, shift))
+    o.set_fields(*fields)
+    o.step(4)
+    assert rel_point(g.fields()[0], o.fields()[0]) <= tol
+    g.close()
