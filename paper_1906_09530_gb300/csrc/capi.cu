@@ -58,7 +58,8 @@ struct lbm_ctx {
     int64_t t;
     int64_t failed;
     bool ready;      // fields set
-    cudaGraphExec_t graph[2];  // two steps, starting from f[0] / f[1]
+    cudaGraphExec_t graph[2];    // two steps, starting from f[0] / f[1]
+    cudaGraphExec_t graph16[2];  // kLongGraph steps, likewise (fewer graph launches)
     double timeout_s;
 };
 
@@ -173,27 +174,33 @@ lbm_status enqueue_step(lbm_ctx* c, cudaStream_t s, int from) {
     return enqueue_force(c, s, 1);
 }
 
+// Steps in the long graph: even, so a replay ends on the buffer it started from.
+constexpr int kLongGraph = 16;
+
 void drop_graphs(lbm_ctx* c) {
     for (int i = 0; i < 2; ++i)
-        if (c->graph[i]) {
-            cudaGraphExecDestroy(c->graph[i]);
-            c->graph[i] = nullptr;
-        }
+        for (cudaGraphExec_t* gp : {&c->graph[i], &c->graph16[i]})
+            if (*gp) {
+                cudaGraphExecDestroy(*gp);
+                *gp = nullptr;
+            }
 }
 
-lbm_status build_graph(lbm_ctx* c, int from) {
-    if (c->graph[from]) return LBM_OK;
+// Capture `steps` (even) time steps starting from f[from] into *out.
+lbm_status build_graph(lbm_ctx* c, int from, int steps, cudaGraphExec_t* out) {
+    if (*out) return LBM_OK;
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-    lbm_status st = enqueue_step(c, c->cap_stream, from);
-    if (st == LBM_OK) st = enqueue_step(c, c->cap_stream, 1 - from);
+    lbm_status st = LBM_OK;
+    for (int i = 0; i < steps && st == LBM_OK; ++i)
+        st = enqueue_step(c, c->cap_stream, (from + i) & 1);
     cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
     if (st != LBM_OK) {
         if (g) cudaGraphDestroy(g);
         return st;
     }
     if (e != cudaSuccess) return LBM_ECUDA;
-    e = cudaGraphInstantiate(&c->graph[from], g, 0);
+    e = cudaGraphInstantiate(out, g, 0);
     cudaGraphDestroy(g);
     return e == cudaSuccess ? LBM_OK : LBM_ECUDA;
 }
@@ -474,8 +481,14 @@ lbm_status lbm_step_async(lbm_ctx* c, int64_t n) {
     lbm_status st = use_dev(c);
     if (st) return st;
     int64_t left = n;
+    if (left >= kLongGraph) {
+        st = build_graph(c, c->cur, kLongGraph, &c->graph16[c->cur]);
+        if (st) return st;
+        for (; left >= kLongGraph; left -= kLongGraph)
+            CK(cudaGraphLaunch(c->graph16[c->cur], c->stream));
+    }
     if (left >= 2) {
-        st = build_graph(c, c->cur);
+        st = build_graph(c, c->cur, 2, &c->graph[c->cur]);
         if (st) return st;
         for (; left >= 2; left -= 2) CK(cudaGraphLaunch(c->graph[c->cur], c->stream));
     }
