@@ -10,9 +10,10 @@ rest).  Synthetic, seeded inputs.
 
 Also reported: `equilibrium`, the wall time from lbm_set_fields to
 Maxwell-accurate equilibrium of a flat interface (see equilibrium_time);
-`large_grid`, the same drop at 4096 x 4096 (working set far above L2); and
-`batch`, 256 independent instances of uneven sizes and temperatures advanced
-by one launch per pass (see batch_config).
+`large_grid`, the same drop at 4096 x 4096 (working set far above L2), with
+MRT, at 8192 x 8192, and in FP64; `batch`, 256 independent instances of uneven
+sizes and temperatures advanced by one launch per pass (see batch_config); and
+the two drop-splashing cases with walls (splash_config, splash_paper_config).
 
 One "step" is one time step: the device passes of the chosen precision (mixed:
 collide-stream, x|y compact FD of rho, pointwise chemical potential, x|y
@@ -875,6 +876,12 @@ def main():
         line["large_grid_mrt"] = large_grid(args.precision, min(args.steps, 100),
                                             max(args.warmup, 3), collision="mrt", T_r=0.7,
                                             k=0.3, width=4.0 / 0.3)
+        # the same drop at 8192^2 (about 7 GB of workspace), and the FP64 path at 4096^2
+        line["large_grid_8192"] = large_grid(args.precision, min(args.steps, 50),
+                                             max(args.warmup, 3), size=8192)
+        if args.precision != "fp64":
+            line["large_grid_fp64"] = large_grid("fp64", min(args.steps, 20),
+                                                 max(args.warmup, 3), size=4096)
     if not args.no_batch and args.precision == "mixed":
         line["batch"] = batch_config(min(args.steps, 50), max(args.warmup // 10, 3))
     if rank == 0 and not args.no_splash:

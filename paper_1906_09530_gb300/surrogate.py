@@ -4,9 +4,10 @@ The network (lbm_mlp_* of the C ABI, trained by this library's own kernels)
 maps (T_r, kappa-hat, k) to the equilibrium state of one flat interface as the
 method itself settles it, including its offsets from Maxwell.  That state,
 mapped onto a slab or a drop, starts a run close to its equilibrium, so most of
-the slow relaxation of the bulk densities (Sec. 5.7: the initialisation causes
+the slow relaxation of the bulk densities (Sec. 5.6: the initialisation causes
 the long transients at low T) is skipped.  Where the prediction is poor the
-plain run still converges: the method is the fallback and the judge.
+plain run still converges: the method itself is the fallback, and its own
+equilibrium is what the prediction is checked against.
 
   * training data: flat interfaces (periodic slabs) run to equilibrium as one
     batch; each gives its bulk gas and liquid densities and the 236 nodes
