@@ -17,8 +17,8 @@
 // run along).  Warp w owns line w; lane l owns positions [l C, l C + C).  Each
 // lane runs both recursions over its chunk from a zero state, then the chunk
 // boundary states are joined by a two-level shuffle scan: the state entering
-// chunk l is T_{l-1} with T_l = E_l + m T_{l-1}, m = (-lam)^C (|m| = 3.7e-6 for
-// C = 13), and each position adds (-lam)^{j+1} times that carry.  The window
+// chunk l is T_{l-1} with T_l = E_l + m T_{l-1}, m = (-lam)^C (|m| = 1.1e-8 for
+// C = 19), and each position adds (-lam)^{j+1} times that carry.  The window
 // starts H positions before the first owned position and ends H after the last,
 // H chosen so that lam^H (or (H+1) lam^H for the double recursion) is below the
 // arithmetic's rounding.  The second derivative D(D u) ("applying CFM twice",
@@ -122,16 +122,17 @@ __device__ __forceinline__ typename P2::V to2(float v) { return (typename P2::V)
 template <class P2>
 __device__ __forceinline__ typename P2::V to2(df v) { return (typename P2::V)v.hi; }
 
-constexpr int kC = 13;         // positions per lane
+constexpr int kC = 19;         // positions per lane (odd: chunk starts hit distinct banks)
 constexpr int kW = 32 * kC;    // window length
 constexpr int kNL = 8;         // lines (warps) per block
-// Shared-memory strides of one line in the staged input (window + margin 4 on
-// each side) and in the outputs.  Both are 4 mod 32: lanes reading chunk starts
-// (stride 13) and the y-line staging/epilogue (8 lines x 4 positions per warp)
-// then touch 32 distinct banks.
-constexpr int kLW = 452;
-constexpr int kSO = 420;
-static_assert(kLW >= kW + 8 && kLW % 32 == 4 && kSO >= kW && kSO % 32 == 4, "strides");
+// Shared-memory stride of one line, in the staged input (window + margin 4 on
+// each side) and in the outputs, which take over the staged rows once the
+// solve has read them (each warp reads and writes only its own line's rows).
+// It is 4 mod 32: lanes reading chunk starts (odd stride) and the y-line
+// staging/epilogue (8 lines x 4 positions per warp) then touch 32 distinct banks.
+constexpr int kLW = 644;
+constexpr int kSO = kLW;
+static_assert(kLW >= kW + 8 && kLW % 32 == 4, "strides");
 
 template <class P>
 struct LineConst {
@@ -402,9 +403,13 @@ __device__ __forceinline__ void lines_body(In& in, const LineGeo& g, const LineC
     using S1 = typename P1::S;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int kPS = kNL * kLW;                                   // plane stride
+    // the outputs reuse the staged planes: the first derivative plane 0, the
+    // second plane 1 (double-float input) or a plane of its own
     S1* tin = reinterpret_cast<S1*>(smem_raw);                      // [planes][kNL][kLW]
-    O1* tout1 = reinterpret_cast<O1*>(tin + P1::kPlanes * kPS);     // [kNL][kSO]
-    V2* tout2 = reinterpret_cast<V2*>(tout1 + kNL * kSO);           // [kNL][kSO]
+    static_assert(sizeof(O1) == sizeof(S1), "first derivative over the staged plane 0");
+    O1* tout1 = reinterpret_cast<O1*>(tin);                         // [kNL][kSO]
+    V2* tout2 = P1::kPlanes >= 2 ? reinterpret_cast<V2*>(tin + kPS)
+                                 : reinterpret_cast<V2*>(tin + P1::kPlanes * kPS);
 
     const int grp = bid % g.ngroups;
     const int win = bid / g.ngroups;
@@ -502,7 +507,7 @@ __device__ __forceinline__ void lines_body(In& in, const LineGeo& g, const LineC
     // ---- epilogue over the owned positions, coalesced ----
     // Each thread takes elements tid, tid + 256, ...; operands are fetched in
     // groups of kB before any of the group's results is written.
-    constexpr int kB = 4;
+    constexpr int kB = Epi::kBatch;
     const int nown = e - s;
     const int lmax = min(kNL, g.nlines - line0);
     bool bad = false;
@@ -609,7 +614,7 @@ __global__ void __launch_bounds__(kNL * 32)
 // nbx take the x windows, the rest the y windows.
 template <class P1, class P2, bool SIXTH, bool SECOND, class InX, class EpiX, class InY,
           class EpiY>
-__global__ void __launch_bounds__(kNL * 32, 4)
+__global__ void __launch_bounds__(kNL * 32, SECOND && P1::kPlanes >= 2 ? 3 : 4)
     k_lines_xy(InX inx, LineGeo gx, EpiX ex, InY iny, LineGeo gy, EpiY ey, LineConst<P1> k1,
                LineConst<PolF> k1f, LineConst<P2> k2, DevState* st, int bump, int nbx) {
     if (bump && blockIdx.x == 0 && threadIdx.x == 0) st->t += 1;
@@ -670,6 +675,7 @@ __global__ void __launch_bounds__(kNL * 32, 3)
 // ---- epilogues: return true when a value is bad (flags the run) ----
 template <class O, class V2>
 struct EpiStore {
+    static constexpr int kBatch = 4;  // outputs fetched per thread before any is written
     O* d1;
     V2* d2;
     struct Ops {};
@@ -695,6 +701,7 @@ struct EpiStore {
 // is the arithmetic of the EOS.
 template <class R, class O, class RhoT>
 struct EpiMu {
+    static constexpr int kBatch = 4;
     O* dyr;
     O* mu;
     const RhoT* __restrict__ rho;
@@ -734,6 +741,7 @@ struct EpiMu {
 // F = -rho d(mu-hat) + c_s^2 d(rho), Eq. 12.
 template <class O, class RhoT>
 struct EpiForce {
+    static constexpr int kBatch = 2;  // its operands are float4 pairs: two in flight
     O* F;
     const RhoT* __restrict__ rho;
     const O* __restrict__ dr;
@@ -844,8 +852,7 @@ LineGeo make_geo(int nx, int ny, int axis, int H, bool walls_y = false) {
 template <class P1, class P2, bool SECOND>
 size_t smem_bytes() {
     return (size_t)P1::kPlanes * kNL * kLW * sizeof(typename P1::S) +
-           (size_t)kNL * kSO * sizeof(typename P1::O) +
-           (SECOND ? (size_t)kNL * kSO * sizeof(typename P2::V) : 0);
+           (SECOND && P1::kPlanes < 2 ? (size_t)kNL * kSO * sizeof(typename P2::V) : 0);
 }
 
 template <int AXIS, class P1, class P2, bool SIXTH, bool SECOND, class In, class Epi>
