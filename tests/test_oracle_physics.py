@@ -1,0 +1,102 @@
+"""The oracle against the paper's physical invariants (Secs. 5.1, 5.3-5.5), on
+CPU at sizes the plain C oracle finishes in seconds.  The Maxwell pair and the
+flat-interface tension these compare with come from oracle/thermo.py, pinned
+by closed forms in test_oracle_lbm.py and test_oracle_eos_variants.py.
+
+  * flat coexistence (Sec. 5.1): the liquid settles on the Maxwell density; the
+    gas settles slightly above it, by the discrete scheme's offset (+0.65% at
+    T_r 0.8, k 0.3), which the paper's logarithmic axis does not resolve;
+  * Young-Laplace (Sec. 5.3): Delta P R is the same for drops of radius 12 and
+    15, and the slope is the flat tension of Eq. 24 times 1.5-1.9 (the
+    effective kappa of the discrete scheme, measured 1.73);
+  * spurious current (Sec. 5.4): below 1e-3 at equilibrium (measured 3.1e-4 at
+    T_r 0.7, k 0.25);
+  * Galilean invariance (Sec. 5.5): a drop advected at 0.05 for 400 steps moves
+    by 20 nodes and keeps the static drop's outline.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import OracleSim, thermo
+from paper_1906_09530_gb300 import workloads as W
+
+pytestmark = pytest.mark.slow
+TC, _ = thermo.critical_point()
+
+
+def test_flat_coexistence_against_maxwell():
+    tr, k, ny = 0.8, 0.3, 100
+    rg, rl = thermo.maxwell(tr)
+    o = OracleSim(8, ny, tr * TC, 0.1, 1.0, k, 6)
+    o.set_fields(W.flat(8, ny, rg, rl, ny / 2, 4.0 / k))
+    o.step(10_000)
+    r = o.fields()[0][:, 0]
+    gas = np.r_[r[:10], r[-10:]].mean()
+    liq = r[ny // 2 - 10: ny // 2 + 10].mean()
+    assert abs(liq / rl - 1) <= 1e-4
+    assert 0 < gas / rg - 1 <= 1e-2
+
+
+def _drop_state(n, T, k, R, steps, width=4.0):
+    rg, rl = thermo.maxwell(T / TC)
+    o = OracleSim(n, n, T, 0.1, 1.0, k, 6)
+    o.set_fields(W.drop(n, n, rg, rl, R, width))
+    o.step(steps)
+    return o.fields()[:3], rg, rl
+
+
+def test_laplace_law():
+    tr, k, n = 0.7, 0.5, 48
+    T = tr * TC
+    y, x = np.mgrid[0:n, 0:n]
+    d = np.hypot(x - n / 2, y - n / 2)
+    prod, R_eff, dP_all = [], [], []
+    for R in (12.0, 15.0):
+        (rho, _, _), rg, rl = _drop_state(n, T, k, R, 3000)
+        Ri = math.sqrt((rho > 0.5 * (rg + rl)).sum() / math.pi)
+        rin = rho[d < 0.5 * Ri].mean()
+        rout = rho[d > Ri + 0.5 * (n / 2 - Ri)].mean()
+        dP = k * k * (thermo.p0(rin, T) - thermo.p0(rout, T))
+        prod.append(dP * Ri)
+        R_eff.append(Ri)
+        dP_all.append(dP)
+    assert dP_all[0] > dP_all[1] > 0
+    assert abs(prod[0] / prod[1] - 1) <= 0.02
+    ratio = np.mean(prod) / thermo.sigma_flat(tr, 0.1, k)
+    assert 1.5 <= ratio <= 1.9, ratio
+
+
+def test_spurious_current():
+    tr, k, n = 0.7, 0.25, 96
+    (rho, vx, vy), _, _ = _drop_state(n, tr * TC, k, 24.0, 4000, width=4.0 / k)
+    assert np.hypot(vx, vy).max() < 1e-3
+
+
+def test_galilean_translation():
+    tr, k, n, u0, steps = 0.7, 0.5, 32, 0.05, 400
+    T = tr * TC
+    rg, rl = thermo.maxwell(tr)
+    out = []
+    for u in (0.0, u0):
+        o = OracleSim(n, n, T, 0.1, 1.0, k, 6)
+        rho = W.drop(n, n, rg, rl, 8.0, 4.0)
+        o.set_fields(rho, np.full_like(rho, u), np.zeros_like(rho))
+        o.step(steps)
+        out.append(o.fields()[0])
+
+    def centre_x(r):  # centre of the excess mass along the periodic x axis
+        w = (r - rg).sum(axis=0)
+        ang = 2 * np.pi * np.arange(n) / n
+        return (np.angle((w * np.exp(1j * ang)).sum()) / (2 * np.pi) * n) % n
+
+    static, moved = out
+    shift = (centre_x(moved) - centre_x(static)) % n
+    assert abs(shift - u0 * steps) <= 0.5
+    back = np.roll(moved, -int(round(u0 * steps)), axis=1)
+    mid = 0.5 * (rg + rl)
+    ps, pm = static > mid, back > mid
+    links = (np.diff(ps.astype(np.int8), axis=1) != 0).sum() + \
+        (np.diff(ps.astype(np.int8), axis=0) != 0).sum()
+    assert (ps != pm).sum() <= 0.25 * links
