@@ -605,6 +605,7 @@ def surrogate_demo():
         cases.append(row)
         if t_r == 0.35:
             cases.append(warm_drop_case(s, eq, t_r))
+    cases.append(coexistence_curve_case(s))
     s.close()
     return {"workload": "slab-8x1536-k0.2-kappa0.1, surrogate trained on 256 slabs T_r 0.33-0.5",
             "training_data_s": data_s, "fit_s": fit_s, "fit_loss": loss,
@@ -613,6 +614,86 @@ def surrogate_demo():
                          "frac": tflops / peak,
                          "note": "256-wide products: latency-bound, microseconds per step"},
             "cases": cases}
+
+
+def coexistence_curve_case(s, n=16, ny=1536, tol=1e-3, every=500, window=16,
+                           max_steps=300_000):
+    """A coexistence curve of n temperatures (T_r 0.35-0.48, kappa-hat 0.1, k 0.2,
+    flat slabs 8 x ny), two ways, each until both bulk densities of every slab,
+    averaged over the last `window` samples taken every `every` steps, are
+    within tol of the method's own equilibrium (a batched 300 000-step run of
+    8 x 384 slabs at the same parameters; the gas never reaches Maxwell at these
+    temperatures).  The average filters the acoustic waves of the tall liquid
+    layer, which viscosity damps only over about 3e5 steps and which a single
+    sample would alias.
+      plain: one lone context per temperature from the tanh start, one after
+             another;
+      batched: one batch of all n from the tanh starts (batching alone);
+      batched + warm: one batch of all n from the surrogate's warm starts.
+    Wall times are the host clock around the stepping and the sampling."""
+    import numpy as np
+    from paper_1906_09530_gb300 import Batch, Simulation, lbm_maxwell, surrogate as SG
+    from paper_1906_09530_gb300 import workloads as W
+    T = np.linspace(0.35, 0.48, n)
+    K, k = np.full(n, 0.1), np.full(n, 0.2)
+    G, L, _ = SG.equilibrium_profiles(T, K, k, steps=300_000)
+
+    def bulk(r):
+        return (np.r_[r[: ny // 10], r[-ny // 10:]].mean(),
+                r[ny // 2 - ny // 10: ny // 2 + ny // 10].mean())
+
+    def run(step, sample, idx):
+        """Steps until the windowed means of every listed slab are within tol."""
+        hist, t = [], 0
+        while t < max_steps:
+            hist.append([sample(i) for i in idx])
+            if len(hist) >= window:
+                m = np.mean(np.array(hist[-window:]), axis=0)  # [slab][gas, liq]
+                if all(abs(m[j][0] / G[i] - 1) <= tol and abs(m[j][1] / L[i] - 1) <= tol
+                       for j, i in enumerate(idx)):
+                    return t, m
+            step(every)
+            t += every
+        return None, np.mean(np.array(hist[-window:]), axis=0)
+    t0 = time.perf_counter()
+    plain_steps = []
+    for i, t in enumerate(T):
+        rg, rl = lbm_maxwell(float(t))
+        sim = Simulation(8, ny, float(t), 0.1, 1.0, 0.2, fd_order=6, precision="mixed")
+        sim.set_fields(W.flat(8, ny, rg, rl, ny / 2, 20.0))
+        st, _ = run(sim.step, lambda _i: bulk(sim.fields()[0][:, 0]), [i])
+        plain_steps.append(st)
+        sim.close()
+    plain_s = time.perf_counter() - t0
+    specs = [dict(nx=8, ny=ny, T_r=float(t), k=0.2, kappa=0.1, tau=1.0) for t in T]
+    # batched, tanh starts (what batching alone gains)
+    t0 = time.perf_counter()
+    b = Batch(specs)
+    for i, t in enumerate(T):
+        b.set_fields(i, W.flat(8, ny, *lbm_maxwell(float(t)), ny / 2, 20.0))
+    tanh_steps, _ = run(b.step, lambda i: bulk(b.fields(i)[0][:, 0]), list(range(n)))
+    batch_tanh_s = time.perf_counter() - t0
+    b.close()
+    # batched, warm starts
+    t0 = time.perf_counter()
+    g, l, w = s.predict(T, K, k)
+    b = Batch(specs)
+    for i in range(n):
+        b.set_fields(i, SG.flat_field(8, ny, g[i], l[i], w[i]))
+    steps, m = run(b.step, lambda i: bulk(b.fields(i)[0][:, 0]), list(range(n)))
+    batch_s = time.perf_counter() - t0
+    b.close()
+    worst = float(max(max(abs(m[i][0] / G[i] - 1), abs(m[i][1] / L[i] - 1)) for i in range(n)))
+    return {"case": f"coexistence-curve-{n}-slabs-8x{ny}-Tr0.35-0.48-k0.2-mixed",
+            "criterion": f"both bulks, averaged over {window} samples {every} steps apart, "
+                         f"within {tol:g} of the method's equilibrium, every slab",
+            "plain_sequential_tanh": {"wall_s": plain_s, "steps_per_slab": plain_steps,
+                                      "all_reached": all(x is not None for x in plain_steps)},
+            "batched_tanh": {"wall_s": batch_tanh_s, "steps": tanh_steps,
+                             "reached": tanh_steps is not None},
+            "batched_warm": {"wall_s": batch_s, "steps": steps, "reached": steps is not None,
+                             "worst_windowed_rel_dev": worst},
+            "speedup": plain_s / batch_s}
 
 
 def warm_drop_case(s, eq, t_r, n=4096, radius=1000.0, every=5000, max_steps=100_000):
