@@ -234,7 +234,7 @@ def lbm_cfd_df(u_hi, u_lo, axis, fd_order, second=False, stream=None):
 
 
 class Simulation:
-    """One periodic D2Q9 run of the method on the current CUDA device.
+    """One D2Q9 run of the method (periodic, or with walls in y) on the current CUDA device.
 
     Owns a torch uint8 workspace and the library context.  Host inputs/outputs are
     numpy float64 [ny][nx]; device variants take/return torch float64 tensors.
