@@ -23,6 +23,11 @@
  *
  * Populations are stored structure-of-arrays, f[i][y][x], i = 0..8 in the
  * velocity order of Sec. 2.
+ *
+ * Periodic in x; in y periodic or between solid walls (Sec. 5.5): halfway
+ * bounce-back, walls that may move along x (a moving reference frame), and the
+ * density and mu-hat extended evenly about the walls for their y-derivatives.
+ * The chemical-potential upper limit of Sec. 5.6 also takes the EOS pole.
  */
 #include <math.h>
 #include <stddef.h>
