@@ -74,3 +74,41 @@ def test_moving_frame_keeps_the_outline(cuda):
     links = (np.diff(a.astype(np.int8), axis=1) != 0).sum() + \
         (np.diff(a.astype(np.int8), axis=0) != 0).sum()
     assert links > 500 and (a != b).sum() <= 0.1 * links, ((a != b).sum(), links)
+
+
+def _small_pr_impact(precision, cap, steps=200):
+    """(GPU density, oracle density) after `steps` steps of a small PR impact:
+    water at T_r 0.6, k 0.1, kappa-hat 0.005, tau 0.7, walls in y, a drop (R 10)
+    falling at 0.1 onto a film (8) of a 96 x 48 channel; cap: the upper limit
+    mu_max, active throughout, or None."""
+    from oracle import OracleSim
+    from oracle import eos as E
+    import paper_1906_09530_gb300 as P
+    ee = E.Eos("pr", omega=0.344)
+    tc, _ = ee.critical_point()
+    rg, rl = ee.maxwell(0.6)
+    nx, ny = 96, 48
+    fields = W.splash(nx, ny, rg, rl, 8, 10.0, 14.0, 20.0, -0.1)
+    kw = dict(mu_max=cap, mu_cap_steps=1000) if cap else {}
+    g = P.Simulation(nx, ny, 0.6, 0.005, 0.7, 0.1, fd_order=6, precision=precision,
+                     eos=P.make_eos("pr", omega=0.344), walls_y=True, **kw)
+    g.set_fields(*fields)
+    g.step(steps)
+    o = OracleSim(nx, ny, 0.6 * tc, 0.005, 0.7, 0.1, 6, eos=ee, walls_y=True, **kw)
+    o.set_fields(*fields)
+    o.step(steps)
+    got = g.fields()[0]
+    g.close()
+    return got, o.fields()[0]
+
+
+@pytest.mark.parametrize("precision,cap,tol", [("fp64", None, 1e-10), ("fp64", 0.9, 1e-10),
+                                               ("mixed", None, 1e-4), ("mixed", 0.9, 1e-4)])
+def test_small_pr_impact_against_oracle(cuda, precision, cap, tol):
+    """The splash's arithmetic at a size the oracle steps in seconds, 200 steps.
+    Without a limit the impact compresses the liquid to 10.06, below the PR
+    pole 1/b = 10.5.  With mu_max = 0.9 (mu0 passes it near rho 10) the limit
+    acts, the compression then passes the pole (to 11.0) and those nodes take
+    the limit (reading of Sec. 5.6 in the oracle's force stage)."""
+    got, want = _small_pr_impact(precision, cap)
+    assert np.max(np.abs(got - want) / want) <= tol
