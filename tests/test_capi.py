@@ -149,3 +149,28 @@ def test_oracle_and_library_share_nothing():
     for f in os.listdir(os.path.join(root, "oracle")):
         if f.endswith((".py", ".c")):
             assert not bad_orc.search(open(os.path.join(root, "oracle", f)).read()), f
+
+
+def test_batch_init_validates_before_any_device_work():
+    """Batches hold periodic instances of the mixed path only; the checks run
+    before the library touches a device."""
+    import ctypes as C
+    lib = P.lib()
+    eos = P.cs_eos()
+
+    def init(periodic_y=1, prec=B.LBM_PREC_MIXED, order=6):
+        inst = (B.LbmInstance * 1)()
+        inst[0] = B.LbmInstance(B.LbmGrid(64, 64, 1, periodic_y), 0.7, 0.1, 1.0, 0.5,
+                                float("inf"), 0)
+        opts = B.LbmOpts(prec, order, float("inf"), 0)
+        out = C.c_void_p()
+        return lib.lbm_batch_init(C.byref(out), inst, 1, C.byref(eos), C.byref(opts), None, 0,
+                                  None), out
+    st, out = init(periodic_y=0)
+    assert st == B.LBM_ENOTIMPL and not out.value
+    st, _ = init(prec=B.LBM_PREC_FP64)
+    assert st == B.LBM_ENOTIMPL
+    st, _ = init(order=5)
+    assert st == B.LBM_EINVAL
+    st, _ = init()  # valid instance, but no workspace
+    assert st == B.LBM_EINVAL
