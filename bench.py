@@ -33,7 +33,6 @@ on the data path); rank 0 prints the JSON line.
 """
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess

@@ -13,7 +13,6 @@ Tolerances (written here, justified by the arithmetic):
     FP64 oracle, the 128^2 k = 1 drop (velocities ~0.03, the most dynamic case)
     stays within 1e-4 after 200 steps (measured 4.4e-5).
 """
-import math
 
 import numpy as np
 import pytest

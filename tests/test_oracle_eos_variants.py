@@ -12,7 +12,6 @@ with CS (Eqs. 20-21) by the same generic route.
     solver reproduces the dedicated CS solver of oracle/thermo.py;
   * the C oracle's p0 and mu0 equal the Python ones.
 """
-import math
 
 import numpy as np
 import pytest
