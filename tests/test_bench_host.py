@@ -1,0 +1,63 @@
+"""The benchmark's host-side measurement helpers on known inputs: the
+algorithmic bytes per pass, the spreading radius of an impact, the fit of the
+square-root spreading law, and the outline mismatch of two phase fields."""
+import math
+import os
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_pass_layout_bytes():
+    names, b = bench.pass_layout("mixed", 0)
+    assert names == ["collide_stream", "cfd_rho_xy", "mu_pointwise", "cfd_mu_force_xy"]
+    assert b == [88, 20, 16, 24] and sum(b) == 148
+    assert bench.pass_layout("mixed", 2)[1] == [88, 24, 16, 24]  # double-float density lines
+    names, b = bench.pass_layout("fp64")
+    assert len(names) == 5 and sum(b) == 288
+
+
+def test_spreading_radius_crosses_the_crater_to_the_rim():
+    row = np.zeros((3, 64))
+    row[1, 20:26] = 1.0  # left rim, outer edge at x = 20
+    row[1, 38:45] = 1.0  # right rim, outer edge at x = 44
+    assert bench.spreading_radius(row, 1, 32, 0.5) == pytest.approx((44 - 20 + 1) / 2)
+    full = np.zeros((3, 64))
+    full[1, 28:37] = 1.0  # liquid through the impact column
+    assert bench.spreading_radius(full, 1, 32, 0.5) == pytest.approx(4.5)
+    assert bench.spreading_radius(np.zeros((3, 64)), 1, 32, 0.5) == 0.0
+    wrap = np.ones((3, 16))
+    wrap[1, 3] = 0.0  # one gas node; the run wraps around the periodic row, and each
+    # way the search covers half the row: right edge 7 nodes out, left edge 6
+    assert bench.spreading_radius(wrap, 1, 10, 0.5) == pytest.approx(7.0)
+
+
+def test_spread_fit_recovers_a_square_root_law_and_drops_glitches():
+    D, C = 100.0, 1.3
+    t = np.linspace(0.1, 4.0, 80)
+    r = C * np.sqrt(t) * D
+    c, e = bench.spread_fit(t, r, D)
+    assert c == pytest.approx(C, rel=1e-12) and e == pytest.approx(0.5, rel=1e-12)
+    r2 = r.copy()
+    r2[30] *= 0.2  # the probe row met a bubble
+    c2, e2 = bench.spread_fit(t, r2, D)
+    assert c2 == pytest.approx(C, rel=1e-12) and e2 == pytest.approx(0.5, rel=1e-12)
+
+
+def test_phase_mismatch_of_a_shifted_disk():
+    n, R = 64, 10.0
+    y, x = np.mgrid[0:n, 0:n]
+    a = (np.hypot(x - 32, y - 32) < R).astype(float)
+    bad, links = bench.phase_mismatch(a, a, 0.5)
+    assert bad == 0
+    # about 2 pi R interface links on each axis pair: 4 R links per axis
+    assert links == pytest.approx(8 * R, rel=0.1)
+    b = np.roll(a, 1, axis=1)  # shifted by one node
+    bad, _ = bench.phase_mismatch(a, b, 0.5)
+    assert bad == pytest.approx(4 * R, rel=0.15)  # two half-perimeters' worth of columns
+    assert math.isfinite(bad / links)
