@@ -12,7 +12,12 @@ by closed forms in test_oracle_lbm.py and test_oracle_eos_variants.py.
   * spurious current (Sec. 5.4): below 1e-3 at equilibrium (measured 3.1e-4 at
     T_r 0.7, k 0.25);
   * Galilean invariance (Sec. 5.5): a drop advected at 0.05 for 400 steps moves
-    by 20 nodes and keeps the static drop's outline.
+    by 20 nodes and keeps the static drop's outline;
+  * independence of the relaxation time (Sec. 5.1): the MRT model at tau 0.8 and
+    the single-relaxation-time model at tau 3.0 settle on the same coexistence
+    densities (here to 1e-6);
+  * the interface width is inversely proportional to k (Sec. 5.2, Fig. 6): the
+    10-90% width at k 0.1 is twice that at k 0.2, to 5%.
 """
 import math
 
@@ -100,3 +105,42 @@ def test_galilean_translation():
     links = (np.diff(ps.astype(np.int8), axis=1) != 0).sum() + \
         (np.diff(ps.astype(np.int8), axis=0) != 0).sum()
     assert (ps != pm).sum() <= 0.25 * links
+
+
+def _flat_bulks(tr, k, ny, tau, steps, mrt=None):
+    from oracle import sim as S
+    rg, rl = thermo.maxwell(tr)
+    o = OracleSim(8, ny, tr * TC, 0.1, tau, k, 6, mrt=S.PAPER_MRT if mrt else None)
+    o.set_fields(W.flat(8, ny, rg, rl, ny / 2, 4.0 / k))
+    o.step(steps)
+    return o.fields()[0][:, 0]
+
+
+def test_coexistence_independent_of_relaxation_time():
+    ny = 64
+    a = _flat_bulks(0.7, 0.3, ny, 3.0, 20_000)
+    b = _flat_bulks(0.7, 0.3, ny, 0.8, 20_000, mrt=True)
+    for r in (a, b):
+        assert np.isfinite(r).all()
+    ga, la = np.r_[a[:6], a[-6:]].mean(), a[ny // 2 - 6: ny // 2 + 6].mean()
+    gb, lb = np.r_[b[:6], b[-6:]].mean(), b[ny // 2 - 6: ny // 2 + 6].mean()
+    assert abs(ga / gb - 1) <= 1e-6 and abs(la / lb - 1) <= 1e-6
+
+
+def _width_10_90(r):
+    n = r.size
+    g = np.r_[r[:10], r[-10:]].mean()
+    l = r[n // 2 - 10: n // 2 + 10].mean()
+    half = r[: n // 2]
+
+    def cross(v):
+        i = int(np.argmax(half >= v))
+        return (i - 1) + (v - half[i - 1]) / (half[i] - half[i - 1])
+    return cross(g + 0.9 * (l - g)) - cross(g + 0.1 * (l - g))
+
+
+def test_interface_width_inversely_proportional_to_k():
+    w2 = _width_10_90(_flat_bulks(0.6, 0.2, 200, 1.0, 10_000))
+    w1 = _width_10_90(_flat_bulks(0.6, 0.1, 400, 1.0, 10_000))
+    assert abs(w1 / w2 / 2 - 1) <= 0.05, (w1, w2)
+
