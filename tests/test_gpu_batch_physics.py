@@ -8,8 +8,8 @@ height 400, k = 0.1, 200 000 steps):
   * the gas density settles above the Maxwell value by an offset that grows as
     T_r falls (+3e-3 at 0.62, +2.5e-2 at 0.47, +7.3e-2 at 0.4, +0.38 at 0.3) and
     is the same for tau = 0.8, 1.0, 1.5 and for the FP64 and mixed paths: a
-    property of the discrete scheme (its bulk chemical potentials differ by
-    k^2 R T ln(rho_g / rho_g,Maxwell)), not of the precision.  On the paper's
+    property of the discrete scheme (its bulk chemical potentials differ, by
+    about k^2 R T ln(rho_g / rho_g,Maxwell) at low T_r), not of the precision.  On the paper's
     logarithmic gas axis these offsets are at most 0.14 decade.
 So the batch is checked against Maxwell on the liquid side and against the lone
 FP64 path on the gas side.
