@@ -16,8 +16,9 @@ by closed forms in test_oracle_lbm.py and test_oracle_eos_variants.py.
   * independence of the relaxation time (Sec. 5.1): the MRT model at tau 0.8 and
     the single-relaxation-time model at tau 3.0 settle on the same coexistence
     densities (here to 1e-6);
-  * the interface width is inversely proportional to k (Sec. 5.2, Fig. 6): the
-    10-90% width at k 0.1 is twice that at k 0.2, to 5%;
+  * the interface width is inversely proportional to k and the mesh-space
+    tension proportional to it (Sec. 5.2, Figs. 6-7): at k 0.1 the 10-90% width
+    is twice and kappa-hat * sum (d rho/dy)^2 half that at k 0.2, to 5%;
   * the chemical potential is constant in the bulk phases at equilibrium (Sec.
     5.1): within each bulk of a flat interface to 1e-6 (measured 2e-7 in the gas,
     3e-10 in the liquid; |mu-hat| is 5e-3).
@@ -142,10 +143,21 @@ def _width_10_90(r):
     return cross(g + 0.9 * (l - g)) - cross(g + 0.1 * (l - g))
 
 
-def test_interface_width_inversely_proportional_to_k():
-    w2 = _width_10_90(_flat_bulks(0.6, 0.2, 200, 1.0, 10_000))
-    w1 = _width_10_90(_flat_bulks(0.6, 0.1, 400, 1.0, 10_000))
+def _sigma(r, kappa=0.1):
+    """kappa-hat times the sum of (d rho / dy)^2 over one interface (Eq. 24's
+    integral over the measured profile, central differences)."""
+    d = np.gradient(r[: r.size // 2 + 1])
+    return kappa * np.sum(d * d)
+
+
+def test_interface_width_and_tension_scale_with_k():
+    """Width proportional to 1/k and the mesh-space tension to k, so both are
+    the same in the momentum space (Sec. 5.2, Figs. 6-7)."""
+    r2 = _flat_bulks(0.6, 0.2, 200, 1.0, 10_000)
+    r1 = _flat_bulks(0.6, 0.1, 400, 1.0, 10_000)
+    w2, w1 = _width_10_90(r2), _width_10_90(r1)
     assert abs(w1 / w2 / 2 - 1) <= 0.05, (w1, w2)
+    assert abs(_sigma(r2) / _sigma(r1) / 2 - 1) <= 0.05
 
 
 def test_chemical_potential_constant_in_each_bulk():
