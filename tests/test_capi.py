@@ -174,3 +174,23 @@ def test_batch_init_validates_before_any_device_work():
     assert st == B.LBM_EINVAL
     st, _ = init()  # valid instance, but no workspace
     assert st == B.LBM_EINVAL
+
+
+def test_header_is_plain_c():
+    """include/cplbm.h is a C header: it compiles as C99 with -pedantic."""
+    import shutil
+    import subprocess
+    import tempfile
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(__file__))
+    with tempfile.TemporaryDirectory() as d:
+        src = os.path.join(d, "t.c")
+        with open(src, "w") as f:
+            f.write('#include "cplbm.h"\nint main(void) { lbm_grid g = {8, 8, 1, 0}; '
+                    '(void)g; return 0; }\n')
+        r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I",
+                            os.path.join(root, "include"), "-c", src, "-o",
+                            os.path.join(d, "t.o")], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
