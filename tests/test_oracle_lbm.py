@@ -1,6 +1,11 @@
 """Pins of the oracle's lattice Boltzmann step (Eqs. 1-5, 12, 33), CPU only.
 
-  * the exact-difference forcing of Eq. 5 adds no mass and exactly the momentum F;
+  * the exact-difference forcing of Eq. 5 adds no mass and exactly the momentum F,
+    and changes the second moment by rho[(u + F/rho)(u + F/rho) - u u], the
+    equilibrium's own change (a Guo-type or first-order forcing does not);
+  * at a converged flat interface the fluid velocity v = u + F/(2 rho) of Sec. 2
+    vanishes (under 1e-9 after 8000 steps) while the bare moment u = sum e_i f_i / rho does not
+    (0.05): this fixes the half-force shift;
   * the equilibrium of Eq. 2 has the textbook moments;
   * a uniform fluid at rest is a fixed point (the compact derivative of a
     constant is exactly zero, so F = 0);
@@ -30,6 +35,28 @@ def test_forcing_adds_momentum_F(rho, ux, uy, Fx, Fy):
     assert abs(Fi.sum()) < 1e-15 * rho
     assert (EX * Fi).sum() == pytest.approx(Fx, rel=1e-10, abs=1e-18)
     assert (EY * Fi).sum() == pytest.approx(Fy, rel=1e-10, abs=1e-18)
+
+
+@pytest.mark.parametrize("rho,ux,uy,Fx,Fy", [(0.4, 0.01, -0.02, 1e-3, 2e-3),
+                                             (2.0, -0.1, 0.07, -0.05, 0.03)])
+def test_forcing_second_moment(rho, ux, uy, Fx, Fy):
+    Fi = forcing_terms(rho, ux, uy, Fx, Fy)
+    vx, vy = ux + Fx / rho, uy + Fy / rho
+    assert (EX * EX * Fi).sum() == pytest.approx(rho * (vx * vx - ux * ux), rel=1e-12)
+    assert (EY * EY * Fi).sum() == pytest.approx(rho * (vy * vy - uy * uy), rel=1e-12)
+    assert (EX * EY * Fi).sum() == pytest.approx(rho * (vx * vy - ux * uy), rel=1e-12)
+
+
+def test_flat_equilibrium_is_at_rest_in_the_half_force_velocity():
+    tr, k, ny = 0.8, 0.3, 64
+    rg, rl = thermo.maxwell(tr)
+    sim = OracleSim(4, ny, tr * TC, 0.1, 1.0, k, 6)
+    sim.set_fields(W.flat(4, ny, rg, rl, ny / 2, 4.0 / k))
+    sim.step(8000)  # measured: |v| 3e-11
+    rho, vx, vy = sim.fields()[:3]
+    u = (EY[:, None, None] * sim.f).sum(axis=0) / rho
+    assert np.abs(vy).max() <= 1e-9 and np.all(vx == 0.0)
+    assert np.abs(u).max() >= 0.01
 
 
 def test_equilibrium_moments():
