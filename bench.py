@@ -22,9 +22,9 @@ passes).  Timing: W warm-up steps, then K steps, each bracketed by one pair of
 CUDA events on the library's stream; between steps a 512 MB buffer is written
 and another 512 MB read to flush the L2 (not timed).  value = nodes x K / sum
 of step times.  The per-pass breakdown and the roofline come from a further
-min(K, 200) flushed steps with events around every pass (lbm_step_timed).  e2e = the same metric through the public host
-API (lbm_set_fields from pinned host memory, K steps, lbm_fields back to host),
-wall clock.
+min(K, 200) flushed steps with events around every pass (lbm_step_timed).
+e2e = the same metric through the public host API (lbm_set_fields from pinned
+host memory, K steps, lbm_fields back to host), wall clock.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -803,8 +803,8 @@ def run_reference(args, w):
             "config": {"workload": workload_name(w, args.precision),
                        "arithmetic": "the FP64 oracle on the same workload"},
             "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                             "sample": f"{k} full-grid FP64 oracle steps (of {args.steps} "
-                                       "asked; bounded to ~150 s), 1 thread"},
+                             "sample": f"{k} full-grid FP64 oracle step{'s' * (k != 1)} "
+                                       f"(of {args.steps} asked; bounded to ~150 s), 1 thread"},
             "e2e": {"value": val, "unit": "MLUPS", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -954,7 +954,8 @@ def main():
             "dtype": "f32+f64" if args.precision == "mixed" else "f64",
             "data": "synthetic",
             "config": {"workload": workload_name(w, args.precision), "nodes": N,
-                       "l2": "512 MB write + 512 MB read between timed steps (L2 flushed, left clean)",
+                       "l2": "512 MB write + 512 MB read between timed steps "
+                             "(L2 flushed, left clean)",
                        "parallelism": f"replicas{world}" if world > 1 else "single"},
             "roofline": roofline,
             "step_roofline": {"alg_bytes_per_node": sum(pb), "achieved_GB/s": step_gbs,

@@ -9,8 +9,9 @@ benchmark problems, run to equilibrium on the GPU.
   * Galilean invariance: a drop advected at u0 keeps its shape (Sec. 5.5);
   * the chemical-potential upper limit keeps mass (Sec. 5.6).
 
-Measured levels these bounds were set against: flat coexistence at k = 0.1 settles to gas +7.5e-4 (T_r 0.8) / +1.2e-3 (T_r 0.7) and
-liquid within 2e-4 of Maxwell; drops give Delta P * R constant to < 1% across radii.
+Measured levels these bounds were set against: flat coexistence at k = 0.1
+settles to gas +7.5e-4 (T_r 0.8) / +1.2e-3 (T_r 0.7) and liquid within 2e-4 of
+Maxwell; drops give Delta P * R constant to < 1% across radii.
 """
 import math
 
