@@ -194,3 +194,57 @@ def test_header_is_plain_c():
                             os.path.join(root, "include"), "-c", src, "-o",
                             os.path.join(d, "t.o")], capture_output=True, text=True)
         assert r.returncode == 0, r.stderr
+
+
+C_CONSUMER = r"""
+#include <math.h>
+#include <stdio.h>
+#include "cplbm.h"
+int main(void)
+{
+    lbm_eos cs = {LBM_EOS_CS, 1.0, 4.0, 1.0, 0.0};
+    lbm_grid grid = {1024, 1024, 1, 1}, bad = {4, 1024, 1, 1};
+    lbm_opts opts = {LBM_PREC_MIXED, 6, INFINITY, 0, LBM_COLLIDE_BGK, 0.0, 0.0, 0.0};
+    double tc, rc, g, l;
+    if (lbm_critical(&cs, &tc, &rc) != LBM_OK || lbm_maxwell(&cs, 0.5, &g, &l) != LBM_OK)
+        return 1;
+    printf("%.17g %.17g %.17g %.17g %zu %zu %d\n", tc, rc, g, l,
+           lbm_workspace_bytes(&grid, &opts), lbm_workspace_bytes(&bad, &opts),
+           lbm_strerror(LBM_EINVAL) != NULL && lbm_strerror(LBM_EINVAL)[0] != 0);
+    return 0;
+}
+"""
+
+
+def test_plain_c_program_links_and_calls_the_host_entry_points():
+    """A C99 program built against include/cplbm.h and linked to the library
+    calls the host-only entry points (no GPU needed) and gets the oracle's
+    thermodynamics."""
+    import shutil
+    import subprocess
+    import tempfile
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    so = P.lib()._name
+    root = os.path.dirname(os.path.dirname(__file__))
+    with tempfile.TemporaryDirectory() as d:
+        src, exe = os.path.join(d, "consumer.c"), os.path.join(d, "consumer")
+        with open(src, "w") as f:
+            f.write(C_CONSUMER)
+        r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I",
+                            os.path.join(root, "include"), src, "-o", exe, so,
+                            "-Wl,-rpath," + os.path.dirname(so), "-lm"],
+                           capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
+        r = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+        assert r.returncode == 0, r.stderr
+    tc, rc, g, l, ws, ws_bad, msg = r.stdout.split()
+    otc, orc = thermo.critical_point()
+    og, ol = thermo.maxwell(0.5)
+    assert float(tc) == pytest.approx(otc, rel=1e-12)
+    assert float(rc) == pytest.approx(orc, rel=1e-10)
+    assert float(g) == pytest.approx(og, rel=1e-9) and float(l) == pytest.approx(ol, rel=1e-12)
+    # mixed: two FP32 population buffers (72 B) and eight 4-byte field planes (32 B)
+    assert 1024 * 1024 * 104 <= int(ws) <= 1024 * 1024 * 105
+    assert int(ws_bad) == 0 and msg == "1"
