@@ -364,6 +364,8 @@ lbm_status lbm_mlp_init(lbm_mlp **out, int32_t max_batch, void *d_workspace, siz
 /* Set the parameters from a host vector (and reset Adam's moments and step
  * count); returns when copied. */
 lbm_status lbm_mlp_set_params(lbm_mlp *net, const float *h_params);
+/* Copy the parameters into a host vector of lbm_mlp_param_count() floats;
+ * returns when copied. */
 lbm_status lbm_mlp_get_params(lbm_mlp *net, float *h_params);
 /* y = network(x), enqueued. */
 lbm_status lbm_mlp_forward(lbm_mlp *net, const float *d_x, int32_t batch, float *d_y);
@@ -375,8 +377,11 @@ lbm_status lbm_mlp_loss_grad(lbm_mlp *net, const float *d_x, const float *d_t, i
 /* One Adam step with learning rate lr > 0 on the batch (x, t). */
 lbm_status lbm_mlp_train_step(lbm_mlp *net, const float *d_x, const float *d_t, int32_t batch,
                               float lr, double *h_loss);
+/* Release the network (not the workspace or the stream); NULL is a no-op. */
 void lbm_mlp_free(lbm_mlp *net);
 
+/* A static, NUL-terminated description of a status; never NULL (unknown codes
+ * get a generic message). */
 const char *lbm_strerror(lbm_status s);
 
 /* Release the context (not the workspace or the stream, which the caller owns). */
