@@ -248,3 +248,48 @@ def test_plain_c_program_links_and_calls_the_host_entry_points():
     # mixed: two FP32 population buffers (72 B) and eight 4-byte field planes (32 B)
     assert 1024 * 1024 * 104 <= int(ws) <= 1024 * 1024 * 105
     assert int(ws_bad) == 0 and msg == "1"
+
+
+_SCALAR = {"double": C.c_double, "float": C.c_float, "int32_t": C.c_int32,
+           "int64_t": C.c_int64, "size_t": C.c_size_t, "lbm_status": C.c_int}
+
+
+def _declarations():
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    out = {}
+    for ret, name, params in re.findall(
+            r"((?:const\s+)?[A-Za-z_]\w*\s*\*?)\s*\b(lbm_\w+)\s*\(([^)]*)\)\s*;", src):
+        ps = [p.strip() for p in params.replace("\n", " ").split(",")]
+        out[name] = (ret.strip(), [] if ps == ["void"] else ps)
+    return out
+
+
+def _matches(ctype_decl, ct):
+    """Whether a ctypes type `ct` passes the C type of a declaration (a
+    parameter with its name, or a return type) without truncation."""
+    words = ctype_decl.replace("*", " * ").split()
+    if "*" in words:
+        if words[:2] == ["const", "char"] and words.count("*") == 1 and len(words) <= 4:
+            return ct is C.c_char_p or ct is C.c_void_p
+        return ct is C.c_void_p or ct is C.c_char_p or issubclass(ct, C._Pointer)
+    base = [w for w in words if w != "const"][0]
+    if base == "void":
+        return ct is None
+    return ct is _SCALAR[base]
+
+
+def test_binding_signatures_match_the_header():
+    """Every function the header declares has a ctypes signature in the
+    binding, with the same number of parameters, a pointer type wherever the
+    header has a pointer, and the exact scalar type elsewhere (a default int
+    return or argument would truncate a size_t, an int64_t or a pointer)."""
+    lib = P.lib()
+    decls = _declarations()
+    assert len(decls) == len(declared_symbols())
+    for name, (ret, params) in decls.items():
+        fn = getattr(lib, name)
+        assert fn.argtypes is not None, name
+        assert len(fn.argtypes) == len(params), (name, params, fn.argtypes)
+        assert _matches(ret, fn.restype), (name, ret, fn.restype)
+        for p, ct in zip(params, fn.argtypes):
+            assert _matches(p, ct), (name, p, ct)
