@@ -293,3 +293,43 @@ def test_binding_signatures_match_the_header():
         assert _matches(ret, fn.restype), (name, ret, fn.restype)
         for p, ct in zip(params, fn.argtypes):
             assert _matches(p, ct), (name, p, ct)
+
+
+def test_struct_layouts_match_the_header():
+    """The binding's ctypes structures have the size and the field offsets that
+    a C compiler gives the header's structs (so no field is read across
+    padding)."""
+    import shutil
+    import subprocess
+    import tempfile
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    structs = {"lbm_grid": B.LbmGrid, "lbm_eos": B.LbmEos, "lbm_opts": B.LbmOpts,
+               "lbm_instance": B.LbmInstance}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "cplbm.h"',
+             'int main(void) {']
+    for cname, py in structs.items():
+        lines.append(f'    printf("{cname} size %zu\\n", sizeof({cname}));')
+        for field, _ in py._fields_:
+            lines.append(f'    printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
+    lines += ['    return 0;', '}']
+    root = os.path.dirname(os.path.dirname(__file__))
+    with tempfile.TemporaryDirectory() as d:
+        src, exe = os.path.join(d, "layout.c"), os.path.join(d, "layout")
+        with open(src, "w") as f:
+            f.write("\n".join(lines) + "\n")
+        r = subprocess.run([gcc, "-std=c99", "-Wall", "-Werror", "-I",
+                            os.path.join(root, "include"), src, "-o", exe],
+                           capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
+        out = subprocess.run([exe], capture_output=True, text=True, timeout=60).stdout
+    got = {}
+    for line in out.split("\n"):
+        if line:
+            cname, key, val = line.split()
+            got[(cname, key)] = int(val)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == C.sizeof(py), cname
+        for field, _ in py._fields_:
+            assert got[(cname, field)] == getattr(py, field).offset, (cname, field)
