@@ -71,9 +71,11 @@ def test_batch_coexistence_curve(cuda):
 
 def test_batch_laplace_fit(cuda):
     """Eq. 40 over a batch of drops of radii 29-70 (T_r 0.7, k 0.25): Delta P
-    against 1/R is a line through the origin.  Its slope is the scheme's tension,
-    1.6-1.8 times the Eq. 24 value with the nominal kappa (the effective kappa of
-    the discrete scheme is about 2.9 times nominal; sigma scales as its root)."""
+    against 1/R is a line through the origin.  Its slope is the tension of the
+    scheme's discrete equilibrium, Eq. 24 with kappa-hat replaced by
+    kappa-hat + c_s^4/(4 rho) (the exact-difference forcing's momentum flux at
+    rest), which at T_r 0.7 and kappa-hat 0.1 is 1.76 times the nominal value
+    at any k."""
     from paper_1906_09530_gb300 import Batch
     T_r, k, n = 0.7, 0.25, 192
     rg, rl = thermo.maxwell(T_r)
