@@ -18,7 +18,9 @@ by closed forms in test_oracle_lbm.py and test_oracle_eos_variants.py.
     k 0.4, 6.7e-4 at 0.2, 1.6e-4 at 0.1), for any tau and under MRT, while
     Eq. 23 with the nominal kappa-hat stays 14% away at every k.  A slab at 45
     degrees to the grid follows the same law along its normal (1.5e-3 at
-    k 0.5): the law is isotropic at this order;
+    k 0.5): the law is isotropic at this order.  Started from Eq. 23's profile
+    with the nominal kappa-hat (T_r 0.5, k 0.2), the gas goes negative in the
+    first step; from the law's profile the run starts cleanly;
   * Young-Laplace (Sec. 5.3): Delta P R is the same for drops of radius 12 and
     15, and equals the tension of that law, the integral of
     sqrt(2 k^2 Omega(rho) kappa_eff(rho)) d rho (Eq. 24 with kappa_eff), to 3%
@@ -150,6 +152,25 @@ def test_diagonal_slab_follows_the_same_law():
         sel = (d > ys[0]) & (d < ys[-1])
         errs.append(np.abs(half[sel] - np.interp(d[sel], ys, rs)).max() / (rl - rg))
     assert errs[0] <= 3e-3 and errs[1] >= 0.1, errs
+
+
+def test_nominal_eq23_start_fails_and_the_law_start_does_not():
+    tr, kappa, k, ny = 0.5, 0.1, 0.2, 384
+    rg, rl = thermo.maxwell(tr)
+    rs = np.linspace(rg, rl, 4002)[1:-1]
+    d = ny / 4.0 - np.abs(np.arange(ny, dtype=np.float64) - ny / 2.0)  # > 0 in the liquid
+    mins = []
+    for kap in (lambda r_, c: c, _kappa_eff):
+        col = np.interp(d, _profile_y(rs, tr, kappa, k, kap), rs, left=rg, right=rl)
+        o = OracleSim(4, ny, tr * TC, kappa, 1.0, k, 6)
+        o.set_fields(np.repeat(col[:, None], 4, axis=1))
+        o.step(1)
+        mins.append(o.fields()[0].min())
+        if kap is _kappa_eff:
+            o.step(199)
+            r = o.fields()[0]
+            assert np.isfinite(r).all() and r.min() > 0.5 * rg
+    assert mins[0] < 0 < mins[1], mins
 
 
 def test_laplace_law():
