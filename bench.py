@@ -616,6 +616,25 @@ def surrogate_demo():
             "cases": cases}
 
 
+def windowed_equilibrium(step, sample, targets, tol, every, window, max_steps):
+    """Steps until the means of the last `window` samples of every item are
+    within tol (relative) of its target pair.  sample() returns one (gas,
+    liquid) pair per item; a sample is taken, then `every` steps are run, until
+    max_steps.  Returns (steps, means [item][2]) or (None, the last means)."""
+    import numpy as np
+    hist, t = [], 0
+    while t < max_steps:
+        hist.append(sample())
+        if len(hist) >= window:
+            m = np.mean(np.array(hist[-window:]), axis=0)
+            if all(abs(m[j][0] / g - 1) <= tol and abs(m[j][1] / l - 1) <= tol
+                   for j, (g, l) in enumerate(targets)):
+                return t, m
+        step(every)
+        t += every
+    return None, np.mean(np.array(hist[-window:]), axis=0)
+
+
 def coexistence_curve_case(s, n=16, ny=1536, tol=1e-3, every=500, window=16,
                            max_steps=300_000):
     """A coexistence curve of n temperatures (T_r 0.35-0.48, kappa-hat 0.1, k 0.2,
@@ -644,17 +663,8 @@ def coexistence_curve_case(s, n=16, ny=1536, tol=1e-3, every=500, window=16,
 
     def run(step, sample, idx):
         """Steps until the windowed means of every listed slab are within tol."""
-        hist, t = [], 0
-        while t < max_steps:
-            hist.append([sample(i) for i in idx])
-            if len(hist) >= window:
-                m = np.mean(np.array(hist[-window:]), axis=0)  # [slab][gas, liq]
-                if all(abs(m[j][0] / G[i] - 1) <= tol and abs(m[j][1] / L[i] - 1) <= tol
-                       for j, i in enumerate(idx)):
-                    return t, m
-            step(every)
-            t += every
-        return None, np.mean(np.array(hist[-window:]), axis=0)
+        return windowed_equilibrium(step, lambda: [sample(i) for i in idx],
+                                    [(G[i], L[i]) for i in idx], tol, every, window, max_steps)
     t0 = time.perf_counter()
     plain_steps = []
     for i, t in enumerate(T):

@@ -61,3 +61,41 @@ def test_phase_mismatch_of_a_shifted_disk():
     bad, _ = bench.phase_mismatch(a, b, 0.5)
     assert bad == pytest.approx(4 * R, rel=0.15)  # two half-perimeters' worth of columns
     assert math.isfinite(bad / links)
+
+
+class _Oscillating:
+    """Bulk densities relaxing to their targets with a superposed acoustic
+    oscillation larger than the tolerance: g(t) = G (1 + a e^{-t/T} + b sin(w t))."""
+
+    def __init__(self, targets, a=0.05, T=20_000.0, b=3e-3, period=3000.0):
+        self.t, self.targets = 0, targets
+        self.a, self.T, self.b, self.w = a, T, b, 2 * math.pi / period
+
+    def step(self, n):
+        self.t += n
+
+    def sample(self):
+        f = 1 + self.a * math.exp(-self.t / self.T) + self.b * math.sin(self.w * self.t)
+        return [(g * f, l * f) for g, l in self.targets]
+
+
+def test_windowed_equilibrium_filters_the_oscillation():
+    targets = [(1e-3, 0.45), (2e-4, 0.5)]
+    # the window (16 samples, 500 steps apart) spans 8000 steps, several periods
+    sysm = _Oscillating(targets)
+    steps, m = bench.windowed_equilibrium(sysm.step, sysm.sample, targets, 1e-3, 500, 16,
+                                          300_000)
+    assert steps is not None
+    # the decaying part alone falls below 1e-3 at t = T ln(50) = 78 240
+    assert 70_000 <= steps <= 100_000, steps
+    assert np.all(np.abs(m / np.array(targets) - 1) <= 1e-3)
+    # single samples alias: they stop where a sample happens to fall near a zero
+    # of the oscillation while the underlying deviation is still above tolerance
+    one = _Oscillating(targets)
+    s1, _ = bench.windowed_equilibrium(one.step, one.sample, targets, 1e-3, 500, 1, 300_000)
+    assert s1 is not None and s1 < steps
+    assert 0.05 * math.exp(-s1 / 20_000.0) > 1e-3
+    # not reached within max_steps
+    short = _Oscillating(targets)
+    s2, m2 = bench.windowed_equilibrium(short.step, short.sample, targets, 1e-3, 500, 16, 40_000)
+    assert s2 is None and m2.shape == (2, 2)
