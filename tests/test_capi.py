@@ -333,3 +333,18 @@ def test_struct_layouts_match_the_header():
         assert got[(cname, "size")] == C.sizeof(py), cname
         for field, _ in py._fields_:
             assert got[(cname, field)] == getattr(py, field).offset, (cname, field)
+
+
+def test_workspace_bytes_beyond_two_to_the_31_nodes():
+    """A 46 341 x 46 341 grid has more than 2^31 nodes (about 233 GB of mixed
+    workspace, within a GB300's memory): the size is computed without
+    overflow: mixed, two FP32 population buffers and eight FP32 planes (104
+    bytes per node); FP64, two FP64 population buffers and seven FP64 planes
+    (200 bytes per node); plus alignment."""
+    n = 46_341
+    assert n * n > 2 ** 31
+    g = B.LbmGrid(n, n, 1, 1)
+    for prec, per_node in ((B.LBM_PREC_MIXED, 104), (B.LBM_PREC_FP64, 200)):
+        o = B._opts(prec, 6, math.inf, 0, "bgk", None)
+        ws = P.lib().lbm_workspace_bytes(C.byref(g), C.byref(o))
+        assert ws == pytest.approx(per_node * n * n, rel=1e-6), (prec, ws)
