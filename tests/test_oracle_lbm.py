@@ -12,7 +12,10 @@
   * a shear wave decays at the BGK viscosity nu = c_s^2 (tau - 1/2) (Sec. 2);
   * mass is conserved to rounding by collision + periodic streaming;
   * the force stage reduces to F = (c_s^2 - k^2 R T) grad(rho) for an ideal-gas
-    limit and its sign drives phase separation.
+    limit and its sign drives phase separation;
+  * where the upper limit caps mu-hat at every node, grad(mu-hat) = 0 and the
+    force is exactly c_s^2 D rho: for one Fourier mode of rho, c_s^2 theta(w)
+    times its derivative mode (Sec. 5.6 with Eqs. 12, 37-39).
 """
 import math
 
@@ -144,3 +147,20 @@ def test_mu_cap_limits_and_keeps_mass():
     assert abs(capped.f.sum() - m0) / m0 < 1e-13
     mu_late, _, _ = capped.force_stage(capped.fields()[0], t=capped.t)
     assert mu_late.max() > 0.25 * mu_max  # inactive after n_cap
+
+
+def test_force_where_the_limit_caps_every_node():
+    from oracle import cfd_alpha
+    n, k, order = 48, 0.5, 6
+    T = 0.6 * TC
+    y = np.arange(n)[:, None] * np.ones((1, 4))
+    w = 2 * np.pi * 3 / n
+    rho = 0.45 + 0.02 * np.sin(w * y)  # dense liquid: mu0 far above the limit below
+    sim = OracleSim(4, n, T, 0.1, 1.0, k, order, mu_max=-5.0, mu_cap_steps=10)
+    mu, Fx, Fy = sim.force_stage(rho, t=0)
+    assert np.all(mu == k * k * -5.0)
+    a = cfd_alpha(order)
+    A, B = 2.0 / 3.0 * (a + 2.0), (4.0 * a - 1.0) / 3.0
+    theta = (A * np.sin(w) + B / 2 * np.sin(2 * w)) / (1 + 2 * a * np.cos(w))
+    assert np.abs(Fy - 0.02 * theta * np.cos(w * y) / 3).max() <= 1e-15
+    assert np.all(Fx == 0.0)
