@@ -246,6 +246,8 @@ class Simulation:
                  walls_y=False, wall_ux=(0.0, 0.0)):
         """`walls_y`: solid walls below the first and above the last row (else
         periodic in y); `wall_ux`: their x-velocities (bottom, top)."""
+        if not walls_y and any(wall_ux):
+            raise ValueError("wall_ux needs walls_y: a periodic grid has no walls to move")
         import torch
         self.nx, self.ny = nx, ny
         self.device = torch.device(device if device is not None else "cuda")

@@ -348,3 +348,8 @@ def test_workspace_bytes_beyond_two_to_the_31_nodes():
         o = B._opts(prec, 6, math.inf, 0, "bgk", None)
         ws = P.lib().lbm_workspace_bytes(C.byref(g), C.byref(o))
         assert ws == pytest.approx(per_node * n * n, rel=1e-6), (prec, ws)
+
+
+def test_wall_velocity_without_walls_is_refused_before_any_device_work():
+    with pytest.raises(ValueError, match="walls_y"):
+        P.Simulation(16, 16, 0.6, 0.1, 1.0, 0.5, wall_ux=(0.05, 0.0))
