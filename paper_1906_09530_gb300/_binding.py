@@ -365,8 +365,10 @@ class Batch:
     (lbm_batch_* of the C ABI): one launch per pass for the whole batch.
 
     `instances` is a sequence of dicts with keys nx, ny, T_r, and optionally
-    kappa (0.1), tau (1.0), k (0.5), mu_max (inf), mu_cap_steps (0).
-    `precision` is "mixed" or "mixed_df", as for Simulation.
+    kappa (0.1), tau (1.0), k (0.5), mu_max (inf), mu_cap_steps (0); other keys
+    (a caller's own bookkeeping) are ignored, except that walls are refused:
+    batches are periodic only.  `precision` is "mixed" or "mixed_df", as for
+    Simulation.
     """
 
     def __init__(self, instances, fd_order=6, precision="mixed", eos=None, device=None,
@@ -376,6 +378,8 @@ class Batch:
         arr = (LbmInstance * self.n)()
         self.shapes = []
         for i, d in enumerate(instances):
+            if d.get("walls_y") or any(d.get("wall_ux", ())):
+                raise ValueError(f"instance {i}: batches are periodic only (no walls)")
             arr[i] = LbmInstance(LbmGrid(d["nx"], d["ny"], 1, 1), d["T_r"],
                                  d.get("kappa", 0.1), d.get("tau", 1.0), d.get("k", 0.5),
                                  d.get("mu_max", math.inf), d.get("mu_cap_steps", 0))

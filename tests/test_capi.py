@@ -353,3 +353,8 @@ def test_workspace_bytes_beyond_two_to_the_31_nodes():
 def test_wall_velocity_without_walls_is_refused_before_any_device_work():
     with pytest.raises(ValueError, match="walls_y"):
         P.Simulation(16, 16, 0.6, 0.1, 1.0, 0.5, wall_ux=(0.05, 0.0))
+
+
+def test_batch_refuses_walls_before_any_device_work():
+    with pytest.raises(ValueError, match="periodic only"):
+        P.Batch([dict(nx=16, ny=16, T_r=0.6), dict(nx=16, ny=16, T_r=0.6, walls_y=True)])
