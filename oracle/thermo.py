@@ -128,7 +128,11 @@ def flat_gradient(rho, T, rho_b, kappa, k, a=A_CS, b=B_CS, R=R_CS):
 
 def flat_profile_y(rho_values, T_r, kappa, k, a=A_CS, b=B_CS, R=R_CS):
     """Mesh-space coordinate y(rho) of the flat interface, Eq. 23, with the origin
-    at rho = (rho_g + rho_l)/2 and y increasing towards the liquid."""
+    at rho = (rho_g + rho_l)/2 and y increasing towards the liquid.  This is the
+    continuum profile for the given kappa; the lattice scheme's own equilibrium
+    has kappa + c_s^4/(4 rho) in its place (the exact-difference forcing's
+    momentum flux at rest), which tests/test_oracle_physics.py derives and
+    checks."""
     Tc, _ = critical_point(a, b, R)
     T = T_r * Tc
     rg, rl = maxwell(T_r, a, b, R)
@@ -146,7 +150,9 @@ def flat_profile_y(rho_values, T_r, kappa, k, a=A_CS, b=B_CS, R=R_CS):
 def sigma_flat(T_r, kappa, k, a=A_CS, b=B_CS, R=R_CS):
     """Mesh-space surface tension of the flat interface: the integral of
     P_N - P_T = kappa (d rho/dy)^2 across the interface (Eq. 10), which by
-    Eq. 24 becomes the integral of sqrt(2 kappa k^2 Omega(rho)) d rho."""
+    Eq. 24 becomes the integral of sqrt(2 kappa k^2 Omega(rho)) d rho.  The
+    tension the lattice scheme realises has kappa + c_s^4/(4 rho) in place of
+    kappa inside the root; tests/test_oracle_physics.py integrates that form."""
     Tc, _ = critical_point(a, b, R)
     T = T_r * Tc
     rg, rl = maxwell(T_r, a, b, R)
