@@ -7,7 +7,11 @@ p_xy), S = diag(0, s_e, s_eps, 0, s_q, 0, s_q, s_v, s_v), s_v = 1/tau.
   * with every rate equal to 1/tau the MRT collision is the BGK collision of
     Eq. 1 (S = I/tau and M^-1 M = I);
   * mass is conserved to rounding (the rates of rho and j are 0);
-  * a shear wave decays at nu = (1/s_v - 1/2)/3, whatever s_e, s_eps and s_q are.
+  * a shear wave decays at nu = (1/s_v - 1/2)/3, whatever s_e, s_eps and s_q are;
+  * a sound wave decays at Gamma = q^2 (nu + zeta)/2 with the bulk viscosity
+    zeta = (1/s_e - 1/2)/3, set by the energy mode's rate alone: changing s_eps
+    or s_q leaves it unchanged, so s_e sits on the row of e (a swap with s_eps
+    fails).
 """
 import math
 
@@ -74,3 +78,33 @@ def test_shear_wave_viscosity(rates):
     amp = 2 * np.mean(vx[:, 0] * np.sin(2 * np.pi * y / n))
     nu = -math.log(amp / U) / ((2 * math.pi / n) ** 2 * 400)
     assert nu == pytest.approx((tau - 0.5) / 3, rel=5e-3)
+
+
+def _sound_damping(rates, n=64, steps=1500):
+    """Decay rate of the envelope of a small standing sound wave (nearly ideal
+    fluid: T = 1.5 T_c, kappa-hat ~ 0, k = 1), from its peaks."""
+    o = OracleSim(n, 4, 1.5 * TC, 1e-30, 1.0, 1.0, 6, mrt=rates)
+    x = np.arange(n)[None, :] * np.ones((4, 1))
+    o.set_fields(0.2 * (1 + 1e-4 * np.cos(2 * np.pi * x / n)))
+    c = np.cos(2 * np.pi * np.arange(n) / n)
+    amp = []
+    for _ in range(steps // 5):
+        o.step(5)
+        r = o.fields()[0][0]
+        amp.append(abs((r - r.mean()) @ c) / (n / 2))
+    amp, t = np.array(amp), 5.0 * np.arange(1, len(amp) + 1)
+    pk = [i for i in range(1, len(amp) - 1) if amp[i] >= amp[i - 1] and amp[i] >= amp[i + 1]]
+    return -np.polyfit(t[pk], np.log(amp[pk]), 1)[0], (2 * np.pi / n) ** 2
+
+
+def test_sound_wave_bulk_viscosity():
+    nu = (1.0 - 0.5) / 3  # tau = 1
+    g = {}
+    for name, rates in (("paper", (1.64, 1.54, 1.9)), ("se1", (1.0, 1.54, 1.9)),
+                        ("seps", (1.64, 1.0, 1.9)), ("sq", (1.64, 1.54, 1.2))):
+        g[name], q2 = _sound_damping(rates)
+    for name, se in (("paper", 1.64), ("se1", 1.0)):
+        zeta = 2 * g[name] / q2 - nu
+        assert zeta == pytest.approx((1 / se - 0.5) / 3, rel=0.02), (name, zeta)
+    assert g["seps"] == pytest.approx(g["paper"], rel=1e-3)
+    assert g["sq"] == pytest.approx(g["paper"], rel=1e-3)
