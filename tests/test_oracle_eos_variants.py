@@ -153,3 +153,16 @@ def test_upper_limit_replaces_mu_at_the_pole(kind):
     free = OracleSim(16, 12, 0.6 * tc, kappa, 1.0, k, 6, eos=e)
     mu, _, _ = free.force_stage(rho, t=0)
     assert mu[5, 7] == np.inf and mu[6, 7] == np.inf
+
+
+def test_pr_and_rks_density_ratio_at_tr_0_4_exceeds_the_printed_bound():
+    """Sec. 5.4 (Fig. 9b): at T_r 0.4 the PR and RKS density ratios exceed
+    65,000 (tests/golden/paper_constants.json).  The Maxwell pairs give
+    6.8e5 and 7.5e5."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                       "paper_constants.json")))["pr_rks_ratio_at_tr_0_4"]
+    for kind in ("pr", "rks"):
+        g, l = E.Eos(kind, omega=gold["omega"]).maxwell(gold["T_r"])
+        assert l / g > gold["value"], (kind, l / g)
