@@ -3,10 +3,12 @@
 // library's device image, so that the call itself allocates nothing.
 //
 // Callers that cannot call cudaMalloc (code running under an allocator that
-// owns all device memory, inside a CUDA-graph-only runtime, or a host
-// environment whose policy forbids device allocations after start-up) can still
-// take the run's diagnostics: they pass the context (whose workspace they
-// obtained from their own pool) and host outputs, and nothing is allocated here.
+// owns all device memory, or a host environment whose policy forbids device
+// allocations after start-up) can still take the run's diagnostics: they pass
+// the context (whose workspace they obtained from their own pool) and host
+// outputs, and nothing is allocated here.  Like lbm_diag, the call copies its
+// four results to the host and waits for the context's stream before it
+// returns.
 //
 // The array g_diag_partials is a file-scope __device__ variable: every GPU that
 // loads the library holds its 512 KB until the process exits.  In host code its

@@ -258,7 +258,10 @@ def test_spurious_current_grows_as_temperature_falls():
         o.set_fields(W.drop(n, n, rg, rl, 16.0, 4.0 / k))
         o.step(2000)
         vmax.append(np.hypot(*o.fields()[1:3]).max())
-    assert vmax[0] * 2 < vmax[1] and vmax[1] * 2 < vmax[2] < 1e-3, vmax
+    # measured 6.8e-5, 2.7e-4, 9.7e-4: the claim is the growth, each at least
+    # twice the one above it; the bound only keeps the level in the regime of
+    # Sec. 5.4, with room for step-count and rounding changes
+    assert vmax[0] * 2 < vmax[1] and vmax[1] * 2 < vmax[2] < 2e-3, vmax
 
 
 def test_galilean_translation():
