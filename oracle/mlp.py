@@ -13,6 +13,13 @@ p -= lr (m / (1 - b1^s)) / (sqrt(v / (1 - b2^s)) + eps) at step s.
 
 Parameters travel as one flat float vector in the order W1, b1, W2, b2, W3,
 b3, W4, b4, each W row-major [fan_in][fan_out].
+
+forward_rounded / loss_and_grad_rounded are the same chain rule with the
+operands of every matrix product rounded first (to BF16 by default: 8
+significant bits, round to nearest, ties to even), the products and everything
+else still in FP64.  They define what a network whose products take BF16
+operands computes, up to the accumulation and activation rounding of its own
+arithmetic, so that such a network can be compared with it entry by entry.
 """
 import numpy as np
 
@@ -47,35 +54,64 @@ def init_params(seed):
     return np.concatenate(parts)
 
 
-def forward(p, x):
-    """Outputs y [B, 256] and the activations of every layer (for backward)."""
+def bf16(x):
+    """x rounded to the nearest BF16 value (8 significant bits), ties to even,
+    exactly from FP64 (no intermediate FP32 rounding).  Zero stays zero."""
+    x = np.asarray(x, dtype=np.float64)
+    m, e = np.frexp(x)  # x = m 2^e, 0.5 <= |m| < 1
+    return np.ldexp(np.rint(np.ldexp(m, 8)), e - 8)
+
+
+def _identity(x):
+    return np.asarray(x, dtype=np.float64)
+
+
+def forward(p, x, rnd=_identity):
+    """Outputs y [B, 256] and the activations of every layer (for backward).
+    rnd is applied to both operands of every product (identity: plain FP64)."""
     acts = [np.asarray(x, dtype=np.float64)]
     layers = unpack(np.asarray(p, dtype=np.float64))
     for l, (W, b) in enumerate(layers):
-        z = acts[-1] @ W + b
+        z = rnd(acts[-1]) @ rnd(W) + b
         acts.append(np.tanh(z) if l < N_LAYERS - 1 else z)
     return acts[-1], acts
 
 
-def loss_and_grad(p, x, t):
+def forward_rounded(p, x, rnd=bf16):
+    """forward() with the operands of each product rounded by rnd."""
+    return forward(p, x, rnd)
+
+
+def loss_and_grad(p, x, t, rnd=_identity, parts=False):
     """Mean-squared-error loss and its gradient with respect to every parameter
-    (flat, the order of the parameter vector), by the chain rule."""
+    (flat, the order of the parameter vector), by the chain rule.  rnd is applied
+    to both operands of every product, forward and backward (identity: plain
+    FP64); the bias gradients sum the unrounded signal.  With parts=True also
+    returns y, the activations and the backward signal entering each layer."""
     p = np.asarray(p, dtype=np.float64)
-    y, acts = forward(p, x)
+    y, acts = forward(p, x, rnd)
     B = y.shape[0]
     diff = y - t
     loss = float(np.sum(diff * diff) / (B * y.shape[1]))
     layers = unpack(p)
     grads = [None] * N_LAYERS
+    signals = [None] * N_LAYERS
     d = 2.0 * diff / (B * y.shape[1])  # dL/dy
     for l in range(N_LAYERS - 1, -1, -1):
         W, _ = layers[l]
-        if l < N_LAYERS - 1:
-            d = d * (1.0 - acts[l + 1] ** 2)  # through tanh
-        grads[l] = (acts[l].T @ d, d.sum(axis=0))
-        d = d @ W.T
+        signals[l] = d  # dL/dz of layer l
+        grads[l] = (rnd(acts[l]).T @ rnd(d), d.sum(axis=0))
+        if l > 0:
+            d = (rnd(d) @ rnd(W).T) * (1.0 - acts[l] ** 2)  # through the tanh of layer l-1
     g = np.concatenate([np.concatenate([gw.ravel(), gb]) for gw, gb in grads])
+    if parts:
+        return loss, g, y, acts, signals
     return loss, g
+
+
+def loss_and_grad_rounded(p, x, t, rnd=bf16, parts=False):
+    """loss_and_grad() with the operands of each product rounded by rnd."""
+    return loss_and_grad(p, x, t, rnd, parts)
 
 
 def adam(p, g, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8):

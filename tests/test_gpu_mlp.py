@@ -7,6 +7,16 @@ significant bits, unit 2^-8 = 3.9e-3) with FP32 accumulation over K <= 256 terms
 whose rounding errors add up like a random walk, through four layers.  Relative
 L2 errors of about 1e-2 are expected, and the bounds are 2e-2 (outputs) and 5e-2
 (each layer's gradient), with the gradient's direction within 0.1% (cosine).
+
+Entry by entry the kernels are compared with the oracle's rounded network
+(oracle.mlp.loss_and_grad_rounded), which takes the same BF16 operands in every
+product.  What separates the two is FP32 accumulation and activation rounding,
+and the rare BF16 rounding that lands on the other side of a tie because the
+activation or signal feeding it differs in its last FP32 bits.  Each entry's
+bound is c times its BF16 scale: one BF16 unit (2^-8) on each of the K terms of
+its product, added in quadrature, plus the scale of the signal it was built
+from.  A CPU stand-in of the same arithmetic stays below 2.0 of the scale; a
+single weight off by 0.02 gives 5 to 60.  c = 4.
 """
 import numpy as np
 import pytest
@@ -33,6 +43,32 @@ def _setup(cuda, B, seed=4):
     return net, p, x, t, torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
 
 
+U8 = 2.0 ** -8
+C_BOUND = 4.0
+
+
+def _scales(p, x, t):
+    """The rounded network's outputs and gradient with each entry's BF16 scale."""
+    p = np.asarray(p, np.float64)
+    layers = O.unpack(p)
+    _, g, y, acts, sig = O.loss_and_grad_rounded(p, x, t, parts=True)
+    W4 = O.bf16(layers[-1][0])
+    sy = U8 * np.sqrt((O.bf16(acts[-2]) ** 2) @ (W4 ** 2))
+    B, N = y.shape
+    sd = 2.0 / (B * N) * sy  # scale of dL/dy
+    out = [None] * O.N_LAYERS
+    for l in range(O.N_LAYERS - 1, -1, -1):
+        qa, qd = O.bf16(acts[l]), O.bf16(sig[l])
+        sW = U8 * np.sqrt((qa ** 2).T @ (qd ** 2)) + np.sqrt((qa ** 2).T @ (sd ** 2))
+        out[l] = (sW, np.sqrt((sd ** 2).sum(0)))
+        if l > 0:
+            qW = O.bf16(layers[l][0])
+            sd = (U8 * np.sqrt((qd ** 2) @ (qW.T ** 2)) + np.sqrt((sd ** 2) @ (qW.T ** 2))) \
+                * np.abs(1 - acts[l] ** 2)
+    sg = np.concatenate([np.concatenate([a.ravel(), b]) for a, b in out])
+    return y, sy, g, sg
+
+
 def test_params_round_trip(cuda):
     net, p, *_ = _setup(cuda, 8)
     assert np.array_equal(net.get_params(), p)
@@ -45,6 +81,32 @@ def test_forward_matches_oracle(cuda, B):
     y = net.forward(dx).cpu().numpy()
     y_ref, _ = O.forward(p.astype(np.float64), x.astype(np.float64))
     assert _rel(y, y_ref) <= 2e-2
+
+
+@pytest.mark.parametrize("B", [1, 37, 300])
+def test_forward_entrywise(cuda, B):
+    """Every output entry within C_BOUND BF16 scales of the rounded oracle."""
+    net, p, x, t, dx, dt = _setup(cuda, B)
+    y = net.forward(dx).cpu().numpy().astype(np.float64)
+    y_ref, s, _, _ = _scales(p, x.astype(np.float64), t.astype(np.float64))
+    ratio = np.abs(y - y_ref) / s
+    assert ratio.max() <= C_BOUND, (ratio.max(), np.unravel_index(ratio.argmax(), ratio.shape))
+
+
+def test_gradient_entrywise(cuda):
+    """Every gradient entry, weights and biases of all four layers, within
+    C_BOUND BF16 scales of the rounded oracle's chain rule."""
+    net, p, x, t, dx, dt = _setup(cuda, 200)
+    _, g = net.loss_grad(dx, dt)
+    g = g.cpu().numpy().astype(np.float64)
+    _, _, g_ref, sg = _scales(p, x.astype(np.float64), t.astype(np.float64))
+    ratio = np.abs(g - g_ref) / (sg + 1e-300)
+    o = 0
+    for l, (a, b) in enumerate(zip(O.SIZES[:-1], O.SIZES[1:])):
+        for what, n in (("W", a * b), ("b", b)):
+            r = ratio[o:o + n]
+            assert r.max() <= C_BOUND, (l, what, r.max(), int(r.argmax()))
+            o += n
 
 
 def test_loss_and_gradient_match_oracle(cuda):
