@@ -135,7 +135,7 @@ lbm_status enqueue_force(lbm_ctx* c, cudaStream_t s, int bump, cudaEvent_t* ev =
         CK(launch_mu_mixed(c->m_rh, c->m_dxx, c->m_dyy, nx, ny, c->phys, c->dst, s));
         CK(mark(1));
         CK(lines_mixed_force_xy(c->m_dxx, c->m_rh, c->m_dxr, c->m_dyr, c->m_Fx, c->m_Fy, nx, ny,
-                                o, s, c->walls_y));
+                                o, s, c->walls_y, c->dst));
         CK(mark(2));
         CK(mark(3));
         return LBM_OK;
@@ -228,7 +228,7 @@ lbm_status read_state(lbm_ctx* c) {
     if (c->hst->flag) {
         c->failed = c->hst->failed_t == ULLONG_MAX ? c->t : (int64_t)c->hst->failed_t;
         c->ready = false;
-        return LBM_EUNSTABLE;
+        return (c->hst->flag & FLAG_STAGE) ? LBM_ETIMEOUT : LBM_EUNSTABLE;
     }
     return LBM_OK;
 }

@@ -23,6 +23,8 @@ enum : unsigned int {
     FLAG_RHO = 1u,   // collide-stream: rho <= 0 or not finite
     FLAG_EOS = 2u,   // EOS pass: rho <= 0, the EOS pole with the upper limit off,
                      // or mu not finite
+    FLAG_STAGE = 4u, // a line window's tensor copy did not arrive within the
+                     // bounded wait (the block gave up; the step is void)
 };
 
 // Physical parameters the kernels need.
@@ -236,7 +238,8 @@ cudaError_t lines_mixed_rho_xy_f32(const float* rh, float* dxr, float* dxx, floa
                                    cudaStream_t s, bool walls_y = false);
 cudaError_t lines_mixed_force_xy(const float* mu, const float* rh, const float* dxr,
                                  const float* dyr, float* Fx, float* Fy, int nx, int ny,
-                                 int order, cudaStream_t s, bool walls_y = false);
+                                 int order, cudaStream_t s, bool walls_y = false,
+                                 DevState* st = nullptr);
 // mu-hat = k^2 mu0(rho) - kappa (d_xx + d_yy) rho (Eqs. 21, 33, Sec. 5.6), FP32,
 // written over d_xx rho (`dxx_mu`); flags bad values.
 cudaError_t launch_mu_mixed(const float* rh, float* dxx_mu, const float* dyy, int nx, int ny,

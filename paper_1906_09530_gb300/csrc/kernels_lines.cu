@@ -29,9 +29,12 @@
 // Arithmetic policies: PolD (FP64), PolF (FP32), PolDF (double-float pairs).
 // The mixed path uses PolDF for the first derivative of the density and PolF for
 // everything else (see kernels_mixed.cu for why).
+#include <cuda.h>  // CUtensorMap and its encoder's types (the encoder is fetched at run time)
+
 #include <cfloat>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <type_traits>
 
 #include "cplbm_internal.cuh"
@@ -133,6 +136,7 @@ constexpr int kNL = 8;         // lines (warps) per block
 constexpr int kLW = 644;
 constexpr int kSO = kLW;
 static_assert(kLW >= kW + 8 && kLW % 32 == 4, "strides");
+static_assert((kW + 8) % 88 == 0, "y-line windows split into whole tensor-copy boxes");
 
 template <class P>
 struct LineConst {
@@ -172,6 +176,55 @@ __device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
 }
 __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+// ---- tensor-memory-access (TMA) staging of y-line windows -------------------
+// A y-line window of 8 adjacent columns is 8 floats (32 bytes) of each of kRows
+// consecutive rows: one 2-D tensor copy box of 8 x kBoxRows elements per piece,
+// kRows / kBoxRows pieces, all issued by one thread and completed on one
+// mbarrier.  The wait is bounded: a window that never arrives raises
+// FLAG_STAGE and the block gives up instead of spinning forever.
+constexpr int kBoxRows = 88;
+constexpr unsigned kWaitSpins = 1u << 22;  // ~ tens of milliseconds of polling
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// bounded wait for phase `parity` of the barrier; false when it gave up
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+    for (unsigned i = 0; i < kWaitSpins; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void tma_load_2d(void* sdst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];\n" ::"r"(smem_u32(sdst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
 }
 
 // Input fields: stage(t, i, ps, o) copies the element at global offset o into
@@ -392,16 +445,176 @@ __device__ __forceinline__ void solve_window(const typename P1::S* tin, typename
     }
 }
 
+// y-lines of FP32 fields, window staged row by row: slot r of the window
+// (position r - 4) holds the 8 columns of one grid row, tin[r * 8 + line].  A
+// lane owns chunk c = 4 warp + lane / 8 (kC positions from q0 = c kC) of line
+// lane % 8, so a warp reads 4 chunks x 8 lines of one row offset per access,
+// 32 distinct banks (kC 8 = 24 mod 32).  The chunks of a line sit in different
+// warps, so their boundary states are joined through shared memory: the state
+// entering chunk c is E_{c-1} + m E_{c-2} + m^2 E_{c-3} (m = (-lam)^kC), the
+// same three terms the shuffle scan of solve_window keeps.  Results go to
+// tout1 / tout2 in the same row layout, position q at [q * 8 + line].
+template <bool SIXTH, bool SECOND>
+__device__ __forceinline__ void solve_window_y(const float* tin, float* tout1, float* tout2,
+                                               const LineConst<PolF>& kq,
+                                               const LineConst<PolF>& k2) {
+    __shared__ float xa[32][kNL], xb[32][kNL], xc[32][kNL];  // forward states
+    __shared__ float ya[32][kNL], yb[32][kNL], yc[32][kNL];  // backward states
+    const int tid = threadIdx.x;
+    const int w = tid >> 5, lane = tid & 31;
+    const int l = lane & 7, c = 4 * w + (lane >> 3);
+    const int q0 = c * kC;
+    auto tl = [&](int q) { return tin[(q + 4) * kNL + l]; };  // q in [-4, kW+4)
+
+    float r[kC];
+    {
+        float u[kC + 4];
+#pragma unroll
+        for (int k = 0; k < kC + 4; ++k) u[k] = tl(q0 - 2 + k);
+#pragma unroll
+        for (int j = 0; j < kC; ++j) {
+            float b = (u[j + 3] - u[j + 1]) * kq.c1;
+            if (SIXTH) b = fmaf(u[j + 4] - u[j], kq.c2, b);
+            r[j] = b;
+        }
+    }
+    float r2[kC];
+    if (SECOND) {
+        float bx[kC + 4];
+#pragma unroll
+        for (int k = 0; k < kC + 4; ++k) {
+            if (k >= 2 && k < kC + 2) {
+                bx[k] = r[k - 2];
+            } else {
+                const int qc = q0 - 2 + k;
+                float t = (tl(qc + 1) - tl(qc - 1)) * k2.c1;
+                if (SIXTH) t = fmaf(tl(qc + 2) - tl(qc - 2), k2.c2, t);
+                bx[k] = t;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kC; ++j) {
+            float t = (bx[j + 3] - bx[j + 1]) * k2.c1;
+            if (SIXTH) t = fmaf(bx[j + 4] - bx[j], k2.c2, t);
+            r2[j] = t;
+        }
+    }
+    // forward recursions over the chunk from a zero state
+    float wv = 0.0f;
+#pragma unroll
+    for (int j = 0; j < kC; ++j) {
+        wv = fmaf(wv, kq.nlam, r[j]);
+        r[j] = wv;
+    }
+    float vv = 0.0f, ww = 0.0f;
+    if (SECOND) {
+#pragma unroll
+        for (int j = 0; j < kC; ++j) {
+            vv = fmaf(vv, k2.nlam, r2[j]);
+            ww = fmaf(ww, k2.nlam, vv);
+            r2[j] = ww;
+        }
+    }
+    xa[c][l] = wv;
+    if (SECOND) {
+        xb[c][l] = vv;
+        xc[c][l] = ww;
+    }
+    __syncthreads();  // also: every staged value this block reads has been read
+    {
+        float cf = 0.0f;
+        if (c >= 1) cf = xa[c - 1][l];
+        if (c >= 2) cf = fmaf(xa[c - 2][l], kq.m1, cf);
+        if (c >= 3) cf = fmaf(xa[c - 3][l], kq.m2, cf);
+#pragma unroll
+        for (int j = 0; j < kC; ++j) r[j] = fmaf(cf, kq.pw[j], r[j]);
+    }
+    if (SECOND) {
+        float cv = 0.0f, cw = 0.0f;
+        if (c >= 1) {
+            cv = xb[c - 1][l];
+            cw = xc[c - 1][l];
+        }
+        if (c >= 2) {
+            cw = cw + k2.m1 * xc[c - 2][l] + k2.Cm1 * xb[c - 2][l];
+            cv = cv + k2.m1 * xb[c - 2][l];
+        }
+        if (c >= 3) {
+            cw = cw + k2.m2 * xc[c - 3][l] + k2.Cm2 * xb[c - 3][l];
+            cv = cv + k2.m2 * xb[c - 3][l];
+        }
+#pragma unroll
+        for (int j = 0; j < kC; ++j) r2[j] = r2[j] + k2.pw[j] * ((float)(j + 1) * cv + cw);
+    }
+    // backward recursions over the chunk from a zero state
+    float zv = 0.0f;
+#pragma unroll
+    for (int j = kC - 1; j >= 0; --j) {
+        zv = fmaf(zv, kq.nlam, r[j]);
+        r[j] = zv;
+    }
+    float yv = 0.0f, zz = 0.0f;
+    if (SECOND) {
+#pragma unroll
+        for (int j = kC - 1; j >= 0; --j) {
+            yv = fmaf(yv, k2.nlam, r2[j]);
+            zz = fmaf(zz, k2.nlam, yv);
+            r2[j] = zz;
+        }
+    }
+    ya[c][l] = zv;
+    if (SECOND) {
+        yb[c][l] = yv;
+        yc[c][l] = zz;
+    }
+    __syncthreads();
+    {
+        float cb = 0.0f;
+        if (c <= 30) cb = ya[c + 1][l];
+        if (c <= 29) cb = fmaf(ya[c + 2][l], kq.m1, cb);
+        if (c <= 28) cb = fmaf(ya[c + 3][l], kq.m2, cb);
+#pragma unroll
+        for (int j = 0; j < kC; ++j) r[j] = fmaf(cb, kq.pw[kC - 1 - j], r[j]);
+    }
+    if (SECOND) {
+        float cy = 0.0f, cz = 0.0f;
+        if (c <= 30) {
+            cy = yb[c + 1][l];
+            cz = yc[c + 1][l];
+        }
+        if (c <= 29) {
+            cz = cz + k2.m1 * yc[c + 2][l] + k2.Cm1 * yb[c + 2][l];
+            cy = cy + k2.m1 * yb[c + 2][l];
+        }
+        if (c <= 28) {
+            cz = cz + k2.m2 * yc[c + 3][l] + k2.Cm2 * yb[c + 3][l];
+            cy = cy + k2.m2 * yb[c + 3][l];
+        }
+#pragma unroll
+        for (int j = 0; j < kC; ++j)
+            r2[j] = r2[j] + k2.pw[kC - 1 - j] * ((float)(kC - j) * cy + cz);
+    }
+#pragma unroll
+    for (int j = 0; j < kC; ++j) {
+        tout1[(q0 + j) * kNL + l] = r[j];
+        if (SECOND) tout2[(q0 + j) * kNL + l] = r2[j];
+    }
+}
+
 template <int AXIS, class P1, class P2, bool SIXTH, bool SECOND, class In, class Epi>
 __device__ __forceinline__ void lines_body(In& in, const LineGeo& g, const LineConst<P1>& k1,
                                            const LineConst<PolF>& k1f,
                                            const LineConst<P2>& k2, Epi& epi, DevState* st,
-                                           int bid) {
+                                           int bid, const CUtensorMap* tmap = nullptr) {
+    // FP32 y-lines stage their window row by row ([slot][8 lines]); the rest
+    // stage it line by line ([line][slot])
+    constexpr bool kRowY = AXIS == 1 && std::is_same<P1, PolF>::value &&
+                           std::is_same<P2, PolF>::value;
     using V1 = typename P1::V;
     using V2 = typename P2::V;
     using O1 = typename P1::O;
     using S1 = typename P1::S;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     constexpr int kPS = kNL * kLW;                                   // plane stride
     // the outputs reuse the staged planes: the first derivative plane 0, the
     // second plane 1 (double-float input) or a plane of its own
@@ -422,7 +635,63 @@ __device__ __forceinline__ void lines_body(In& in, const LineGeo& g, const LineC
     constexpr int LWIN = kW + 8;
     const int p0 = wrapi((long long)s - g.H - 4, g.period);  // period position of slot 0
     const bool short_line = g.period < LWIN;
-    if (AXIS == 0 && g.vec) {
+    if constexpr (kRowY) {
+        // row layout: slot q holds columns line0 .. line0 + 7 of period position p0 + q
+        const long long p_end = (long long)s - g.H - 4 + LWIN;  // one past the last slot
+        const bool interior = (long long)s - g.H - 4 >= 0 && p_end <= g.n;
+        if (tmap && st && g.vec && interior && line0 + kNL <= g.nlines &&
+            (smem_u32(tin) & 127u) == 0) {
+            // one elected thread moves the window with tensor copies
+            __shared__ __align__(8) uint64_t bar;
+            if (tid == 0) mbar_init(&bar, 1);
+            __syncthreads();
+            if (tid == 0) {
+                mbar_expect_tx(&bar, (unsigned)(LWIN * kNL * sizeof(float)));
+#pragma unroll 1
+                for (int b = 0; b < LWIN / kBoxRows; ++b)
+                    tma_load_2d(tin + b * kBoxRows * kNL, tmap, line0, p0 + b * kBoxRows, &bar);
+            }
+            const bool arrived = mbar_wait_bounded(&bar, 0);
+            if (__syncthreads_or(!arrived)) {
+                // not arrived in time: flag the run; wait once more (bounded) for
+                // the copies in flight before the block leaves its shared memory
+                if (tid == 0) raise_flag(st, FLAG_STAGE, st->t);
+                mbar_wait_bounded(&bar, 0);
+                return;
+            }
+        } else if (g.vec) {
+            // 16-byte pieces: slot q, half h covers columns line0 + 4h .. + 3
+            for (int idx = tid; idx < 2 * LWIN; idx += kNL * 32) {
+                const int q = idx >> 1, h = idx & 1;
+                const int col = line0 + 4 * h;
+                S1* dst = tin + q * kNL + 4 * h;
+                if (col < g.nlines) {
+                    int p = p0 + q;
+                    if (short_line) p %= g.period;
+                    else if (p >= g.period) p -= g.period;
+                    if (g.mirror && p >= g.n) p = 2 * g.n - 1 - p;
+                    in.stage4(dst, 0, kPS, (size_t)p * g.ps + (size_t)col);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) dst[k] = 0.0f;
+                }
+            }
+        } else {
+            for (int idx = tid; idx < kNL * LWIN; idx += kNL * 32) {
+                const int q = idx >> 3, ll = idx & 7;
+                const int col = line0 + ll;
+                if (col < g.nlines) {
+                    int p = p0 + q;
+                    if (short_line) p %= g.period;
+                    else if (p >= g.period) p -= g.period;
+                    if (g.mirror && p >= g.n) p = 2 * g.n - 1 - p;
+                    in.stage(tin, q * kNL + ll, kPS, (size_t)p * g.ps + (size_t)col);
+                } else {
+                    tin[q * kNL + ll] = 0.0f;
+                }
+            }
+        }
+    } else if (AXIS == 0 && g.vec) {
         // rows: 16-byte chunks (p0, H and own are multiples of 4, and so is the
         // line length, so no chunk straddles the periodic wrap)
         constexpr int CW = LWIN / 4;
@@ -469,7 +738,9 @@ __device__ __forceinline__ void lines_body(In& in, const LineGeo& g, const LineC
     // With all staged densities within a factor 32, FP32 rounding stays below
     // ~2e-6 of the local values, as accurate as the FP32 result that is stored;
     // only windows reaching across an interface need the double-float solve.
-    if constexpr (std::is_same<P1, PolDF>::value) {
+    if constexpr (kRowY) {
+        solve_window_y<SIXTH, SECOND>(tin, tout1, tout2, k1, k2);
+    } else if constexpr (std::is_same<P1, PolDF>::value) {
         __shared__ float red[2][kNL];
         float mn = FLT_MAX, mx = 0.0f;
         for (int idx = tid; idx < kNL * LWIN; idx += kNL * 32) {
@@ -511,6 +782,59 @@ __device__ __forceinline__ void lines_body(In& in, const LineGeo& g, const LineC
     const int nown = e - s;
     const int lmax = min(kNL, g.nlines - line0);
     bool bad = false;
+    if constexpr (kRowY) {
+        // outputs in the row layout: position q of line l at [q * 8 + l]
+        if (g.vec) {
+            // 16-byte pieces: one row, four adjacent lines (columns line0 + 4h ..)
+            const int total = 2 * nown;
+            for (int base = tid; base < total; base += kB * kNL * 32) {
+                int sl[kB];
+                size_t off[kB];
+                typename Epi::Ops4 ops[kB];
+#pragma unroll
+                for (int k = 0; k < kB; ++k) {
+                    const int idx = base + k * kNL * 32;
+                    const int qq = idx >> 1, h4 = 4 * (idx & 1);
+                    sl[k] = (g.H + qq) * kNL + h4;
+                    off[k] = (size_t)(line0 + h4) + (size_t)(s + qq) * g.ps;
+                    if (!(idx < total && h4 < lmax)) sl[k] = -1;
+                    else ops[k] = epi.fetch4(off[k]);
+                }
+#pragma unroll
+                for (int k = 0; k < kB; ++k) {
+                    if (sl[k] < 0) continue;
+                    const float4 a = *reinterpret_cast<const float4*>(tout1 + sl[k]);
+                    float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (SECOND) b = *reinterpret_cast<const float4*>(tout2 + sl[k]);
+                    bad |= epi.put4(off[k], a, b, ops[k]);
+                }
+            }
+        } else {
+            const int total = kNL * nown;
+            for (int base = tid; base < total; base += kB * kNL * 32) {
+                int slot[kB];
+                size_t off[kB];
+                typename Epi::Ops ops[kB];
+#pragma unroll
+                for (int k = 0; k < kB; ++k) {
+                    const int idx = base + k * kNL * 32;
+                    const int qq = idx >> 3, ll = idx & 7;
+                    const bool live = idx < total && ll < lmax;
+                    slot[k] = live ? (g.H + qq) * kNL + ll : -1;
+                    off[k] = (size_t)(line0 + ll) + (size_t)(s + qq) * g.ps;
+                    if (live) ops[k] = epi.fetch(off[k]);
+                }
+#pragma unroll
+                for (int k = 0; k < kB; ++k)
+                    if (slot[k] >= 0)
+                        bad |= epi(off[k], tout1[slot[k]], SECOND ? tout2[slot[k]] : (V2)0,
+                                   ops[k]);
+            }
+        }
+        bad |= in.flagged();
+        if (bad) raise_flag(st, FLAG_EOS, st->t);
+        return;
+    }
     if constexpr (sizeof(O1) == 4 && sizeof(V2) == 4) {
         if (g.vec) {
             // float fields, nx % 4 == 0: chunks of four outputs, 16-byte stores.
@@ -616,7 +940,8 @@ template <class P1, class P2, bool SIXTH, bool SECOND, class InX, class EpiX, cl
           class EpiY>
 __global__ void __launch_bounds__(kNL * 32, SECOND && P1::kPlanes >= 2 ? 3 : 4)
     k_lines_xy(InX inx, LineGeo gx, EpiX ex, InY iny, LineGeo gy, EpiY ey, LineConst<P1> k1,
-               LineConst<PolF> k1f, LineConst<P2> k2, DevState* st, int bump, int nbx) {
+               LineConst<PolF> k1f, LineConst<P2> k2, DevState* st, int bump, int nbx,
+               const __grid_constant__ CUtensorMap tmy, int use_tma) {
     if (bump && blockIdx.x == 0 && threadIdx.x == 0) st->t += 1;
     if ((int)blockIdx.x < nbx) {
         ex.init(st);
@@ -626,7 +951,7 @@ __global__ void __launch_bounds__(kNL * 32, SECOND && P1::kPlanes >= 2 ? 3 : 4)
         ey.init(st);
         iny.init(st);
         lines_body<1, P1, P2, SIXTH, SECOND>(iny, gy, k1, k1f, k2, ey, st,
-                                             (int)blockIdx.x - nbx);
+                                             (int)blockIdx.x - nbx, use_tma ? &tmy : nullptr);
     }
 }
 
@@ -873,6 +1198,48 @@ cudaError_t launch_lines_t(In in, const LineGeo& g, int order, Epi epi, DevState
     return cudaGetLastError();
 }
 
+// Tensor map of an FP32 field [ny][nx] for the y-line windows: boxes of 8
+// columns x kBoxRows rows, no swizzle.  The encoder is the driver's
+// cuTensorMapEncodeTiled, looked up once through the runtime (no link to the
+// driver library); without it, or for fields it cannot describe (nx not a
+// multiple of 4), the windows are staged by cp.async instead.
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn tensor_map_encoder() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+bool y_tensor_map(const float* field, int nx, int ny, CUtensorMap* m) {
+    if (!field || nx % 4 != 0 || nx < kNL || ny < kW + 8) return false;
+    const EncodeTiledFn enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)nx, (cuuint64_t)ny};
+    const cuuint64_t strides[1] = {(cuuint64_t)nx * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)kNL, (cuuint32_t)kBoxRows};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(field), dims, strides,
+               box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
+template <class In>
+const float* y_field(const In&) { return nullptr; }
+const float* y_field(const InF& in) { return in.p; }
+
 template <class P1, class P2, bool SIXTH, bool SECOND, class InX, class EpiX, class InY,
           class EpiY>
 cudaError_t launch_xy_t(InX inx, EpiX ex, InY iny, EpiY ey, int nx, int ny, int order, int H,
@@ -889,9 +1256,16 @@ cudaError_t launch_xy_t(InX inx, EpiX ex, InY iny, EpiY ey, int nx, int ny, int 
     const LineGeo gx = make_geo(nx, ny, 0, H), gy = make_geo(nx, ny, 1, H, walls_y);
     const int nbx = gx.ngroups * gx.nwin;
     const unsigned blocks = (unsigned)(nbx + gy.ngroups * gy.nwin);
+    // FP32 y-lines take their interior windows by tensor copies (a state block
+    // is needed to report a copy that never arrives)
+    CUtensorMap tmy;
+    std::memset(&tmy, 0, sizeof(tmy));
+    int use_tma = 0;
+    if (std::is_same<P1, PolF>::value && std::is_same<P2, PolF>::value && st)
+        use_tma = y_tensor_map(y_field(iny), nx, ny, &tmy) ? 1 : 0;
     kern<<<blocks, kNL * 32, smem, s>>>(inx, gx, ex, iny, gy, ey, make_const<P1>(order),
                                         make_const<PolF>(order), make_const<P2>(order), st, bump,
-                                        nbx);
+                                        nbx, tmy, use_tma);
     return cudaGetLastError();
 }
 
@@ -1003,10 +1377,10 @@ cudaError_t lines_mixed_rho_xy_f32(const float* rh, float* dxr, float* dxx, floa
 }
 cudaError_t lines_mixed_force_xy(const float* mu, const float* rh, const float* dxr,
                                  const float* dyr, float* Fx, float* Fy, int nx, int ny,
-                                 int order, cudaStream_t s, bool walls_y) {
+                                 int order, cudaStream_t s, bool walls_y, DevState* st) {
     return launch_xy<PolF, PolF, false>(InF{mu}, EpiForce<float, float>{Fx, rh, dxr}, InF{mu},
                                         EpiForce<float, float>{Fy, rh, dyr}, nx, ny, order,
-                                        kEpsF, kEpsF, nullptr, 0, s, walls_y);
+                                        kEpsF, kEpsF, st, 0, s, walls_y);
 }
 cudaError_t lines_mixed_plain(const float* uh, const float* ul, float* d1, float* d2, int nx,
                               int ny, int axis, int order, cudaStream_t s) {
