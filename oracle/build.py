@@ -6,7 +6,9 @@ using it; only the tests, the smoke check and the benchmark's CPU-baseline leg
 load the result.
 
 Flags: -O2 without fast-math, and -ffp-contract=off so that no multiply-add is
-fused on either x86 or Arm hosts (the oracle's bits do not depend on the host).
+fused on either x86 or Arm hosts (the oracle's bits do not depend on the host);
+-fopenmp where gcc supports it (the thread count is 1 unless the caller sets it
+with orc_set_threads).
 """
 import os
 import platform
@@ -30,7 +32,11 @@ def build(force: bool = False) -> str:
     tmp = out + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
            "-fno-fast-math", "-Wall", "-Wextra", "-o", tmp, SRC, "-lm"]
-    subprocess.run(cmd, check=True)
+    # with OpenMP when the compiler has it (the loops over lines and nodes are
+    # shared among threads; results do not depend on the thread count)
+    r = subprocess.run(cmd[:1] + ["-fopenmp"] + cmd[1:], capture_output=True, text=True)
+    if r.returncode != 0:
+        subprocess.run(cmd, check=True)
     os.replace(tmp, out)
     return out
 

@@ -28,12 +28,19 @@
  * bounce-back, walls that may move along x (a moving reference frame), and the
  * density and mu-hat extended evenly about the walls for their y-derivatives.
  * The chemical-potential upper limit of Sec. 5.6 also takes the EOS pole.
+ *
+ * Threads: built with OpenMP, the loops over lines and over nodes are shared
+ * among orc_set_threads(n) threads (1 unless set).  Every line and every node is
+ * computed exactly as with one thread, so the results do not depend on n.
  */
 #include <math.h>
 #include <stddef.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* D2Q9 velocity set and weights, Sec. 2 (after Eq. 2). */
 static const int EX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
@@ -185,14 +192,34 @@ int orc_cfd_line(const double *u, ptrdiff_t su, double *d, ptrdiff_t sd, int n,
     return 0;
 }
 
+/* Threads for the loops below (OpenMP builds; ignored otherwise). */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : 1);
+#else
+    (void)n;
+#endif
+}
+
+int orc_get_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
 /* d/dx of a [ny][nx] field: every x-line in turn. */
 static int cfd_x(const orc_params *p, const double *u, double *d)
 {
+    int err = 0;
+#pragma omp parallel for reduction(| : err) schedule(static)
     for (int y = 0; y < p->ny; ++y)
-        if (orc_cfd_line(u + (size_t)y * p->nx, 1, d + (size_t)y * p->nx, 1, p->nx,
-                         p->alpha, 1.0))
-            return -1;
-    return 0;
+        err |= orc_cfd_line(u + (size_t)y * p->nx, 1, d + (size_t)y * p->nx, 1, p->nx,
+                            p->alpha, 1.0) != 0;
+    return err ? -1 : 0;
 }
 
 /* d/dy of a [ny][nx] field: every y-line in turn. */
@@ -204,27 +231,33 @@ static int cfd_x(const orc_params *p, const double *u, double *d)
 static int cfd_y(const orc_params *p, const double *u, double *d)
 {
     int ny = p->ny;
-    if (!p->walls_y) {
-        for (int x = 0; x < p->nx; ++x)
-            if (orc_cfd_line(u + x, p->nx, d + x, p->nx, ny, p->alpha, 1.0))
-                return -1;
-        return 0;
-    }
-    double *line = (double *)malloc(sizeof(double) * 4 * ny);
-    if (!line)
-        return -1;
-    double *dl = line + 2 * ny;
     int err = 0;
-    for (int x = 0; x < p->nx && !err; ++x) {
-        for (int y = 0; y < ny; ++y) {
-            line[y] = u[(size_t)y * p->nx + x];
-            line[2 * ny - 1 - y] = u[(size_t)y * p->nx + x];
-        }
-        err = orc_cfd_line(line, 1, dl, 1, 2 * ny, p->alpha, 1.0);
-        for (int y = 0; y < ny; ++y)
-            d[(size_t)y * p->nx + x] = dl[y];
+    if (!p->walls_y) {
+#pragma omp parallel for reduction(| : err) schedule(static)
+        for (int x = 0; x < p->nx; ++x)
+            err |= orc_cfd_line(u + x, p->nx, d + x, p->nx, ny, p->alpha, 1.0) != 0;
+        return err ? -1 : 0;
     }
-    free(line);
+#pragma omp parallel reduction(| : err)
+    {
+        double *line = (double *)malloc(sizeof(double) * 4 * ny);
+        if (!line)
+            err = 1;
+        double *dl = line ? line + 2 * ny : NULL;
+#pragma omp for schedule(static)
+        for (int x = 0; x < p->nx; ++x) {
+            if (!line)
+                continue;
+            for (int y = 0; y < ny; ++y) {
+                line[y] = u[(size_t)y * p->nx + x];
+                line[2 * ny - 1 - y] = u[(size_t)y * p->nx + x];
+            }
+            err |= orc_cfd_line(line, 1, dl, 1, 2 * ny, p->alpha, 1.0) != 0;
+            for (int y = 0; y < ny; ++y)
+                d[(size_t)y * p->nx + x] = dl[y];
+        }
+        free(line);
+    }
     return err ? -1 : 0;
 }
 
@@ -244,22 +277,28 @@ static int cfd_yy(const orc_params *p, const double *u, double *d)
         free(tmp);
         return err ? -1 : 0;
     }
-    double *line = (double *)malloc(sizeof(double) * 6 * ny);
-    if (!line)
-        return -1;
-    double *dl = line + 2 * ny, *ddl = line + 4 * ny;
     int err = 0;
-    for (int x = 0; x < p->nx && !err; ++x) {
-        for (int y = 0; y < ny; ++y) {
-            line[y] = u[(size_t)y * p->nx + x];
-            line[2 * ny - 1 - y] = u[(size_t)y * p->nx + x];
+#pragma omp parallel reduction(| : err)
+    {
+        double *line = (double *)malloc(sizeof(double) * 6 * ny);
+        if (!line)
+            err = 1;
+        double *dl = line ? line + 2 * ny : NULL, *ddl = line ? line + 4 * ny : NULL;
+#pragma omp for schedule(static)
+        for (int x = 0; x < p->nx; ++x) {
+            if (!line)
+                continue;
+            for (int y = 0; y < ny; ++y) {
+                line[y] = u[(size_t)y * p->nx + x];
+                line[2 * ny - 1 - y] = u[(size_t)y * p->nx + x];
+            }
+            err |= orc_cfd_line(line, 1, dl, 1, 2 * ny, p->alpha, 1.0) != 0;
+            err |= orc_cfd_line(dl, 1, ddl, 1, 2 * ny, p->alpha, 1.0) != 0;
+            for (int y = 0; y < ny; ++y)
+                d[(size_t)y * p->nx + x] = ddl[y];
         }
-        err = orc_cfd_line(line, 1, dl, 1, 2 * ny, p->alpha, 1.0);
-        err |= orc_cfd_line(dl, 1, ddl, 1, 2 * ny, p->alpha, 1.0);
-        for (int y = 0; y < ny; ++y)
-            d[(size_t)y * p->nx + x] = ddl[y];
+        free(line);
     }
-    free(line);
     return err ? -1 : 0;
 }
 
@@ -307,6 +346,7 @@ static void moments(const orc_params *p, const double *f, double *rho, double *u
                     double *uy)
 {
     size_t N = (size_t)p->nx * p->ny;
+#pragma omp parallel for schedule(static)
     for (size_t n = 0; n < N; ++n) {
         double r = 0.0, jx = 0.0, jy = 0.0;
         for (int i = 0; i < 9; ++i) {
@@ -346,6 +386,7 @@ int orc_force_stage(const orc_params *p, int64_t t, const double *rho, double *m
     double k2 = p->k * p->k;
     /* the repulsive pole: b rho / 4 = 1 (CS, Eq. 21) or b rho = 1 (Eqs. 15-19) */
     double bpole = p->eos == 0 ? p->b / 4.0 : p->b;
+#pragma omp parallel for schedule(static)
     for (size_t n = 0; n < N; ++n) {
         /* mu0 grows without bound as rho approaches the pole from below; at or
          * beyond it mu0 is taken as that limit, +infinity (where the printed
@@ -362,6 +403,7 @@ int orc_force_stage(const orc_params *p, int64_t t, const double *rho, double *m
     }
     err |= cfd_x(p, mu, dxmu);
     err |= cfd_y(p, mu, dymu);
+#pragma omp parallel for schedule(static)
     for (size_t n = 0; n < N; ++n) {
         Fx[n] = -rho[n] * dxmu[n] + CS2 * dxr[n];
         Fy[n] = -rho[n] * dymu[n] + CS2 * dyr[n];
@@ -461,6 +503,7 @@ int orc_run(const orc_params *p, double *f, int64_t t0, int64_t nsteps)
         err |= orc_force_stage(p, t, rho, NULL, Fx, Fy);
         /* collision: the right-hand side of Eq. 1 (BGK) or Eq. 4 (MRT,
          * f* = f - M^-1 S M (f - f^eq) + F_i) */
+#pragma omp parallel for schedule(static)
         for (size_t n = 0; n < N; ++n) {
             double Fi[9];
             orc_forcing_terms(rho[n], ux[n], uy[n], Fx[n], Fy[n], Fi);
@@ -495,7 +538,10 @@ int orc_run(const orc_params *p, double *f, int64_t t0, int64_t nsteps)
          *   f_opp(i)(x, t+1) = f*_i(x, t) - 2 w_i rho(x, t) (e_i . U) / c_s^2,
          * with rho the node's own density: mass is conserved, since the two
          * diagonals it changes cancel. */
+        /* every destination is written by exactly one source, so the rows can
+         * be shared among threads */
         for (int i = 0; i < 9; ++i)
+#pragma omp parallel for schedule(static)
             for (int y = 0; y < ny; ++y)
                 for (int x = 0; x < nx; ++x) {
                     int xd = (x + EX[i] + nx) % nx, yd = y + EY[i];

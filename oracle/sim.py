@@ -65,6 +65,11 @@ def lib():
         L.orc_run.argtypes = [P, dp, C.c_int64, C.c_int64]
         L.orc_macro.restype = C.c_int
         L.orc_macro.argtypes = [P, dp, C.c_int64, dp, dp, dp, dp, dp, dp]
+        L.orc_set_threads.restype = None
+        L.orc_set_threads.argtypes = [C.c_int]
+        L.orc_get_threads.restype = C.c_int
+        L.orc_get_threads.argtypes = []
+        L.orc_set_threads(1)
         _lib = L
     return _lib
 
@@ -74,6 +79,13 @@ def _ptr(a):
         return None
     assert a.dtype == np.float64 and a.flags.c_contiguous
     return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def set_threads(n):
+    """Threads the C oracle shares its loops among (1 by default); returns the
+    number it will use.  Results do not depend on it."""
+    lib().orc_set_threads(int(n))
+    return lib().orc_get_threads()
 
 
 def cs_p0(rho, T, a=1.0, b=4.0, R=1.0):

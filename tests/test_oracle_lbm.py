@@ -164,3 +164,27 @@ def test_force_where_the_limit_caps_every_node():
     theta = (A * np.sin(w) + B / 2 * np.sin(2 * w)) / (1 + 2 * a * np.cos(w))
     assert np.abs(Fy - 0.02 * theta * np.cos(w * y) / 3).max() <= 1e-15
     assert np.all(Fx == 0.0)
+
+
+def test_threads_do_not_change_the_bits():
+    """The C oracle shares its loops over lines and nodes among threads when
+    built with OpenMP; every line and node is computed as with one thread, so a
+    run gives the same bits with 1 and with 4 threads (periodic and walled)."""
+    from oracle import sim as S
+    from oracle import thermo as T
+    from paper_1906_09530_gb300 import workloads as W
+    Tc, _ = T.critical_point()
+    rg, rl = T.maxwell(0.6)
+    rho = W.with_noise(W.drop(48, 40, rg, rl, 10.0, 4.0), 7, 1e-4)
+    out = []
+    try:
+        for n in (1, 4):
+            S.set_threads(n)
+            for walls in (False, True):
+                o = S.OracleSim(48, 40, 0.6 * Tc, 0.1, 0.9, 0.5, 6, walls_y=walls)
+                o.set_fields(rho)
+                o.step(30)
+                out.append(o.f.copy())
+    finally:
+        S.set_threads(1)
+    assert np.array_equal(out[0], out[2]) and np.array_equal(out[1], out[3])
