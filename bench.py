@@ -24,7 +24,11 @@ and another 512 MB read to flush the L2 (not timed).  value = nodes x K / sum
 of step times.  The per-pass breakdown and the roofline come from a further
 min(K, 200) flushed steps with events around every pass (lbm_step_timed).
 e2e = the same metric through the public host API (lbm_set_fields from pinned
-host memory, K steps, lbm_fields back to host), wall clock.
+host memory, K steps, lbm_fields back to host), wall clock.  roofline: the
+dominant pass against the measured copy bandwidth (frac) and the 7.9 TB/s
+nominal (frac_nominal), with the whole step ("step") and the same figures at
+4096^2 ("at_4096", working set far above L2).  cpu_baseline: the FP64 oracle on
+all host cores (OpenMP), with its single-thread figure beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -47,6 +51,8 @@ if ROOT not in sys.path:
 WORKLOAD = dict(nx=1024, ny=1024, T_r=0.5, k=0.5, kappa=0.1, tau=1.0, order=6, radius=200.0,
                 width=8.0)
 METRIC = "MLUPS (million lattice-node updates per second) of the full time step"
+HBM_NOMINAL_GBS = 7900.0    # HBM3e nominal of one GB300, quoted beside the measured copy peak
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (non-tensor) nominal: the FP64 path is bound by it
 DF_RATIO = 1e4  # the mixed path's density lines are double-float from this Maxwell ratio
 
 
@@ -150,27 +156,42 @@ def bus_id(dev):
         return None
 
 
-def cpu_baseline(w, target_s=12.0):
-    """The FP64 C oracle, single thread, on a bounded sample of the same workload:
-    as many full-grid time steps as fit in about target_s seconds."""
-    from oracle import OracleSim, thermo
+def cpu_baseline(w, target_s=10.0):
+    """The FP64 C oracle on a bounded sample of the same workload: as many
+    full-grid time steps as fit in about target_s seconds, first on one thread,
+    then with its loops over lines and nodes shared among all host cores
+    (OpenMP).  `value` is the all-cores figure."""
+    from oracle import OracleSim, sim as S, thermo
     from paper_1906_09530_gb300 import workloads as W
     Tc, _ = thermo.critical_point()
     rg, rl = thermo.maxwell(w["T_r"])
     rho = W.drop(w["nx"], w["ny"], rg, rl, w["radius"], w["width"])
-    o = OracleSim(w["nx"], w["ny"], w["T_r"] * Tc, w["kappa"], w["tau"], w["k"], w["order"])
-    o.set_fields(rho)
-    t0 = time.perf_counter()
-    o.step(1)
-    dt1 = time.perf_counter() - t0
-    n = max(1, min(200, int(target_s / max(dt1, 1e-6)) - 1))
-    t0 = time.perf_counter()
-    o.step(n)
-    dt = time.perf_counter() - t0
-    mlups = w["nx"] * w["ny"] * n / dt / 1e6
-    return {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": f"{n} full {w['nx']}x{w['ny']} FP64 time steps of the same drop "
-                      f"(after 1 untimed), plain C oracle, 1 thread, {dt:.1f} s"}
+    nproc = os.cpu_count() or 1
+
+    def timed(threads):
+        used = S.set_threads(threads)
+        o = OracleSim(w["nx"], w["ny"], w["T_r"] * Tc, w["kappa"], w["tau"], w["k"],
+                      w["order"])
+        o.set_fields(rho)
+        t0 = time.perf_counter()
+        o.step(1)
+        dt1 = time.perf_counter() - t0
+        n = max(1, min(400, int(target_s / max(dt1, 1e-6)) - 1))
+        t0 = time.perf_counter()
+        o.step(n)
+        dt = time.perf_counter() - t0
+        return w["nx"] * w["ny"] * n / dt / 1e6, n, dt, used
+    try:
+        one, n1, dt1, _ = timed(1)
+        allc, na, dta, used = timed(nproc)
+    finally:
+        S.set_threads(1)
+    return {"value": allc, "unit": "MLUPS", "cores": used, "nproc": nproc, "kind": "oracle",
+            "sample": f"{na} full {w['nx']}x{w['ny']} FP64 time steps of the same drop "
+                      f"(after 1 untimed), plain C oracle, OpenMP over lines and nodes on "
+                      f"{used} threads, {dta:.1f} s",
+            "single_thread": {"value": one, "unit": "MLUPS", "cores": 1,
+                              "sample": f"{n1} steps, 1 thread, {dt1:.1f} s"}}
 
 
 EQ_WORKLOAD = dict(nx=8, ny=400, T_r=0.8, k=0.1, kappa=0.1, tau=1.0, order=6)
@@ -238,14 +259,42 @@ def large_grid(precision, steps, warmup, size=4096, collision="bgk", **over):
     step_ms = float(ms.sum(axis=1).mean())
     peak, peak_kind = load_peaks()
     gbs = sum(pb) * N / (step_ms / 1e3) / 1e9
+    mean = ms.mean(axis=0)
+    dom = int(np.argmax(mean))
+    dom_gbs = pb[dom] * N / (float(mean[dom]) / 1e3) / 1e9
     return {"workload": workload_name(w, precision) + ("-mrt" if collision == "mrt" else ""),
             "collision": collision, "nodes": N, "steps": steps,
             "mlups": N / (step_ms / 1e3) / 1e6, "ms_per_step": step_ms,
-            "passes_ms": {nm: round(float(ms[:, i].mean()), 5) for i, nm in enumerate(names)},
+            "passes_ms": {nm: round(float(mean[i]), 5) for i, nm in enumerate(names)},
+            "passes_frac_hbm": {nm: round(pb[i] * N / (float(mean[i]) / 1e3) / 1e9 / peak, 4)
+                                for i, nm in enumerate(names)},
+            "dominant": {"kernel": names[dom], "alg_bytes_per_node": pb[dom],
+                         "achieved_GB/s": dom_gbs, "frac": dom_gbs / peak},
             "step_roofline": {"alg_bytes_per_node": sum(pb), "achieved_GB/s": gbs,
                               "peak": peak, "frac": gbs / peak,
                               "peak_kind": f"{peak_kind} copy bandwidth"},
             "l2": "working set above L2 (no flush)"}
+
+
+def fp64_path_summary(lg):
+    """The FP64 path at 4096^2 against the FP64 pipe: its FP64 operations per
+    node (FMA counted as two) from the committed ncu count, if the kernel sources
+    are unchanged since, times the node rate, over the GB300's FP64 nominal."""
+    out = {"workload": lg["workload"], "mlups": lg["mlups"],
+           "frac_hbm": lg["step_roofline"]["frac"], "bound": "fp64 pipe"}
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "fp64_ops.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        h = hashlib.sha256(b"".join(open(os.path.join(ROOT, f), "rb").read()
+                                    for f in d["sources"])).hexdigest()[:16]
+        if h == d["sources_sha256_16"]:
+            fl = d["fp64_flops_per_node"]
+            tf = fl * lg["mlups"] * 1e6 / 1e12
+            out.update({"fp64_flops_per_node": fl, "achieved_tflops": tf,
+                        "peak_tflops": FP64_NOMINAL_TFLOPS, "frac": tf / FP64_NOMINAL_TFLOPS,
+                        "peak_kind": "nominal"})
+    return out
 
 
 def batch_config(steps, warmup, n=256):
@@ -783,11 +832,13 @@ def run_reference(args, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    from oracle import OracleSim, thermo
+    from oracle import OracleSim, sim as S, thermo
     from paper_1906_09530_gb300 import workloads as W
     Tc, _ = thermo.critical_point()
     rg, rl = thermo.maxwell(w["T_r"])
     rho = W.drop(w["nx"], w["ny"], rg, rl, w["radius"], w["width"])
+    # the oracle with its loops shared among all host cores (OpenMP)
+    cores = S.set_threads(os.cpu_count() or 1)
     o = OracleSim(w["nx"], w["ny"], w["T_r"] * Tc, w["kappa"], w["tau"], w["k"], w["order"])
     o.set_fields(rho)
     # each reference step is one full-grid oracle step; up to three warm-up
@@ -812,9 +863,10 @@ def run_reference(args, w):
             "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name(w, args.precision),
                        "arithmetic": "the FP64 oracle on the same workload"},
-            "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": cores, "kind": "oracle",
                              "sample": f"{k} full-grid FP64 oracle step{'s' * (k != 1)} "
-                                       f"(of {args.steps} asked; bounded to ~150 s), 1 thread"},
+                                       f"(of {args.steps} asked; bounded to ~150 s), "
+                                       f"{cores} threads (OpenMP over lines and nodes)"},
             "e2e": {"value": val, "unit": "MLUPS", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -957,6 +1009,12 @@ def main():
                 "peak_kind": f"{peak_kind} copy bandwidth",
                 "alg_bytes_per_launch": pb[dom] * N}
     step_gbs = sum(pb) * N / (float(step_ms.mean()) / 1e3) / 1e9
+    roofline["frac_nominal"] = ach / HBM_NOMINAL_GBS
+    roofline["step"] = {"alg_bytes_per_node": sum(pb), "achieved": step_gbs,
+                        "frac": step_gbs / peak, "frac_nominal": step_gbs / HBM_NOMINAL_GBS,
+                        "what": "whole step: the algorithmic bytes of all its passes over "
+                                "the mean step time; frac against the measured copy peak, "
+                                "frac_nominal against 7.9 TB/s"}
     line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": float(step_ms.mean()), "higher_is_better": True,
@@ -976,8 +1034,18 @@ def main():
             "graph_back_to_back_mlups": graph_mlups,
             "e2e": e2e, "gpu_launches": len(names) * args.steps, "clocks": clk}
     if not args.no_large and args.size < 4096:
-        line["large_grid"] = large_grid(args.precision, min(args.steps, 100),
-                                        max(args.warmup, 3))
+        lg = large_grid(args.precision, min(args.steps, 100), max(args.warmup, 3))
+        line["large_grid"] = lg
+        # the same figures at 4096^2, where the working set is far above L2
+        sr = lg["step_roofline"]
+        roofline["at_4096"] = {
+            "workload": lg["workload"], "mlups": lg["mlups"],
+            "kernel": lg["dominant"]["kernel"], "achieved": lg["dominant"]["achieved_GB/s"],
+            "frac": lg["dominant"]["frac"],
+            "frac_nominal": lg["dominant"]["achieved_GB/s"] / HBM_NOMINAL_GBS,
+            "passes_frac": lg["passes_frac_hbm"],
+            "step_achieved": sr["achieved_GB/s"], "step_frac": sr["frac"],
+            "step_frac_nominal": sr["achieved_GB/s"] / HBM_NOMINAL_GBS}
         # MRT with the paper's rates is unstable on the T_r 0.5, k 0.5 drop
         # (as in the oracle); its throughput is taken on a stable T_r 0.7, k 0.3 one
         line["large_grid_mrt"] = large_grid(args.precision, min(args.steps, 100),
@@ -989,6 +1057,7 @@ def main():
         if args.precision != "fp64":
             line["large_grid_fp64"] = large_grid("fp64", min(args.steps, 20),
                                                  max(args.warmup, 3), size=4096)
+            line["fp64_path"] = fp64_path_summary(line["large_grid_fp64"])
     if not args.no_batch and args.precision == "mixed":
         line["batch"] = batch_config(min(args.steps, 50), max(args.warmup // 10, 3))
     if rank == 0 and not args.no_splash:
