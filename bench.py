@@ -197,16 +197,20 @@ def cpu_baseline(w, target_s=10.0):
 EQ_WORKLOAD = dict(nx=8, ny=400, T_r=0.8, k=0.1, kappa=0.1, tau=1.0, order=6)
 
 
-def equilibrium_time(precision, max_steps=600_000):
+def equilibrium_time(precision, max_steps=600_000, nx=None):
     """Wall time from lbm_set_fields to Maxwell-accurate equilibrium of a flat
-    interface (quasi-1-D, periodic, height 400, k = 0.1, T_r = 0.8; Sec. 5.1).
-    Checked every 500 steps: done when the bulk gas and liquid densities are both
-    within 1e-3 of the Maxwell pair and moved by < 1e-6 (relative) over the last
-    500 steps."""
+    interface (periodic, height 400, k = 0.1, T_r = 0.8; Sec. 5.1), quasi-1-D
+    (8 wide) or nx wide.  Checked every 500 steps: done when the bulk gas and
+    liquid densities are both within 1e-3 of the Maxwell pair and moved by
+    < 1e-6 (relative) over the last 500 steps.  (At k = 0.1 the method's gas
+    settles within 1e-3 of Maxwell only above T_r ~ 0.65: below, the target is
+    out of its reach at this k.)"""
     import numpy as np
     import paper_1906_09530_gb300 as P
     from paper_1906_09530_gb300 import workloads as W
-    e = EQ_WORKLOAD
+    e = dict(EQ_WORKLOAD)
+    if nx is not None:
+        e["nx"] = nx
     rg, rl = P.lbm_maxwell(e["T_r"])
     rho0 = W.flat(e["nx"], e["ny"], rg, rl, e["ny"] / 2, 4.0 / e["k"])
     sim = P.Simulation(e["nx"], e["ny"], e["T_r"], e["kappa"], e["tau"], e["k"],
@@ -1067,6 +1071,9 @@ def main():
         line["surrogate"] = surrogate_demo()
     if rank == 0 and not args.no_equilibrium:
         line["equilibrium"] = equilibrium_time(args.precision)
+        # the same slab 1024 nodes wide (409 600 nodes, the grid scale of the
+        # benchmark drop)
+        line["equilibrium_1024"] = equilibrium_time(args.precision, nx=1024)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     if rank == 0:

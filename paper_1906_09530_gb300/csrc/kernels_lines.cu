@@ -296,13 +296,13 @@ struct Rd<PolF, PolDF> {
 
 // One window, one warp per line: right-hand sides, chunked recursions joined by
 // shuffle scans, results to tout1 (first derivative) and tout2 (second).
-template <class Q, class P1, class P2, bool SIXTH, bool SECOND>
+template <class Q, class P1, class P2, bool SIXTH, bool SECOND, int NL>
 __device__ __forceinline__ void solve_window(const typename P1::S* tin, typename Q::O* tout1,
                                              typename P2::V* tout2, const LineConst<Q>& kq,
                                              const LineConst<P2>& k2) {
     using VQ = typename Q::V;
     using V2 = typename P2::V;
-    constexpr int kPS = kNL * kLW;
+    constexpr int kPS = NL * kLW;
     const int tid = threadIdx.x;
     const int w = tid >> 5, lane = tid & 31;
     const int tb = w * kLW + 4;  // slot of window position 0 of this warp's line
@@ -446,25 +446,27 @@ __device__ __forceinline__ void solve_window(const typename P1::S* tin, typename
 }
 
 // y-lines of FP32 fields, window staged row by row: slot r of the window
-// (position r - 4) holds the 8 columns of one grid row, tin[r * 8 + line].  A
-// lane owns chunk c = 4 warp + lane / 8 (kC positions from q0 = c kC) of line
-// lane % 8, so a warp reads 4 chunks x 8 lines of one row offset per access,
-// 32 distinct banks (kC 8 = 24 mod 32).  The chunks of a line sit in different
-// warps, so their boundary states are joined through shared memory: the state
-// entering chunk c is E_{c-1} + m E_{c-2} + m^2 E_{c-3} (m = (-lam)^kC), the
-// same three terms the shuffle scan of solve_window keeps.  Results go to
-// tout1 / tout2 in the same row layout, position q at [q * 8 + line].
-template <bool SIXTH, bool SECOND>
+// (position r - 4) holds the NL adjacent columns of one grid row,
+// tin[r * NL + line].  A lane owns chunk c = (32 / NL) warp + lane / NL (kC
+// positions from q0 = c kC) of line lane % NL; the lanes of a warp read 32 / NL
+// chunks x NL lines at one row offset per access, in 32 distinct banks (kC is
+// odd).  The chunks of a line sit in different warps, so their boundary states
+// are joined through shared memory: the state entering chunk c is
+// E_{c-1} + m E_{c-2} + m^2 E_{c-3} (m = (-lam)^kC), the same three terms the
+// shuffle scan of solve_window keeps.  Results go to tout1 / tout2 in the same
+// row layout, position q at [q * NL + line].
+template <bool SIXTH, bool SECOND, int NL>
 __device__ __forceinline__ void solve_window_y(const float* tin, float* tout1, float* tout2,
                                                const LineConst<PolF>& kq,
                                                const LineConst<PolF>& k2) {
-    __shared__ float xa[32][kNL], xb[32][kNL], xc[32][kNL];  // forward states
-    __shared__ float ya[32][kNL], yb[32][kNL], yc[32][kNL];  // backward states
+    __shared__ float xa[32][NL], xb[32][NL], xc[32][NL];  // forward states
+    __shared__ float ya[32][NL], yb[32][NL], yc[32][NL];  // backward states
     const int tid = threadIdx.x;
     const int w = tid >> 5, lane = tid & 31;
-    const int l = lane & 7, c = 4 * w + (lane >> 3);
+    static_assert(32 % NL == 0, "a warp holds whole rows of the window");
+    const int l = lane % NL, c = (32 / NL) * w + lane / NL;  // NL warps: 32 chunks
     const int q0 = c * kC;
-    auto tl = [&](int q) { return tin[(q + 4) * kNL + l]; };  // q in [-4, kW+4)
+    auto tl = [&](int q) { return tin[(q + 4) * NL + l]; };  // q in [-4, kW+4)
 
     float r[kC];
     {
@@ -596,17 +598,17 @@ __device__ __forceinline__ void solve_window_y(const float* tin, float* tout1, f
     }
 #pragma unroll
     for (int j = 0; j < kC; ++j) {
-        tout1[(q0 + j) * kNL + l] = r[j];
-        if (SECOND) tout2[(q0 + j) * kNL + l] = r2[j];
+        tout1[(q0 + j) * NL + l] = r[j];
+        if (SECOND) tout2[(q0 + j) * NL + l] = r2[j];
     }
 }
 
-template <int AXIS, class P1, class P2, bool SIXTH, bool SECOND, class In, class Epi>
+template <int AXIS, class P1, class P2, bool SIXTH, bool SECOND, int NL, class In, class Epi>
 __device__ __forceinline__ void lines_body(In& in, const LineGeo& g, const LineConst<P1>& k1,
                                            const LineConst<PolF>& k1f,
                                            const LineConst<P2>& k2, Epi& epi, DevState* st,
                                            int bid, const CUtensorMap* tmap = nullptr) {
-    // FP32 y-lines stage their window row by row ([slot][8 lines]); the rest
+    // FP32 y-lines stage their window row by row ([slot][NL lines]); the rest
     // stage it line by line ([line][slot])
     constexpr bool kRowY = AXIS == 1 && std::is_same<P1, PolF>::value &&
                            std::is_same<P2, PolF>::value;
@@ -615,23 +617,23 @@ __device__ __forceinline__ void lines_body(In& in, const LineGeo& g, const LineC
     using O1 = typename P1::O;
     using S1 = typename P1::S;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    constexpr int kPS = kNL * kLW;                                   // plane stride
+    constexpr int kPS = NL * kLW;                                   // plane stride
     // the outputs reuse the staged planes: the first derivative plane 0, the
     // second plane 1 (double-float input) or a plane of its own
-    S1* tin = reinterpret_cast<S1*>(smem_raw);                      // [planes][kNL][kLW]
+    S1* tin = reinterpret_cast<S1*>(smem_raw);                      // [planes][NL][kLW]
     static_assert(sizeof(O1) == sizeof(S1), "first derivative over the staged plane 0");
-    O1* tout1 = reinterpret_cast<O1*>(tin);                         // [kNL][kSO]
+    O1* tout1 = reinterpret_cast<O1*>(tin);                         // [NL][kSO]
     V2* tout2 = P1::kPlanes >= 2 ? reinterpret_cast<V2*>(tin + kPS)
                                  : reinterpret_cast<V2*>(tin + P1::kPlanes * kPS);
 
     const int grp = bid % g.ngroups;
     const int win = bid / g.ngroups;
-    const int line0 = grp * kNL;
+    const int line0 = grp * NL;
     const int s = win * g.own;                      // first owned position
     const int e = min(s + g.own, g.n);              // one past the last
     const int tid = threadIdx.x;
 
-    // ---- stage the window: positions s-H-4 .. s-H+kW+3 of kNL lines ----
+    // ---- stage the window: positions s-H-4 .. s-H+kW+3 of NL lines ----
     constexpr int LWIN = kW + 8;
     const int p0 = wrapi((long long)s - g.H - 4, g.period);  // period position of slot 0
     const bool short_line = g.period < LWIN;
@@ -639,17 +641,17 @@ __device__ __forceinline__ void lines_body(In& in, const LineGeo& g, const LineC
         // row layout: slot q holds columns line0 .. line0 + 7 of period position p0 + q
         const long long p_end = (long long)s - g.H - 4 + LWIN;  // one past the last slot
         const bool interior = (long long)s - g.H - 4 >= 0 && p_end <= g.n;
-        if (tmap && st && g.vec && interior && line0 + kNL <= g.nlines &&
+        if (tmap && st && g.vec && interior && line0 + NL <= g.nlines &&
             (smem_u32(tin) & 127u) == 0) {
             // one elected thread moves the window with tensor copies
             __shared__ __align__(8) uint64_t bar;
             if (tid == 0) mbar_init(&bar, 1);
             __syncthreads();
             if (tid == 0) {
-                mbar_expect_tx(&bar, (unsigned)(LWIN * kNL * sizeof(float)));
+                mbar_expect_tx(&bar, (unsigned)(LWIN * NL * sizeof(float)));
 #pragma unroll 1
                 for (int b = 0; b < LWIN / kBoxRows; ++b)
-                    tma_load_2d(tin + b * kBoxRows * kNL, tmap, line0, p0 + b * kBoxRows, &bar);
+                    tma_load_2d(tin + b * kBoxRows * NL, tmap, line0, p0 + b * kBoxRows, &bar);
             }
             const bool arrived = mbar_wait_bounded(&bar, 0);
             if (__syncthreads_or(!arrived)) {
@@ -660,11 +662,12 @@ __device__ __forceinline__ void lines_body(In& in, const LineGeo& g, const LineC
                 return;
             }
         } else if (g.vec) {
-            // 16-byte pieces: slot q, half h covers columns line0 + 4h .. + 3
-            for (int idx = tid; idx < 2 * LWIN; idx += kNL * 32) {
-                const int q = idx >> 1, h = idx & 1;
+            // 16-byte pieces: slot q, piece h covers columns line0 + 4h .. + 3
+            constexpr int PR = NL / 4;  // pieces per row
+            for (int idx = tid; idx < PR * LWIN; idx += NL * 32) {
+                const int q = idx / PR, h = idx % PR;
                 const int col = line0 + 4 * h;
-                S1* dst = tin + q * kNL + 4 * h;
+                S1* dst = tin + q * NL + 4 * h;
                 if (col < g.nlines) {
                     int p = p0 + q;
                     if (short_line) p %= g.period;
@@ -677,47 +680,50 @@ __device__ __forceinline__ void lines_body(In& in, const LineGeo& g, const LineC
                 }
             }
         } else {
-            for (int idx = tid; idx < kNL * LWIN; idx += kNL * 32) {
-                const int q = idx >> 3, ll = idx & 7;
+            for (int idx = tid; idx < NL * LWIN; idx += NL * 32) {
+                const int q = idx / NL, ll = idx % NL;
                 const int col = line0 + ll;
                 if (col < g.nlines) {
                     int p = p0 + q;
                     if (short_line) p %= g.period;
                     else if (p >= g.period) p -= g.period;
                     if (g.mirror && p >= g.n) p = 2 * g.n - 1 - p;
-                    in.stage(tin, q * kNL + ll, kPS, (size_t)p * g.ps + (size_t)col);
+                    in.stage(tin, q * NL + ll, kPS, (size_t)p * g.ps + (size_t)col);
                 } else {
-                    tin[q * kNL + ll] = 0.0f;
+                    tin[q * NL + ll] = 0.0f;
                 }
             }
         }
     } else if (AXIS == 0 && g.vec) {
-        // rows: 16-byte chunks (p0, H and own are multiples of 4, and so is the
-        // line length, so no chunk straddles the periodic wrap)
+        // rows: warp w stages line line0 + w in 16-byte chunks (p0, H and own are
+        // multiples of 4, and so is the line length, so no chunk straddles the
+        // periodic wrap)
         constexpr int CW = LWIN / 4;
-        for (int idx = tid; idx < kNL * CW; idx += kNL * 32) {
-            const int l = idx / CW;
-            const int q = 4 * (idx - l * CW);
-            const int line = line0 + l;
-            if (line < g.nlines) {
-                int p = p0 + q;
+        const int l = tid >> 5, lane = tid & 31;
+        const int line = line0 + l;
+        if (line < g.nlines) {
+            const size_t lbase = (size_t)line * g.ls;
+            for (int c = lane; c < CW; c += 32) {
+                int p = p0 + 4 * c;
                 if (short_line) p %= g.period;
                 else if (p >= g.period) p -= g.period;
-                in.stage4(tin, l * kLW + q, kPS, (size_t)line * g.ls + (size_t)p);
-            } else {
+                in.stage4(tin, l * kLW + 4 * c, kPS, lbase + (size_t)p);
+            }
+        } else {
+            for (int c = lane; c < CW; c += 32) {
 #pragma unroll
-                for (int k = 0; k < 4; ++k) P1::sput(tin, l * kLW + q + k, kPS, P1::zero());
+                for (int k = 0; k < 4; ++k) P1::sput(tin, l * kLW + 4 * c + k, kPS, P1::zero());
             }
         }
     } else {
-        for (int idx = tid; idx < kNL * LWIN; idx += kNL * 32) {
+        for (int idx = tid; idx < NL * LWIN; idx += NL * 32) {
             int l, q;
             if (AXIS == 0) {
                 l = idx / LWIN;
                 q = idx - l * LWIN;
             } else {
-                q = idx / kNL;
-                l = idx - q * kNL;
+                q = idx / NL;
+                l = idx - q * NL;
             }
             const int line = line0 + l;
             if (line < g.nlines) {
@@ -739,11 +745,11 @@ __device__ __forceinline__ void lines_body(In& in, const LineGeo& g, const LineC
     // ~2e-6 of the local values, as accurate as the FP32 result that is stored;
     // only windows reaching across an interface need the double-float solve.
     if constexpr (kRowY) {
-        solve_window_y<SIXTH, SECOND>(tin, tout1, tout2, k1, k2);
+        solve_window_y<SIXTH, SECOND, NL>(tin, tout1, tout2, k1, k2);
     } else if constexpr (std::is_same<P1, PolDF>::value) {
-        __shared__ float red[2][kNL];
+        __shared__ float red[2][NL];
         float mn = FLT_MAX, mx = 0.0f;
-        for (int idx = tid; idx < kNL * LWIN; idx += kNL * 32) {
+        for (int idx = tid; idx < NL * LWIN; idx += NL * 32) {
             const int l = idx / LWIN, q = idx - l * LWIN;
             const float v = tin[l * kLW + q];
             mn = fminf(mn, v);
@@ -762,16 +768,16 @@ __device__ __forceinline__ void lines_body(In& in, const LineGeo& g, const LineC
         mn = red[0][0];
         mx = red[1][0];
 #pragma unroll
-        for (int k = 1; k < kNL; ++k) {
+        for (int k = 1; k < NL; ++k) {
             mn = fminf(mn, red[0][k]);
             mx = fmaxf(mx, red[1][k]);
         }
         if (mn > 0.0f && mx <= 32.0f * mn)
-            solve_window<PolF, P1, P2, SIXTH, SECOND>(tin, tout1, tout2, k1f, k2);
+            solve_window<PolF, P1, P2, SIXTH, SECOND, NL>(tin, tout1, tout2, k1f, k2);
         else
-            solve_window<P1, P1, P2, SIXTH, SECOND>(tin, tout1, tout2, k1, k2);
+            solve_window<P1, P1, P2, SIXTH, SECOND, NL>(tin, tout1, tout2, k1, k2);
     } else {
-        solve_window<P1, P1, P2, SIXTH, SECOND>(tin, tout1, tout2, k1, k2);
+        solve_window<P1, P1, P2, SIXTH, SECOND, NL>(tin, tout1, tout2, k1, k2);
     }
     __syncthreads();
 
@@ -780,22 +786,23 @@ __device__ __forceinline__ void lines_body(In& in, const LineGeo& g, const LineC
     // groups of kB before any of the group's results is written.
     constexpr int kB = Epi::kBatch;
     const int nown = e - s;
-    const int lmax = min(kNL, g.nlines - line0);
+    const int lmax = min(NL, g.nlines - line0);
     bool bad = false;
     if constexpr (kRowY) {
-        // outputs in the row layout: position q of line l at [q * 8 + l]
+        // outputs in the row layout: position q of line l at [q * NL + l]
         if (g.vec) {
             // 16-byte pieces: one row, four adjacent lines (columns line0 + 4h ..)
-            const int total = 2 * nown;
-            for (int base = tid; base < total; base += kB * kNL * 32) {
+            constexpr int PR = NL / 4;  // pieces per row
+            const int total = PR * nown;
+            for (int base = tid; base < total; base += kB * NL * 32) {
                 int sl[kB];
                 size_t off[kB];
                 typename Epi::Ops4 ops[kB];
 #pragma unroll
                 for (int k = 0; k < kB; ++k) {
-                    const int idx = base + k * kNL * 32;
-                    const int qq = idx >> 1, h4 = 4 * (idx & 1);
-                    sl[k] = (g.H + qq) * kNL + h4;
+                    const int idx = base + k * NL * 32;
+                    const int qq = idx / PR, h4 = 4 * (idx % PR);
+                    sl[k] = (g.H + qq) * NL + h4;
                     off[k] = (size_t)(line0 + h4) + (size_t)(s + qq) * g.ps;
                     if (!(idx < total && h4 < lmax)) sl[k] = -1;
                     else ops[k] = epi.fetch4(off[k]);
@@ -810,17 +817,17 @@ __device__ __forceinline__ void lines_body(In& in, const LineGeo& g, const LineC
                 }
             }
         } else {
-            const int total = kNL * nown;
-            for (int base = tid; base < total; base += kB * kNL * 32) {
+            const int total = NL * nown;
+            for (int base = tid; base < total; base += kB * NL * 32) {
                 int slot[kB];
                 size_t off[kB];
                 typename Epi::Ops ops[kB];
 #pragma unroll
                 for (int k = 0; k < kB; ++k) {
-                    const int idx = base + k * kNL * 32;
-                    const int qq = idx >> 3, ll = idx & 7;
+                    const int idx = base + k * NL * 32;
+                    const int qq = idx / NL, ll = idx % NL;
                     const bool live = idx < total && ll < lmax;
-                    slot[k] = live ? (g.H + qq) * kNL + ll : -1;
+                    slot[k] = live ? (g.H + qq) * NL + ll : -1;
                     off[k] = (size_t)(line0 + ll) + (size_t)(s + qq) * g.ps;
                     if (live) ops[k] = epi.fetch(off[k]);
                 }
@@ -835,20 +842,51 @@ __device__ __forceinline__ void lines_body(In& in, const LineGeo& g, const LineC
         if (bad) raise_flag(st, FLAG_EOS, st->t);
         return;
     }
+    if constexpr (AXIS == 0 && sizeof(O1) == 4 && sizeof(V2) == 4) {
+        if (g.vec) {
+            // float fields, nx % 4 == 0: warp w writes line line0 + w in chunks
+            // of four outputs, 16-byte loads from the staged plane and stores
+            const int ll = tid >> 5, lane = tid & 31;
+            if (ll < lmax) {
+                const size_t lbase = (size_t)(line0 + ll) * g.ls + (size_t)s;
+                const int sbase = ll * kSO + g.H;
+                for (int q4 = 4 * lane; q4 < nown; q4 += 4 * 32 * kB) {
+                    typename Epi::Ops4 ops[kB];
+#pragma unroll
+                    for (int k = 0; k < kB; ++k) {
+                        const int qq = q4 + 4 * 32 * k;
+                        if (qq < nown) ops[k] = epi.fetch4(lbase + qq);
+                    }
+#pragma unroll
+                    for (int k = 0; k < kB; ++k) {
+                        const int qq = q4 + 4 * 32 * k;
+                        if (qq >= nown) continue;
+                        const float4 a = *reinterpret_cast<const float4*>(tout1 + sbase + qq);
+                        float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (SECOND) b = *reinterpret_cast<const float4*>(tout2 + sbase + qq);
+                        bad |= epi.put4(lbase + qq, a, b, ops[k]);
+                    }
+                }
+            }
+            bad |= in.flagged();
+            if (bad) raise_flag(st, FLAG_EOS, st->t);
+            return;
+        }
+    }
     if constexpr (sizeof(O1) == 4 && sizeof(V2) == 4) {
         if (g.vec) {
             // float fields, nx % 4 == 0: chunks of four outputs, 16-byte stores.
             // x-lines: four consecutive positions of one line; y-lines: one
             // position of four adjacent lines (columns line0 + 4h .. + 3).
             const int cpl = AXIS == 0 ? nown / 4 : 2;  // chunks per line / per position
-            const int total = AXIS == 0 ? kNL * cpl : 2 * nown;
-            for (int base = tid; base < total; base += kB * kNL * 32) {
+            const int total = AXIS == 0 ? NL * cpl : 2 * nown;
+            for (int base = tid; base < total; base += kB * NL * 32) {
                 int sl[kB];
                 size_t off[kB];
                 typename Epi::Ops4 ops[kB];
 #pragma unroll
                 for (int k = 0; k < kB; ++k) {
-                    const int idx = base + k * kNL * 32;
+                    const int idx = base + k * NL * 32;
                     bool live;
                     if (AXIS == 0) {
                         const int ll = idx / cpl;
@@ -887,12 +925,12 @@ __device__ __forceinline__ void lines_body(In& in, const LineGeo& g, const LineC
             return;
         }
     }
-    const int total = kNL * nown;
+    const int total = NL * nown;
     int l0 = 0, q0e = tid;  // AXIS 0 walk: position q0e within line l0
     if (AXIS == 0) {
-        while (q0e >= nown && l0 < kNL) { q0e -= nown; ++l0; }
+        while (q0e >= nown && l0 < NL) { q0e -= nown; ++l0; }
     }
-    for (int base = tid; base < total; base += kB * kNL * 32) {
+    for (int base = tid; base < total; base += kB * NL * 32) {
         int slot[kB];
         size_t off[kB];
         typename Epi::Ops ops[kB];
@@ -902,12 +940,12 @@ __device__ __forceinline__ void lines_body(In& in, const LineGeo& g, const LineC
             if (AXIS == 0) {
                 ll = l0;
                 qq = q0e;
-                q0e += kNL * 32;
-                while (q0e >= nown && l0 < kNL) { q0e -= nown; ++l0; }
+                q0e += NL * 32;
+                while (q0e >= nown && l0 < NL) { q0e -= nown; ++l0; }
             } else {
-                const int idx = base + k * kNL * 32;
-                qq = idx / kNL;
-                ll = idx - qq * kNL;
+                const int idx = base + k * NL * 32;
+                qq = idx / NL;
+                ll = idx - qq * NL;
             }
             const bool live = ll < lmax && qq < nown;
             slot[k] = live ? ll * kSO + g.H + qq : -1;
@@ -931,14 +969,20 @@ __global__ void __launch_bounds__(kNL * 32)
     if (bump && blockIdx.x == 0 && threadIdx.x == 0) st->t += 1;
     epi.init(st);
     in.init(st);
-    lines_body<AXIS, P1, P2, SIXTH, SECOND>(in, g, k1, k1f, k2, epi, st, (int)blockIdx.x);
+    lines_body<AXIS, P1, P2, SIXTH, SECOND, kNL>(in, g, k1, k1f, k2, epi, st, (int)blockIdx.x);
 }
 
 // x-lines and y-lines of two independent solves in one launch: blocks below
 // nbx take the x windows, the rest the y windows.
-template <class P1, class P2, bool SIXTH, bool SECOND, class InX, class EpiX, class InY,
-          class EpiY>
-__global__ void __launch_bounds__(kNL * 32, SECOND && P1::kPlanes >= 2 ? 3 : 4)
+// Blocks of NL lines (NL warps); the launch bounds keep 32 warps per SM.
+template <int NL, bool SECOND, class P1>
+constexpr int xy_min_blocks() {
+    return NL == 8 ? (SECOND && P1::kPlanes >= 2 ? 3 : 4) : 8 * 4 / NL;
+}
+
+template <class P1, class P2, bool SIXTH, bool SECOND, int NL, class InX, class EpiX,
+          class InY, class EpiY>
+__global__ void __launch_bounds__(NL * 32, (xy_min_blocks<NL, SECOND, P1>()))
     k_lines_xy(InX inx, LineGeo gx, EpiX ex, InY iny, LineGeo gy, EpiY ey, LineConst<P1> k1,
                LineConst<PolF> k1f, LineConst<P2> k2, DevState* st, int bump, int nbx,
                const __grid_constant__ CUtensorMap tmy, int use_tma) {
@@ -946,11 +990,11 @@ __global__ void __launch_bounds__(kNL * 32, SECOND && P1::kPlanes >= 2 ? 3 : 4)
     if ((int)blockIdx.x < nbx) {
         ex.init(st);
         inx.init(st);
-        lines_body<0, P1, P2, SIXTH, SECOND>(inx, gx, k1, k1f, k2, ex, st, (int)blockIdx.x);
+        lines_body<0, P1, P2, SIXTH, SECOND, NL>(inx, gx, k1, k1f, k2, ex, st, (int)blockIdx.x);
     } else {
         ey.init(st);
         iny.init(st);
-        lines_body<1, P1, P2, SIXTH, SECOND>(iny, gy, k1, k1f, k2, ey, st,
+        lines_body<1, P1, P2, SIXTH, SECOND, NL>(iny, gy, k1, k1f, k2, ey, st,
                                              (int)blockIdx.x - nbx, use_tma ? &tmy : nullptr);
     }
 }
@@ -986,14 +1030,14 @@ __global__ void __launch_bounds__(kNL * 32, 3)
         const LineGeo g = D.gx;
         epi.init(st);
         in.init(st);
-        lines_body<0, P1, P2, SIXTH, SECOND>(in, g, k1, k1f, k2, epi, st, local);
+        lines_body<0, P1, P2, SIXTH, SECOND, kNL>(in, g, k1, k1f, k2, epi, st, local);
     } else {
         InY in = D.iny;
         EpiY epi = D.ey;
         const LineGeo g = D.gy;
         epi.init(st);
         in.init(st);
-        lines_body<1, P1, P2, SIXTH, SECOND>(in, g, k1, k1f, k2, epi, st, local - D.nbx);
+        lines_body<1, P1, P2, SIXTH, SECOND, kNL>(in, g, k1, k1f, k2, epi, st, local - D.nbx);
     }
 }
 
@@ -1066,7 +1110,7 @@ struct EpiMu {
 // F = -rho d(mu-hat) + c_s^2 d(rho), Eq. 12.
 template <class O, class RhoT>
 struct EpiForce {
-    static constexpr int kBatch = 2;  // its operands are float4 pairs: two in flight
+    static constexpr int kBatch = 4;  // its operands are float4 pairs: four in flight
     O* F;
     const RhoT* __restrict__ rho;
     const O* __restrict__ dr;
@@ -1153,7 +1197,7 @@ int halo(int order, double eps1, bool second, double eps2) {
 // Walls in y (walls_y): the y-lines are extended evenly about both walls, a
 // periodic line of period 2 ny whose first ghost equals its fluid neighbour
 // (the wall rule of Sec. 5.5); only the ny fluid positions are owned.
-LineGeo make_geo(int nx, int ny, int axis, int H, bool walls_y = false) {
+LineGeo make_geo(int nx, int ny, int axis, int H, bool walls_y = false, int nl = kNL) {
     LineGeo g;
     if (axis == 0) {
         g.n = nx; g.nlines = ny; g.ps = 1; g.ls = nx;
@@ -1167,17 +1211,17 @@ LineGeo make_geo(int nx, int ny, int axis, int H, bool walls_y = false) {
     g.own = kW - 2 * H;
     if (g.own > g.n) g.own = g.n;
     g.nwin = (g.n + g.own - 1) / g.own;
-    g.ngroups = (g.nlines + kNL - 1) / kNL;
+    g.ngroups = (g.nlines + nl - 1) / nl;
     g.vec = nx % 4 == 0;
     g.mirror = axis == 1 && walls_y;
     g.period = g.mirror ? 2 * g.n : g.n;
     return g;
 }
 
-template <class P1, class P2, bool SECOND>
+template <class P1, class P2, bool SECOND, int NL = kNL>
 size_t smem_bytes() {
-    return (size_t)P1::kPlanes * kNL * kLW * sizeof(typename P1::S) +
-           (SECOND && P1::kPlanes < 2 ? (size_t)kNL * kSO * sizeof(typename P2::V) : 0);
+    return (size_t)P1::kPlanes * NL * kLW * sizeof(typename P1::S) +
+           (SECOND && P1::kPlanes < 2 ? (size_t)NL * kSO * sizeof(typename P2::V) : 0);
 }
 
 template <int AXIS, class P1, class P2, bool SIXTH, bool SECOND, class In, class Epi>
@@ -1222,13 +1266,13 @@ EncodeTiledFn tensor_map_encoder() {
     return fn;
 }
 
-bool y_tensor_map(const float* field, int nx, int ny, CUtensorMap* m) {
-    if (!field || nx % 4 != 0 || nx < kNL || ny < kW + 8) return false;
+bool y_tensor_map(const float* field, int nx, int ny, int nl, CUtensorMap* m) {
+    if (!field || nx % 4 != 0 || nx < nl || ny < kW + 8) return false;
     const EncodeTiledFn enc = tensor_map_encoder();
     if (!enc) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)nx, (cuuint64_t)ny};
     const cuuint64_t strides[1] = {(cuuint64_t)nx * sizeof(float)};
-    const cuuint32_t box[2] = {(cuuint32_t)kNL, (cuuint32_t)kBoxRows};
+    const cuuint32_t box[2] = {(cuuint32_t)nl, (cuuint32_t)kBoxRows};
     const cuuint32_t estr[2] = {1, 1};
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(field), dims, strides,
                box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -1240,12 +1284,21 @@ template <class In>
 const float* y_field(const In&) { return nullptr; }
 const float* y_field(const InF& in) { return in.p; }
 
-template <class P1, class P2, bool SIXTH, bool SECOND, class InX, class EpiX, class InY,
-          class EpiY>
+// Lines per block of a merged launch.  16 lines make the FP32 y-line windows
+// move 64-byte row pieces (32-byte pieces lose about a quarter of the DRAM
+// bandwidth: 2.5 against 3.35 TB/s measured for windows read alone), but halve
+// the blocks resident per SM.  Measured on the merged density lines: 16 lines
+// win on grids up to 1024^2 (13.3 against 14.8 us), 8 from 2048^2 up (30 against
+// 32 us; 95 against 107 us at 4096^2).  Double-float and FP64 solves keep 8.
+// The choice moves no result: every line is solved the same way either way.
+constexpr long long kWideLinesMaxNodes = 1LL << 21;
+
+template <class P1, class P2, bool SIXTH, bool SECOND, int NL, class InX, class EpiX,
+          class InY, class EpiY>
 cudaError_t launch_xy_t(InX inx, EpiX ex, InY iny, EpiY ey, int nx, int ny, int order, int H,
                         DevState* st, int bump, bool walls_y, cudaStream_t s) {
-    auto kern = k_lines_xy<P1, P2, SIXTH, SECOND, InX, EpiX, InY, EpiY>;
-    const size_t smem = smem_bytes<P1, P2, SECOND>();
+    auto kern = k_lines_xy<P1, P2, SIXTH, SECOND, NL, InX, EpiX, InY, EpiY>;
+    const size_t smem = smem_bytes<P1, P2, SECOND, NL>();
     static bool attr = false;  // one flag per kernel instantiation
     if (!attr) {
         cudaError_t e =
@@ -1253,7 +1306,8 @@ cudaError_t launch_xy_t(InX inx, EpiX ex, InY iny, EpiY ey, int nx, int ny, int 
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    const LineGeo gx = make_geo(nx, ny, 0, H), gy = make_geo(nx, ny, 1, H, walls_y);
+    const LineGeo gx = make_geo(nx, ny, 0, H, false, NL),
+                  gy = make_geo(nx, ny, 1, H, walls_y, NL);
     const int nbx = gx.ngroups * gx.nwin;
     const unsigned blocks = (unsigned)(nbx + gy.ngroups * gy.nwin);
     // FP32 y-lines take their interior windows by tensor copies (a state block
@@ -1262,10 +1316,10 @@ cudaError_t launch_xy_t(InX inx, EpiX ex, InY iny, EpiY ey, int nx, int ny, int 
     std::memset(&tmy, 0, sizeof(tmy));
     int use_tma = 0;
     if (std::is_same<P1, PolF>::value && std::is_same<P2, PolF>::value && st)
-        use_tma = y_tensor_map(y_field(iny), nx, ny, &tmy) ? 1 : 0;
-    kern<<<blocks, kNL * 32, smem, s>>>(inx, gx, ex, iny, gy, ey, make_const<P1>(order),
-                                        make_const<PolF>(order), make_const<P2>(order), st, bump,
-                                        nbx, tmy, use_tma);
+        use_tma = y_tensor_map(y_field(iny), nx, ny, NL, &tmy) ? 1 : 0;
+    kern<<<blocks, NL * 32, smem, s>>>(inx, gx, ex, iny, gy, ey, make_const<P1>(order),
+                                       make_const<PolF>(order), make_const<P2>(order), st, bump,
+                                       nbx, tmy, use_tma);
     return cudaGetLastError();
 }
 
@@ -1274,11 +1328,21 @@ cudaError_t launch_xy(InX inx, EpiX ex, InY iny, EpiY ey, int nx, int ny, int or
                       double eps1, double eps2, DevState* st, int bump, cudaStream_t s,
                       bool walls_y = false) {
     const int H = halo(order, eps1, SECOND, eps2);
+    constexpr bool kF32 = std::is_same<P1, PolF>::value && std::is_same<P2, PolF>::value;
+    if constexpr (kF32) {
+        if ((long long)nx * ny <= kWideLinesMaxNodes) {
+            if (order == 6)
+                return launch_xy_t<P1, P2, true, SECOND, 16>(inx, ex, iny, ey, nx, ny, order, H,
+                                                             st, bump, walls_y, s);
+            return launch_xy_t<P1, P2, false, SECOND, 16>(inx, ex, iny, ey, nx, ny, order, H, st,
+                                                          bump, walls_y, s);
+        }
+    }
     if (order == 6)
-        return launch_xy_t<P1, P2, true, SECOND>(inx, ex, iny, ey, nx, ny, order, H, st, bump,
-                                                 walls_y, s);
-    return launch_xy_t<P1, P2, false, SECOND>(inx, ex, iny, ey, nx, ny, order, H, st, bump,
-                                              walls_y, s);
+        return launch_xy_t<P1, P2, true, SECOND, kNL>(inx, ex, iny, ey, nx, ny, order, H, st,
+                                                      bump, walls_y, s);
+    return launch_xy_t<P1, P2, false, SECOND, kNL>(inx, ex, iny, ey, nx, ny, order, H, st, bump,
+                                                   walls_y, s);
 }
 
 // dispatch on axis and scheme order
