@@ -13,16 +13,19 @@ What it finds, from the stored study (tests/golden/flat_coexistence.json,
 written by tests/golden/make_flat_coexistence.py from oracle/ only; one entry is
 recomputed here to tie the file to the code):
   * the liquid sits on Maxwell's density at every temperature (within 1e-4);
-  * the gas sits above Maxwell's density by an offset that falls as k^2
-    (measured order 1.9-2.2 between k 0.2, 0.1 and 0.05);
+  * the gas sits above Maxwell's density by an offset that falls as k^2: the
+    measured order is 1.9-2.3 between k 0.1 and 0.05 at every temperature from
+    T_r 0.6 down to 0.16;
   * at the paper's k = 0.1 that offset grows as the temperature falls:
-    0.027 decade at T_r 0.4, 0.12 at 0.3, 0.62 at 0.2, 2.7 decades at 0.16;
-    at T_r 0.2 and below the gas side of the interface no longer fits the
-    height-400 domain's gas layer (the gas at the slab's far edge is still on
-    the interface's tail: at T_r 0.2 a height of 800 gives 0.48 decade), so
-    there the offset is not in its asymptotic k^2 range either;
-  * the known gap: at k = 0.5 (the 1024x1024 drop workload's) the gas is 0.1 to 1.6 above Maxwell,
-    not within 1e-3 (xfail, strict).
+    0.027 decade at T_r 0.4, 0.12 at 0.3, 0.65 at 0.2 and 1.7 decades at 0.16
+    (where Fig. 4d shows the CS gas on Maxwell's curve down to a density ratio
+    above 1e14); at k = 0.05 it is 0.29 decade at T_r 0.2 and 1.0 at 0.16;
+  * below T_r ~ 0.25 the dilute gas is 1e9 and more times below the liquid, and
+    the solver's Newton step leaves it unresolved; those entries are finished
+    by the C oracle's time stepping to a relative residual below 1e-12 (and the
+    GPU's FP64 path, run long from a tanh start, ends on the same gas to 1e-9);
+  * the known gap: at k = 0.5 (the 1024x1024 drop workload's) the gas is 0.1 to
+    1.6 above Maxwell, not within 1e-3 (xfail, strict).
 """
 import json
 import math
@@ -34,7 +37,6 @@ import pytest
 from oracle import equilibrium as E
 from oracle import sim
 from oracle.eos import Eos
-
 
 
 def gold():
@@ -92,7 +94,7 @@ def test_stored_study_is_what_the_solver_gives():
 def test_liquid_on_maxwell_at_every_temperature():
     for e in gold()["curve_k0.1"] + gold()["k_series"]:
         assert abs(e["liq_offset"]) <= (1e-4 if e["k"] <= 0.2 else 2e-4), e
-        assert e["newton_residual"] < 1e-12, e
+        assert e["relative_residual"] < 1e-10, e  # every population, gas included
 
 
 def test_gas_offset_falls_as_k_squared():
@@ -108,8 +110,7 @@ def test_gas_offset_falls_as_k_squared():
         # order between the two finest spacings of each temperature
         k1, k2 = ks[0], ks[1]
         order = math.log(s[k2] / s[k1]) / math.log(k2 / k1)
-        if s[k2] < 0.5:  # in the asymptotic range
-            assert 1.8 <= order <= 2.3, (T_r, order, s)
+        assert 1.8 <= order <= 2.4, (T_r, order, s)
 
 
 def test_gas_offset_at_the_paper_k_grows_as_temperature_falls():
@@ -122,8 +123,8 @@ def test_gas_offset_at_the_paper_k_grows_as_temperature_falls():
     dec = {e["T_r"]: e["gas_offset_decades"] for e in curve}
     assert dec[0.8] < 1e-3 / math.log(10)
     assert 0.1 < dec[0.3] < 0.15
-    assert 0.5 < dec[0.2] < 0.75
-    assert dec[0.16] > 2.0
+    assert 0.6 < dec[0.2] < 0.7
+    assert 1.5 < dec[0.16] < 1.8
 
 
 @pytest.mark.xfail(strict=True, reason="known gap: at k = 0.5 (the 1024x1024 drop workload's k) the flat gas "
