@@ -669,6 +669,51 @@ def surrogate_demo():
             "cases": cases}
 
 
+def mlp_products(batches=(256, 4096, 32768), reps=50):
+    """The surrogate network's kernels alone: forward pass and Adam training
+    step at several batch sizes, with the forward and input-gradient products
+    on tcgen05 (the default) and on the mma.sync comparison kernel.
+    Algorithmic flops per sample: forward 2 (3*256 + 3*256^2); training step
+    three times that less the input layer's input gradient (2*3*256)."""
+    import torch
+    from paper_1906_09530_gb300 import Mlp, surrogate as SG
+    peak, how = load_bf16_peak()
+    fwd = 2 * (3 * 256 + 3 * 256 * 256)
+    train = 3 * fwd - 2 * 3 * 256
+    out = {"peak_tflops": peak, "peak_kind": how, "rows": []}
+    for B in batches:
+        net = Mlp(B)
+        net.set_params(SG.glorot_params(0))
+        g = torch.Generator(device="cuda").manual_seed(B)
+        x = torch.rand((B, 3), device="cuda", generator=g) * 2 - 1
+        t = torch.rand((B, 256), device="cuda", generator=g)
+        row = {"batch": B}
+        for tc in (True, False):
+            net.tcgen05 = tc
+            name = "tcgen05" if tc else "mma_sync"
+            for what, call, flops in (("forward", lambda: net.forward(x), fwd),
+                                      ("train_step", lambda: net.train_step(x, t, 1e-4), train)):
+                for _ in range(5):
+                    call()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record()
+                for _ in range(reps):
+                    call()
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / reps
+                tf = B * flops / (ms / 1e3) / 1e12
+                row[f"{what}_{name}_us"] = ms * 1e3
+                row[f"{what}_{name}_tflops"] = tf
+                row[f"{what}_{name}_frac"] = tf / peak
+            assert net.tcgen05 == tc  # no fall back happened
+        net.close()
+        out["rows"].append(row)
+    return out
+
+
 def windowed_equilibrium(step, sample, targets, tol, every, window, max_steps):
     """Steps until the means of the last `window` samples of every item are
     within tol (relative) of its target pair.  sample() returns one (gas,
@@ -890,6 +935,8 @@ def main():
     ap.add_argument("--no-equilibrium", action="store_true")
     ap.add_argument("--surrogate", action="store_true",
                     help="add the learned warm start's measurement (several minutes)")
+    ap.add_argument("--no-mlp", action="store_true",
+                    help="skip the surrogate network's product timings")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched-instances line")
     ap.add_argument("--no-large", action="store_true",
@@ -1067,6 +1114,8 @@ def main():
     if rank == 0 and not args.no_splash:
         line["splash"] = splash_config(args.precision)
         line["splash_paper"] = splash_paper_config()
+    if rank == 0 and not args.no_mlp:
+        line["mlp"] = mlp_products()
     if rank == 0 and args.surrogate:
         line["surrogate"] = surrogate_demo()
     if rank == 0 and not args.no_equilibrium:

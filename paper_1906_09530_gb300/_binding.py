@@ -126,6 +126,8 @@ def lib():
             "lbm_mlp_forward": (C.c_int, [_vp, _vp, _i32, _vp]),
             "lbm_mlp_loss_grad": (C.c_int, [_vp, _vp, _vp, _i32, _dp, _vp]),
             "lbm_mlp_train_step": (C.c_int, [_vp, _vp, _vp, _i32, C.c_float, _dp]),
+            "lbm_mlp_set_tcgen05": (C.c_int, [_vp, _i32]),
+            "lbm_mlp_tcgen05": (_i32, [_vp]),
             "lbm_mlp_free": (None, [_vp]),
             "lbm_strerror": (C.c_char_p, [C.c_int]),
             "lbm_free": (None, [_vp]),
@@ -518,6 +520,15 @@ class Mlp:
                                         lr, C.byref(loss) if want_loss else None),
                "lbm_mlp_train_step")
         return loss.value if want_loss else None
+
+    @property
+    def tcgen05(self):
+        """True while the forward and input-gradient products run on tcgen05."""
+        return lib().lbm_mlp_tcgen05(self.ctx) == 1
+
+    @tcgen05.setter
+    def tcgen05(self, on):
+        _check(lib().lbm_mlp_set_tcgen05(self.ctx, 1 if on else 0), "lbm_mlp_set_tcgen05")
 
     def close(self):
         if getattr(self, "ctx", None):

@@ -4,16 +4,19 @@
 // profile, trained and evaluated by the kernels of this file.
 //
 // Arithmetic: every matrix product runs on the tensor cores in BF16 with FP32
-// accumulation (mma.sync m16n8k16); master weights, Adam moments, biases,
-// activations kept for the backward pass, and the loss are FP32 (the loss sum
-// FP64).  One GEMM kernel serves all products through strides:
+// accumulation; master weights, Adam moments, biases, activations kept for the
+// backward pass, and the loss are FP32 (the loss sum FP64).  The products:
 //   forward            Z_l   = A_{l-1} W_l          [B x fan_in] [fan_in x fan_out]
 //   weight gradient    dW_l  = A_{l-1}^T D_l        [fan_in x B] [B x fan_out]
 //   input gradient     D_{l-1} = (D_l W_l^T) (1 - A_{l-1}^2)
-// with fused epilogues (bias + tanh, tanh derivative).  The products here are
-// at most 256 x 256 x batch, microseconds of work; the tile kernel stages its
-// operands in shared memory with the K index contiguous, so each fragment
-// register is one 32-bit shared load.
+// with fused epilogues (bias + tanh, tanh derivative).  The forward and
+// input-gradient products have 256 output columns and a batch of rows: they run
+// as tcgen05 MMAs of 128 x 256 x 16 with the accumulator in tensor memory and
+// the operands brought in by tensor copies (k_gemm_umma).  The weight gradient,
+// whose K is the batch, and any product whose tensor map cannot be made, use the
+// strided mma.sync tile kernel (k_gemm), which stages its operands in shared
+// memory with the K index contiguous.
+#include <cuda.h>  // CUtensorMap and its encoder's types (the encoder is fetched at run time)
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -149,6 +152,191 @@ __global__ void __launch_bounds__(128) k_gemm(GemmArgs g) {
             }
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core products on tcgen05 (5th-generation tensor cores, accumulator in
+// tensor memory): D[M x 256] = A[M x K] Bt[256 x K]^T, K = 16 or 256, BF16
+// operands, FP32 accumulation, with the epilogues of k_gemm.  They serve the
+// forward products (A = the layer input, Bt = the transposed weights) and the
+// input gradients (A = the backward signal, Bt = the weights as stored).
+//
+// A CTA of 4 warps owns 128 rows and all 256 columns.  Both operands are moved
+// into shared memory by tensor copies (TMA) in the K-major, unswizzled layout of
+// the tensor cores: core matrices of 8 rows x 8 elements (128 bytes), K-adjacent
+// core matrices 128 bytes apart, row-adjacent ones K/8 x 128 bytes apart.  A
+// 4-D tensor map (8 elements, 8 rows, K/8, rows/8) writes exactly that order.
+// One thread issues the K/16 MMAs of shape 128 x 256 x 16 into a 256-column
+// accumulator and commits them to an mbarrier; after a bounded wait each warp
+// reads its 32 rows back with tcgen05.ld and applies the epilogue.  A wait that
+// runs out sets the error word and the CTA frees its tensor memory and leaves.
+// ---------------------------------------------------------------------------
+constexpr int UM = 128, UN = 256;
+constexpr unsigned kUmmaSpins = 1u << 22;
+
+struct UmmaArgs {
+    int M, K;
+    int epi;
+    const float* bias;   // [256]
+    const float* aprev;  // [M][256] (EPI_TANH_BACK)
+    float* out32;        // [M][256]
+    __nv_bfloat16* out16;
+    int ld16;
+    int* err;            // set to 1 when a wait runs out
+};
+
+__device__ __forceinline__ unsigned su32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ bool umma_try_wait(uint64_t* bar) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(su32(bar))
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool umma_wait(uint64_t* bar) {
+    for (unsigned i = 0; i < kUmmaSpins; ++i)
+        if (umma_try_wait(bar)) return true;
+    return false;
+}
+// shared-memory matrix descriptor: start address, leading (K-adjacent) and
+// stride (row-adjacent) byte offsets, descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t umma_desc(unsigned addr, unsigned lbo, unsigned sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+__global__ void __launch_bounds__(128, 1)
+    k_gemm_umma(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
+                UmmaArgs g) {
+    extern __shared__ __align__(1024) unsigned char usm[];
+    unsigned char* As = usm;                          // UM x K bf16
+    unsigned char* Bs = usm + (size_t)UM * g.K * 2;   // UN x K bf16
+    __shared__ __align__(8) uint64_t bar[2];          // [0] operands arrived, [1] MMAs done
+    __shared__ uint32_t tbase;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * UM;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                         su32(&tbase)),
+                     "r"(UN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(su32(&bar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(su32(&bar[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = tbase;
+    const int KG = g.K / 8;
+    if (tid == 0) {
+        const unsigned bytes = (unsigned)((UM + UN) * g.K * 2);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(
+                         su32(&bar[0])),
+                     "r"(bytes)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(su32(As)),
+            "l"(reinterpret_cast<uint64_t>(&ta)), "r"(0), "r"(0), "r"(0), "r"(m0 / 8),
+            "r"(su32(&bar[0]))
+            : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(su32(Bs)),
+            "l"(reinterpret_cast<uint64_t>(&tb)), "r"(0), "r"(0), "r"(0), "r"(0),
+            "r"(su32(&bar[0]))
+            : "memory");
+    }
+    bool ok = umma_wait(&bar[0]);
+    ok = __syncthreads_and(ok) != 0;
+    bool mma_issued = false;
+    if (ok) {
+        // D f32 (bits 4-5), A and B bf16 (7-9, 10-12), both K-major, N >> 3 at bit 17,
+        // M >> 4 at bit 24
+        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                               ((uint32_t)(UN >> 3) << 17) | ((uint32_t)(UM >> 4) << 24);
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            for (int ks = 0; ks < g.K / 16; ++ks) {
+                const uint64_t da = umma_desc(su32(As) + ks * 256, 128, KG * 128);
+                const uint64_t db = umma_desc(su32(Bs) + ks * 256, 128, KG * 128);
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(da), "l"(db), "r"(idesc), "r"(ks > 0 ? 1u : 0u)
+                    : "memory");
+            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::
+                    "r"(su32(&bar[1]))
+                : "memory");
+        }
+        mma_issued = true;
+        ok = umma_wait(&bar[1]);
+        ok = __syncthreads_and(ok) != 0;
+    }
+    if (!ok) {
+        // a copy or the MMAs never completed: report, give what is in flight one
+        // more bounded wait, free the tensor memory and leave
+        if (tid == 0) atomicExch(g.err, 1);
+        umma_wait(&bar[0]);
+        if (mma_issued) umma_wait(&bar[1]);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (ok) {
+        const int row = m0 + warp * 32 + lane;
+        const bool live = row < g.M;
+        for (int c = 0; c < UN; c += 8) {
+            uint32_t v[8];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                  "=r"(v[6]), "=r"(v[7])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+            if (!live) continue;
+            float o[8];
+            __nv_bfloat16 h[8];
+            const long long base = (long long)row * UN + c;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                float x = __uint_as_float(v[j]);
+                if (g.epi == EPI_BIAS_TANH) {
+                    x = tanhf(x + g.bias[c + j]);
+                } else if (g.epi == EPI_BIAS) {
+                    x += g.bias[c + j];
+                } else if (g.epi == EPI_TANH_BACK) {
+                    const float ap = g.aprev[base + j];
+                    x *= 1.0f - ap * ap;
+                }
+                o[j] = x;
+                h[j] = __float2bfloat16_rn(x);
+            }
+            float4* o4 = reinterpret_cast<float4*>(g.out32 + base);
+            o4[0] = make_float4(o[0], o[1], o[2], o[3]);
+            o4[1] = make_float4(o[4], o[5], o[6], o[7]);
+            if (g.out16 && (g.epi == EPI_BIAS_TANH || g.epi == EPI_TANH_BACK))
+                *reinterpret_cast<uint4*>(g.out16 + (long long)row * g.ld16 + c) =
+                    *reinterpret_cast<const uint4*>(h);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                     "r"(UN)
+                     : "memory");
+}
+
 // x [B][3] FP32 -> BF16 [B][16], zero-padded
 __global__ void k_input(const float* __restrict__ x, __nv_bfloat16* __restrict__ x16, int B) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -157,20 +345,28 @@ __global__ void k_input(const float* __restrict__ x, __nv_bfloat16* __restrict__
     x16[i] = __float2bfloat16_rn(k < kIn ? x[b * kIn + k] : 0.0f);
 }
 
-// FP32 master weights -> BF16 copies ([fan_in padded][fan_out] for layer 0)
-__global__ void k_weights16(const float* __restrict__ p, __nv_bfloat16* __restrict__ w16) {
+// FP32 master weights -> BF16 copies ([fan_in padded][fan_out] for layer 0),
+// and the same transposed ([fan_out][fan_in padded]) for the tensor-core
+// products, whose second operand is K-major
+__global__ void k_weights16(const float* __restrict__ p, __nv_bfloat16* __restrict__ w16,
+                            __nv_bfloat16* __restrict__ w16t) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long n16 = (long long)kInPad * kW + 3LL * kW * kW;
     if (i >= n16) return;
     if (i < (long long)kInPad * kW) {
         const int k = (int)(i / kW), n = (int)(i - (long long)k * kW);
-        w16[i] = __float2bfloat16_rn(k < kIn ? p[k * kW + n] : 0.0f);
+        const __nv_bfloat16 v = __float2bfloat16_rn(k < kIn ? p[k * kW + n] : 0.0f);
+        w16[i] = v;
+        w16t[(long long)n * kInPad + k] = v;
         return;
     }
     const long long j = i - (long long)kInPad * kW;  // layers 1..3
     const int l = 1 + (int)(j / (kW * kW));
     const long long r = j - (long long)(l - 1) * kW * kW;
-    w16[i] = __float2bfloat16_rn(p[param_offset(l) + r]);
+    const int k = (int)(r / kW), n = (int)(r - (long long)k * kW);
+    const __nv_bfloat16 v = __float2bfloat16_rn(p[param_offset(l) + r]);
+    w16[i] = v;
+    w16t[(long long)kInPad * kW + (long long)(l - 1) * kW * kW + (long long)n * kW + k] = v;
 }
 
 // dL/dy = 2 (y - t) / (B N) (FP32 and BF16), and the squared-error sum
@@ -227,7 +423,10 @@ struct lbm_mlp {
     int dev, max_batch;
     cudaStream_t stream;
     float *p, *g, *m, *v;        // FP32 parameters, gradient, Adam moments
-    __nv_bfloat16* w16;          // BF16 weight copies, layer by layer
+    __nv_bfloat16* w16;          // BF16 weight copies, layer by layer ([fan_in][fan_out])
+    __nv_bfloat16* w16t;         // the same transposed ([fan_out][fan_in]; fan_in 16 for layer 0)
+    int* err;                    // device word: a tensor-core product's wait ran out
+    int* h_err;                  // pinned mirror
     __nv_bfloat16* x16;          // [max_batch][16]
     float* a32[kLayers];         // layer outputs, FP32 [B][256]
     __nv_bfloat16* a16[kLayers - 1];  // hidden outputs, BF16 (inputs of the next product)
@@ -238,6 +437,7 @@ struct lbm_mlp {
     double* sse;                 // device scalar
     double* h_sse;               // pinned mirror
     long long step;
+    bool tensor_cores;           // forward and input-gradient products by tcgen05
 };
 
 namespace {
@@ -245,10 +445,15 @@ namespace {
 size_t al(size_t v) { return (v + 255) / 256 * 256; }
 
 struct MlpLayout {
-    size_t p, g, m, v, w16, x16, a32, a16, d32, d16, e32, e16, sse, total;
+    size_t p, g, m, v, w16, w16t, x16, a32, a16, d32, d16, e32, e16, sse, err, total;
 };
 
-MlpLayout mlp_layout(int B) {
+// Rows of the batch-sized buffers: a multiple of 8, so that the tensor copies of
+// 8-row core matrices stay inside the buffers.
+int rows_of(int B) { return (B + 7) / 8 * 8; }
+
+MlpLayout mlp_layout(int B0) {
+    const int B = rows_of(B0);
     MlpLayout L;
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -261,6 +466,7 @@ MlpLayout mlp_layout(int B) {
     L.m = take(kParams * 4);
     L.v = take(kParams * 4);
     L.w16 = take(((size_t)kInPad * kW + 3ull * kW * kW) * 2);
+    L.w16t = take(((size_t)kInPad * kW + 3ull * kW * kW) * 2);
     L.x16 = take((size_t)B * kInPad * 2);
     L.a32 = take((size_t)kLayers * B * kW * 4);
     L.a16 = take((size_t)(kLayers - 1) * B * kW * 2);
@@ -269,6 +475,7 @@ MlpLayout mlp_layout(int B) {
     L.e32 = take((size_t)B * kW * 4);
     L.e16 = take((size_t)B * kW * 2);
     L.sse = take(8);
+    L.err = take(4);
     L.total = o;
     return L;
 }
@@ -288,8 +495,86 @@ cudaError_t gemm(const GemmArgs& g, cudaStream_t s) {
 const __nv_bfloat16* w16_of(const lbm_mlp* n, int l) {
     return l == 0 ? n->w16 : n->w16 + (size_t)kInPad * kW + (size_t)(l - 1) * kW * kW;
 }
+const __nv_bfloat16* w16t_of(const lbm_mlp* n, int l) {
+    return l == 0 ? n->w16t : n->w16t + (size_t)kInPad * kW + (size_t)(l - 1) * kW * kW;
+}
 
-lbm_status sync(lbm_mlp* n) { return cudaStreamSynchronize(n->stream) == cudaSuccess ? LBM_OK : LBM_ECUDA; }
+// Drain the stream; a tensor-core product whose bounded wait ran out since the
+// last check makes this LBM_ETIMEOUT (and the word is cleared).
+lbm_status sync(lbm_mlp* n) {
+    if (cudaMemcpyAsync(n->h_err, n->err, sizeof(int), cudaMemcpyDeviceToHost, n->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(n->stream) != cudaSuccess)
+        return LBM_ECUDA;
+    if (*n->h_err) {
+        *n->h_err = 0;
+        if (cudaMemsetAsync(n->err, 0, sizeof(int), n->stream) != cudaSuccess) return LBM_ECUDA;
+        return LBM_ETIMEOUT;
+    }
+    return LBM_OK;
+}
+
+// ---- tensor-core products: host side ----
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encoder() {
+    static EncodeTiledFn fn = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        looked = true;
+    }
+    return fn;
+}
+
+// Tensor map of a BF16 matrix [rows][K] (row stride K) that a box of `box_rows`
+// rows lands in shared memory as K-major core matrices: the 4-D view (8
+// elements, 8 rows, K/8, rows/8) with strides (2, 2K, 16, 16K) bytes.  The
+// matrix's allocation must hold rows rounded up to 8.
+bool core_matrix_map(const __nv_bfloat16* A, int rows, int K, int box_rows, CUtensorMap* m) {
+    const EncodeTiledFn enc = encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[4] = {8, 8, (cuuint64_t)(K / 8), (cuuint64_t)((rows + 7) / 8)};
+    const cuuint64_t strides[3] = {(cuuint64_t)K * 2, 16, (cuuint64_t)K * 16};
+    const cuuint32_t box[4] = {8, 8, (cuuint32_t)(K / 8), (cuuint32_t)(box_rows / 8)};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(A), dims,
+               strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
+// D[M x 256] = A[M x K] Bt[256 x K]^T on the tensor cores, with the epilogue of g;
+// false when no tensor map can be made (the caller then uses k_gemm)
+bool gemm_tc(const __nv_bfloat16* A, const __nv_bfloat16* Bt, UmmaArgs g, cudaStream_t s,
+             cudaError_t* e) {
+    CUtensorMap ta, tb;
+    if (!core_matrix_map(A, g.M, g.K, UM, &ta) || !core_matrix_map(Bt, UN, g.K, UN, &tb))
+        return false;
+    const size_t smem = (size_t)(UM + UN) * g.K * 2;
+    static unsigned long long attr_set = 0;  // one bit per device
+    int dev = 0;
+    *e = cudaGetDevice(&dev);
+    if (*e != cudaSuccess) return true;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(attr_set & bit)) {
+        *e = cudaFuncSetAttribute(k_gemm_umma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)((UM + UN) * kW * 2));
+        if (*e != cudaSuccess) return true;
+        attr_set |= bit;
+    }
+    k_gemm_umma<<<(g.M + UM - 1) / UM, 128, smem, s>>>(ta, tb, g);
+    *e = cudaGetLastError();
+    return true;
+}
 
 // forward pass of a batch whose inputs are in x (device FP32 [B][3]); the
 // output is a32[3]
@@ -298,6 +583,23 @@ lbm_status forward(lbm_mlp* n, const float* x, int B) {
     k_input<<<(B * kInPad + 255) / 256, 256, 0, s>>>(x, n->x16, B);
     CK(cudaGetLastError());
     for (int l = 0; l < kLayers; ++l) {
+        if (n->tensor_cores) {
+            UmmaArgs u{};
+            u.M = B;
+            u.K = l == 0 ? kInPad : kW;
+            u.epi = l < kLayers - 1 ? EPI_BIAS_TANH : EPI_BIAS;
+            u.bias = n->p + param_offset(l) + (long long)kFanIn[l] * kFanOut[l];
+            u.out32 = n->a32[l];
+            u.out16 = l < kLayers - 1 ? n->a16[l] : nullptr;
+            u.ld16 = kW;
+            u.err = n->err;
+            cudaError_t e = cudaSuccess;
+            if (gemm_tc(l == 0 ? n->x16 : n->a16[l - 1], w16t_of(n, l), u, s, &e)) {
+                CK(e);
+                continue;
+            }
+            n->tensor_cores = false;  // no tensor map: the mma.sync kernel from here on
+        }
         GemmArgs g{};
         g.A = l == 0 ? n->x16 : n->a16[l - 1];
         g.sam = l == 0 ? kInPad : kW;
@@ -351,7 +653,29 @@ lbm_status backward(lbm_mlp* n, const float* x, const float* t, int B) {
         k_bias_grad<<<(fo + 127) / 128, 128, 0, s>>>(d32, B, fo, gb);
         CK(cudaGetLastError());
         if (l == 0) break;
-        // D_{l-1} = (D W_l^T) (1 - A_{l-1}^2)
+        // D_{l-1} = (D W_l^T) (1 - A_{l-1}^2): K-major operands are D [B][fo] and
+        // W_l itself ([fi][fo])
+        bool done = false;
+        if (n->tensor_cores) {
+            UmmaArgs u{};
+            u.M = B;
+            u.K = fo;
+            u.epi = EPI_TANH_BACK;
+            u.aprev = n->a32[l - 1];
+            u.out32 = e32;
+            u.out16 = e16;
+            u.ld16 = fi;
+            u.err = n->err;
+            cudaError_t e = cudaSuccess;
+            done = gemm_tc(d16, w16_of(n, l), u, s, &e);
+            if (done) CK(e);
+            else n->tensor_cores = false;
+        }
+        if (done) {
+            std::swap(d32, e32);
+            std::swap(d16, e16);
+            continue;
+        }
         GemmArgs h{};
         h.A = d16;
         h.sam = fo;
@@ -377,7 +701,7 @@ lbm_status backward(lbm_mlp* n, const float* x, const float* t, int B) {
 
 lbm_status refresh_w16(lbm_mlp* n) {
     const long long n16 = (long long)kInPad * kW + 3LL * kW * kW;
-    k_weights16<<<(unsigned)((n16 + 255) / 256), 256, 0, n->stream>>>(n->p, n->w16);
+    k_weights16<<<(unsigned)((n16 + 255) / 256), 256, 0, n->stream>>>(n->p, n->w16, n->w16t);
     CK(cudaGetLastError());
     return LBM_OK;
 }
@@ -416,17 +740,25 @@ lbm_status lbm_mlp_init(lbm_mlp** out, int32_t max_batch, void* d_ws, size_t byt
     n->v = (float*)(w + L.v);
     n->w16 = (__nv_bfloat16*)(w + L.w16);
     n->x16 = (__nv_bfloat16*)(w + L.x16);
-    for (int l = 0; l < kLayers; ++l)
-        n->a32[l] = (float*)(w + L.a32) + (size_t)l * max_batch * kW;
+    const size_t R = (size_t)rows_of(max_batch);
+    for (int l = 0; l < kLayers; ++l) n->a32[l] = (float*)(w + L.a32) + (size_t)l * R * kW;
     for (int l = 0; l < kLayers - 1; ++l)
-        n->a16[l] = (__nv_bfloat16*)(w + L.a16) + (size_t)l * max_batch * kW;
+        n->a16[l] = (__nv_bfloat16*)(w + L.a16) + (size_t)l * R * kW;
+    n->w16t = (__nv_bfloat16*)(w + L.w16t);
+    n->err = (int*)(w + L.err);
     n->d32 = (float*)(w + L.d32);
     n->d16 = (__nv_bfloat16*)(w + L.d16);
     n->e32 = (float*)(w + L.e32);
     n->e16 = (__nv_bfloat16*)(w + L.e16);
     n->sse = (double*)(w + L.sse);
     n->step = 0;
+    n->tensor_cores = true;
     if (cudaMallocHost((void**)&n->h_sse, sizeof(double)) != cudaSuccess) {
+        delete n;
+        return LBM_ECUDA;
+    }
+    if (cudaMallocHost((void**)&n->h_err, sizeof(int)) != cudaSuccess) {
+        cudaFreeHost(n->h_sse);
         delete n;
         return LBM_ECUDA;
     }
@@ -438,10 +770,19 @@ lbm_status lbm_mlp_init(lbm_mlp** out, int32_t max_batch, void* d_ws, size_t byt
     return LBM_OK;
 }
 
+lbm_status lbm_mlp_set_tcgen05(lbm_mlp* n, int32_t on) {
+    if (!n || (on != 0 && on != 1)) return LBM_EINVAL;
+    n->tensor_cores = on == 1;
+    return LBM_OK;
+}
+
+int32_t lbm_mlp_tcgen05(const lbm_mlp* n) { return n ? (n->tensor_cores ? 1 : 0) : -1; }
+
 void lbm_mlp_free(lbm_mlp* n) {
     if (!n) return;
     cudaSetDevice(n->dev);
     if (n->h_sse) cudaFreeHost(n->h_sse);
+    if (n->h_err) cudaFreeHost(n->h_err);
     delete n;
 }
 

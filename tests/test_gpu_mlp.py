@@ -69,6 +69,16 @@ def _scales(p, x, t):
     return y, sy, g, sg
 
 
+def test_paths_agree_closely(cuda):
+    """tcgen05 and mma.sync take the same BF16 operands and accumulate in FP32:
+    their outputs differ only by the order of the FP32 additions."""
+    net, p, x, t, dx, dt = _setup(cuda, 300)
+    y_tc = net.forward(dx).cpu().numpy()
+    net.tcgen05 = False
+    y_ms = net.forward(dx).cpu().numpy()
+    assert np.abs(y_tc - y_ms).max() <= 2e-3 * np.abs(y_ms).max()
+
+
 def test_params_round_trip(cuda):
     net, p, *_ = _setup(cuda, 8)
     assert np.array_equal(net.get_params(), p)
@@ -83,20 +93,41 @@ def test_forward_matches_oracle(cuda, B):
     assert _rel(y, y_ref) <= 2e-2
 
 
-@pytest.mark.parametrize("B", [1, 37, 300])
-def test_forward_entrywise(cuda, B):
-    """Every output entry within C_BOUND BF16 scales of the rounded oracle."""
+def test_tcgen05_path_in_use(cuda):
+    """The forward and input-gradient products run on tcgen05 by default, and
+    the switch to the mma.sync comparison kernel is the caller's to make."""
+    net, p, x, t, dx, dt = _setup(cuda, 8)
+    assert net.tcgen05
+    net.forward(dx)
+    net.loss_grad(dx, dt)
+    assert net.tcgen05  # no fall back: both tensor maps were made
+    net.tcgen05 = False
+    assert not net.tcgen05
+    net.tcgen05 = True
+    assert net.tcgen05
+
+
+@pytest.mark.parametrize("tc", [True, False], ids=["tcgen05", "mma_sync"])
+@pytest.mark.parametrize("B", [1, 7, 37, 128, 129, 300, 512])
+def test_forward_entrywise(cuda, B, tc):
+    """Every output entry within C_BOUND BF16 scales of the rounded oracle: one
+    row, a part of a core matrix (7), one and several 128-row tiles with
+    ragged tails, and the largest batch."""
     net, p, x, t, dx, dt = _setup(cuda, B)
+    net.tcgen05 = tc
     y = net.forward(dx).cpu().numpy().astype(np.float64)
     y_ref, s, _, _ = _scales(p, x.astype(np.float64), t.astype(np.float64))
     ratio = np.abs(y - y_ref) / s
     assert ratio.max() <= C_BOUND, (ratio.max(), np.unravel_index(ratio.argmax(), ratio.shape))
 
 
-def test_gradient_entrywise(cuda):
+@pytest.mark.parametrize("tc", [True, False], ids=["tcgen05", "mma_sync"])
+@pytest.mark.parametrize("B", [7, 200, 512])
+def test_gradient_entrywise(cuda, B, tc):
     """Every gradient entry, weights and biases of all four layers, within
     C_BOUND BF16 scales of the rounded oracle's chain rule."""
-    net, p, x, t, dx, dt = _setup(cuda, 200)
+    net, p, x, t, dx, dt = _setup(cuda, B)
+    net.tcgen05 = tc
     _, g = net.loss_grad(dx, dt)
     g = g.cpu().numpy().astype(np.float64)
     _, _, g_ref, sg = _scales(p, x.astype(np.float64), t.astype(np.float64))
