@@ -937,6 +937,9 @@ def main():
                     help="add the learned warm start's measurement (several minutes)")
     ap.add_argument("--no-mlp", action="store_true",
                     help="skip the surrogate network's product timings")
+    ap.add_argument("--mlp-batches", default="256,4096,32768",
+                    help="batch sizes of the network timings (comma-separated)")
+    ap.add_argument("--mlp-reps", type=int, default=50)
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched-instances line")
     ap.add_argument("--no-large", action="store_true",
@@ -1115,7 +1118,8 @@ def main():
         line["splash"] = splash_config(args.precision)
         line["splash_paper"] = splash_paper_config()
     if rank == 0 and not args.no_mlp:
-        line["mlp"] = mlp_products()
+        line["mlp"] = mlp_products(tuple(int(b) for b in args.mlp_batches.split(",")),
+                                   args.mlp_reps)
     if rank == 0 and args.surrogate:
         line["surrogate"] = surrogate_demo()
     if rank == 0 and not args.no_equilibrium:

@@ -347,9 +347,10 @@ void lbm_batch_free(lbm_batch *b);
  * layers, linear output) that maps (T_r, kappa-hat, k), scaled by the caller, to
  * a 256-point equilibrium interface profile.  Every matrix product runs on the
  * tensor cores in BF16 with FP32 accumulation; master weights, Adam moments,
- * activations and the gradient are FP32.  The forward and input-gradient
- * products (256 output columns) are tcgen05 MMAs with the accumulator in tensor
- * memory; the weight gradient uses mma.sync tiles.  A tcgen05 product whose
+ * activations and the gradient are FP32.  The products are tcgen05 MMAs with
+ * the accumulator in tensor memory (the weight gradient split over the batch
+ * and its partials added in a fixed order, so results do not depend on timing);
+ * an mma.sync kernel is kept as the comparison point.  A tcgen05 product whose
  * bounded wait runs out sets an error word that the next call that waits for
  * the stream (set/get_params, a loss read) reports as LBM_ETIMEOUT.  Loss: mean squared error over the
  * batch and the 256 outputs.  Training: Adam (beta1 0.9, beta2 0.999, eps 1e-8,
@@ -382,11 +383,10 @@ lbm_status lbm_mlp_loss_grad(lbm_mlp *net, const float *d_x, const float *d_t, i
 /* One Adam step with learning rate lr > 0 on the batch (x, t). */
 lbm_status lbm_mlp_train_step(lbm_mlp *net, const float *d_x, const float *d_t, int32_t batch,
                               float lr, double *h_loss);
-/* Product path of the forward and input-gradient products: 1 = tcgen05 (the
- * default), 0 = the mma.sync tile kernel (kept as the comparison point).
- * LBM_EINVAL for other values. */
+/* Product path: 1 = tcgen05 (the default), 0 = the mma.sync tile kernel (kept
+ * as the comparison point).  LBM_EINVAL for other values. */
 lbm_status lbm_mlp_set_tcgen05(lbm_mlp *net, int32_t on);
-/* 1 while those products run on tcgen05; 0 when switched off, or after a tensor
+/* 1 while the products run on tcgen05; 0 when switched off, or after a tensor
  * map could not be made (the library then falls back to mma.sync); -1 for NULL. */
 int32_t lbm_mlp_tcgen05(const lbm_mlp *net);
 /* Release the network (not the workspace or the stream); NULL is a no-op. */

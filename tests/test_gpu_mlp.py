@@ -38,7 +38,7 @@ def _setup(cuda, B, seed=4):
     x = rng.uniform(-1, 1, (B, 3)).astype(np.float32)
     t = (0.5 + 0.4 * np.sin(np.outer(x[:, 0] + 0.5 * x[:, 1] - x[:, 2], np.linspace(0, 3, 256)))
          ).astype(np.float32)
-    net = Mlp(max_batch=512)
+    net = Mlp(max_batch=max(512, B))
     net.set_params(p)
     return net, p, x, t, torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
 
@@ -79,6 +79,27 @@ def test_paths_agree_closely(cuda):
     assert np.abs(y_tc - y_ms).max() <= 2e-3 * np.abs(y_ms).max()
 
 
+def test_batch_size_changes(cuda):
+    """One network called with batch sizes in turn (the tensor maps are made
+    again for each new size) gives what fresh networks give, bit for bit."""
+    from paper_1906_09530_gb300 import Mlp
+    net, p, x, t, dx, dt = _setup(cuda, 300)
+    got = {}
+    for B in (300, 37, 300, 129):
+        got.setdefault(B, []).append(net.forward(dx[:B].contiguous()).cpu().numpy())
+        got.setdefault(("g", B), []).append(
+            net.loss_grad(dx[:B].contiguous(), dt[:B].contiguous())[1].cpu().numpy())
+    for B in (300, 37, 129):
+        fresh = Mlp(max_batch=512)
+        fresh.set_params(p)
+        y = fresh.forward(dx[:B].contiguous()).cpu().numpy()
+        g = fresh.loss_grad(dx[:B].contiguous(), dt[:B].contiguous())[1].cpu().numpy()
+        for a in got[B]:
+            assert np.array_equal(a, y)
+        for a in got[("g", B)]:
+            assert np.array_equal(a, g)
+
+
 def test_params_round_trip(cuda):
     net, p, *_ = _setup(cuda, 8)
     assert np.array_equal(net.get_params(), p)
@@ -108,7 +129,7 @@ def test_tcgen05_path_in_use(cuda):
 
 
 @pytest.mark.parametrize("tc", [True, False], ids=["tcgen05", "mma_sync"])
-@pytest.mark.parametrize("B", [1, 7, 37, 128, 129, 300, 512])
+@pytest.mark.parametrize("B", [1, 7, 37, 128, 129, 300, 512, 40000])
 def test_forward_entrywise(cuda, B, tc):
     """Every output entry within C_BOUND BF16 scales of the rounded oracle: one
     row, a part of a core matrix (7), one and several 128-row tiles with
@@ -122,7 +143,7 @@ def test_forward_entrywise(cuda, B, tc):
 
 
 @pytest.mark.parametrize("tc", [True, False], ids=["tcgen05", "mma_sync"])
-@pytest.mark.parametrize("B", [7, 200, 512])
+@pytest.mark.parametrize("B", [7, 200, 512, 5000])
 def test_gradient_entrywise(cuda, B, tc):
     """Every gradient entry, weights and biases of all four layers, within
     C_BOUND BF16 scales of the rounded oracle's chain rule."""
