@@ -669,6 +669,50 @@ def surrogate_demo():
             "cases": cases}
 
 
+def collide_forms(sizes=(1024, 2048, 4096), reps=50):
+    """The mixed collide-stream pass alone in each of its forms (sliding window,
+    row ring with 8, 16 or 32 rows a block, the default choice) on the bench drop
+    at each size: CUDA-event times of the pass (lbm_step_timed), the L2 flushed
+    before every step as in the main timing.  88 algorithmic bytes a node (nine FP32 populations and
+    the force read and written back, the density pair written)."""
+    import numpy as np
+    import torch
+    import paper_1906_09530_gb300 as P
+    from paper_1906_09530_gb300 import workloads as W
+    peak, how = load_peaks()
+    # the main timing's flush: dirty lines written, then evicted by a clean read,
+    # so the timed pass pays no write-back of the flush itself
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    clean = torch.zeros(128 << 20, dtype=torch.float32, device="cuda")
+    out = {"peak_GB/s": peak, "peak_kind": how, "alg_bytes_per_node": 88, "rows": []}
+    for size in sizes:
+        w = dict(WORKLOAD)
+        sc = size / w["nx"]
+        w.update(nx=size, ny=size, radius=w["radius"] * sc)
+        rg, rl = P.lbm_maxwell(w["T_r"])
+        sim = P.Simulation(w["nx"], w["ny"], w["T_r"], w["kappa"], w["tau"], w["k"],
+                           fd_order=w["order"], precision="mixed")
+        sim.set_fields(W.drop(w["nx"], w["ny"], rg, rl, w["radius"], w["width"]))
+        sim.step(4)
+        N = size * size
+        row = {"size": size}
+        for name, form in (("sliding_window", -1), ("ring_rows8", 8), ("ring_rows16", 16),
+                           ("ring_rows32", 32), ("default", 0)):
+            sim.set_collide_form(form)
+            ms = []
+            for _ in range(reps + 3):
+                flush.zero_()
+                clean.amax()
+                ms.append(sim.step_timed()[0])
+            us = float(np.mean(ms[3:])) * 1e3
+            row[name + "_us"] = round(us, 2)
+            row[name + "_frac"] = round(88 * N / (us / 1e6) / 1e9 / peak, 4)
+        row["default_is_ring"] = bool(sim.path_flags & 4)
+        sim.close()
+        out["rows"].append(row)
+    return out
+
+
 def mlp_products(batches=(256, 4096, 32768), reps=50):
     """The surrogate network's kernels alone: forward pass and Adam training
     step at several batch sizes, with the forward and input-gradient products
@@ -935,6 +979,8 @@ def main():
     ap.add_argument("--no-equilibrium", action="store_true")
     ap.add_argument("--surrogate", action="store_true",
                     help="add the learned warm start's measurement (several minutes)")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the collide-stream form comparison")
     ap.add_argument("--no-mlp", action="store_true",
                     help="skip the surrogate network's product timings")
     ap.add_argument("--mlp-batches", default="256,4096,32768",
@@ -1117,6 +1163,8 @@ def main():
     if rank == 0 and not args.no_splash:
         line["splash"] = splash_config(args.precision)
         line["splash_paper"] = splash_paper_config()
+    if rank == 0 and not args.no_forms and args.precision == "mixed":
+        line["collide_forms"] = collide_forms()
     if rank == 0 and not args.no_mlp:
         line["mlp"] = mlp_products(tuple(int(b) for b in args.mlp_batches.split(",")),
                                    args.mlp_reps)

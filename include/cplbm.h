@@ -169,9 +169,25 @@ lbm_status lbm_step_timed(lbm_ctx *ctx, float *pass_ms);
 /* How a mixed context runs its passes (chosen at lbm_init), as a bit set:
  * LBM_PATH_RHO_DF: the density lines are double-float (density ratio at or
  *   above 1e4, or LBM_PREC_MIXED_DF), else FP32 on the hi part.
+ * LBM_PATH_CS_RING: the collide-stream pass runs the row-ring kernel (see
+ *   lbm_set_collide_form).
  * 0 for FP64, -1 for NULL. */
-enum { LBM_PATH_RHO_DF = 2 };
+enum { LBM_PATH_RHO_DF = 2, LBM_PATH_CS_RING = 4 };
 int32_t lbm_path_flags(const lbm_ctx *ctx);
+
+/* Form of the mixed path's collide-stream pass (Eqs. 1-5 and streaming):
+ *   -1  the sliding-window kernel: one warp per 30 columns, three rows of
+ *       post-collision populations in registers, neighbours by warp shuffles;
+ *    0  the default: the row-ring kernel on grids of at least 2^23 nodes where
+ *       it applies (periodic, nx a multiple of 4 and at least 128), else the
+ *       sliding window (faster on smaller grids).  A row-ring block of 128
+ *       threads streams rows of 128 columns into a shared-memory ring by
+ *       16-byte asynchronous copies, several rows ahead, and writes 120 of them;
+ *   > 0 the row-ring kernel wherever it applies, with that many rows a block
+ *       (at most 4096).
+ * Both give bit-identical results; LBM_PATH_CS_RING in lbm_path_flags says
+ * which one runs.  LBM_EINVAL for other values. */
+lbm_status lbm_set_collide_form(lbm_ctx *ctx, int32_t ring_rows);
 
 /* Outputs of the current state to host FP64 [ny][nx] arrays, any may be NULL:
  * rho (Eq. 3), the velocity v = u + F/(2 rho) (Sec. 2, after Eq. 5) and the

@@ -99,6 +99,7 @@ def lib():
             "lbm_cfd_df": (C.c_int, [_vp, _vp, _vp, _vp, _i32, _i32, _i32, _i32, _vp]),
             "lbm_time": (C.c_int64, [_vp]),
             "lbm_path_flags": (C.c_int32, [_vp]),
+            "lbm_set_collide_form": (C.c_int, [_vp, _i32]),
             "lbm_failed_step": (C.c_int64, [_vp]),
             "lbm_set_timeout": (C.c_int, [_vp, C.c_double]),
             "lbm_set_wall_velocity": (C.c_int, [_vp, C.c_double, C.c_double]),
@@ -306,8 +307,15 @@ class Simulation:
 
     @property
     def path_flags(self):
-        """Bit set: LBM_PATH_RHO_DF (2) for double-float density lines; 0 for FP64."""
+        """Bit set: LBM_PATH_RHO_DF (2) for double-float density lines, LBM_PATH_CS_RING
+        (4) for the row-ring collide-stream kernel; 0 for FP64."""
         return lib().lbm_path_flags(self.ctx)
+
+    def set_collide_form(self, ring_rows):
+        """Mixed collide-stream form: -1 sliding window, 0 by grid size (the
+        default: the row ring from 2^23 nodes), > 0 row ring with that many rows
+        a block (lbm_set_collide_form)."""
+        _check(lib().lbm_set_collide_form(self.ctx, int(ring_rows)), "lbm_set_collide_form")
 
     @property
     def failed_step(self):

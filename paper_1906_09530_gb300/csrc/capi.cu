@@ -35,6 +35,8 @@ struct lbm_ctx {
     bool walls_y; // solid walls below row 0 and above row ny-1 (Sec. 5.5)
     Walls walls;  // the same, with the walls' x-velocities, for the collide pass
     bool mrt;     // MRT collision (Eq. 4) with the rates below
+    int ring_rows; // mixed collide-stream form: -1 sliding window, 0 by grid size,
+                   // > 0 row ring with that many rows a block
     MrtRates rates;
     double T, Tc, rhoc, kappa, tau, k;
     double mu_max;
@@ -163,7 +165,7 @@ lbm_status enqueue_collide(lbm_ctx* c, cudaStream_t s, int from) {
     else
         CK(launch_cs_mixed((const float*)c->f[from], (float*)c->f[to], c->m_Fx, c->m_Fy,
                            c->m_rh, c->m_rl, c->nx, c->ny, c->plane, c->phys.omega,
-                           c->mrt ? &c->rates : nullptr, c->dst, s, c->walls));
+                           c->mrt ? &c->rates : nullptr, c->dst, s, c->walls, c->ring_rows));
     return LBM_OK;
 }
 
@@ -323,6 +325,7 @@ lbm_status lbm_init(lbm_ctx** out, const lbm_grid* grid, const lbm_eos* eos, dou
     c->fd_order = opts->fd_order;
     c->rho_df = opts->prec == LBM_PREC_MIXED_DF;
     c->mrt = opts->collision == LBM_COLLIDE_MRT;
+    c->ring_rows = 0;
     c->walls_y = !grid->periodic_y;
     c->walls.on = c->walls_y;
     c->rates = MrtRates{opts->s_e, opts->s_eps, opts->s_q};
@@ -425,7 +428,20 @@ lbm_status lbm_set_wall_velocity(lbm_ctx* c, double u_bottom, double u_top) {
 int32_t lbm_path_flags(const lbm_ctx* c) {
     if (!c) return -1;
     if (c->prec == LBM_PREC_FP64) return 0;
-    return c->rho_df ? LBM_PATH_RHO_DF : 0;
+    int32_t f = c->rho_df ? LBM_PATH_RHO_DF : 0;
+    if (cs_ring_used(c->nx, c->ny, c->plane, c->f[0], c->m_Fx, c->m_Fy, c->walls_y,
+                     c->ring_rows) &&
+        cs_ring_used(c->nx, c->ny, c->plane, c->f[1], c->m_Fx, c->m_Fy, c->walls_y,
+                     c->ring_rows))
+        f |= LBM_PATH_CS_RING;
+    return f;
+}
+
+lbm_status lbm_set_collide_form(lbm_ctx* c, int32_t ring_rows) {
+    if (!c || ring_rows < -1 || ring_rows > 4096) return LBM_EINVAL;
+    c->ring_rows = ring_rows;
+    drop_graphs(c);  // the captured collide launches hold the old form
+    return LBM_OK;
 }
 
 int64_t lbm_time(const lbm_ctx* c) { return c ? c->t : -1; }

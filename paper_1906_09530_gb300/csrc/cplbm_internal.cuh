@@ -84,10 +84,16 @@ cudaError_t launch_f_from_double(const double* in, TF* f, size_t n, cudaStream_t
 cudaError_t launch_diag_final(const double* partials, int nparts, DevState* st, cudaStream_t s);
 
 // ---- mixed precision path (kernels_mixed.cu) ------------------------------
+// ring_rows: -1 = the sliding-window kernel; 0 = the row-ring kernel where the
+// grid allows it (periodic, nx a multiple of 4 and >= 128, aligned planes), with
+// its default rows a block; > 0 = the row-ring kernel with that many rows a block
 cudaError_t launch_cs_mixed(const float* fin, float* fout, const float* Fx, const float* Fy,
                             float* rh, float* rl, int nx, int ny, size_t plane, double omega,
                             const MrtRates* mrt, DevState* st, cudaStream_t s,
-                            const Walls& walls = Walls());
+                            const Walls& walls = Walls(), int ring_rows = -1);
+// whether launch_cs_mixed with these arguments runs the row-ring kernel
+bool cs_ring_used(int nx, int ny, size_t plane, const void* fin, const void* Fx,
+                  const void* Fy, bool walls, int ring_rows);
 cudaError_t launch_init_mixed(const double* rho, const double* ux, const double* uy, float* f,
                               float* rh, float* rl, int nx, int ny, size_t plane,
                               cudaStream_t s);

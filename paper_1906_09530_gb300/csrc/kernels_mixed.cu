@@ -175,6 +175,129 @@ __global__ void __launch_bounds__(kSwWarps * 32, 10) k_cs_mixed_sw_walls(CsArgs 
     cs_mixed_body<MRT, true>(a, blockIdx.x * kSwWarps + (threadIdx.x >> 5));
 }
 
+// ---------------------------------------------------------------------------
+// Pass 1, mixed, row-ring form (periodic grids, nx a multiple of 4 and at least
+// kRingT): a block of kRingT threads owns the kRingW destination columns
+// [x0, x0 + kRingW), x0 = kRingW s, and a segment of rows [y0, y1); thread t
+// stands for column x0 - 4 + t (periodically).  The raw rows y0 - 1 .. y1 (nine
+// populations and the two force components, 128 columns from the 16-byte-aligned
+// column x0 - 4) stream into a ring of kRingD row slots in shared memory, kRingD
+// - 1 rows ahead of use, as 16-byte asynchronous copies: 352 pieces a row, three
+// per thread, each piece four columns of one plane (nx a multiple of 4 puts every
+// periodic seam on a piece boundary).  Every thread collides its column of the
+// next row from the ring into a ring of post-collision rows; after a block
+// barrier the threads of columns x0 .. x0 + kRingW - 1 gather row y from rows
+// y - 1, y, y + 1 and columns x - 1, x, x + 1 and write it.  The collision and
+// the gather are the sliding-window kernel's (same rounding), so the results are
+// bit-identical; what changes is how many rows are in flight per thread and that
+// no halo lane is wasted per warp.
+// ---------------------------------------------------------------------------
+constexpr int kRingT = 128, kRingW = kRingT - 8, kRingD = 5;
+constexpr int kRingPieces = 11 * kRingT / 4;  // 16-byte pieces a row
+constexpr int kRingPer = (kRingPieces + kRingT - 1) / kRingT;
+
+__device__ __forceinline__ void ring_cp16(float* dst, const float* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(
+                     (unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void ring_commit() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void ring_wait_groups() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <bool MRT>
+__global__ void __launch_bounds__(kRingT) k_cs_mixed_ring(CsArgs a) {
+    __shared__ __align__(16) float raw[kRingD][11 * kRingT];
+    // three post-collision rows: row r overwrites row r - 3, whose last reader
+    // (the gather of row r - 2) finished before the barrier that precedes it
+    __shared__ __align__(16) float post[3][9][kRingT];
+    const int t = threadIdx.x;
+    const int strip = blockIdx.x % a.nstrips, seg = blockIdx.x / a.nstrips;
+    const int x0 = strip * kRingW, xa = x0 - 4;
+    const int y0 = seg * a.rows, y1 = min(y0 + a.rows, a.ny);
+    const int R = y1 - y0 + 2;  // rows y0 - 1 .. y1
+    const int nx = a.nx, ny = a.ny;
+    const size_t plane = a.plane;
+    // this thread's pieces: plane, source column (wrapped), offset in a slot
+    const float* src[kRingPer];
+    int off[kRingPer];
+#pragma unroll
+    for (int j = 0; j < kRingPer; ++j) {
+        const int k = t + j * kRingT;
+        const int p = k < kRingPieces ? k / (kRingT / 4) : 0;
+        const int c = k - p * (kRingT / 4);
+        const float* base = p < 9 ? a.fin + (size_t)p * plane : (p == 9 ? a.Fx : a.Fy);
+        src[j] = base + wrap_near(xa + 4 * c, nx);
+        off[j] = k < kRingPieces ? p * kRingT + 4 * c : -1;
+    }
+    auto issue = [&](int r) {  // raw row y0 - 1 + r into slot r % kRingD
+        const size_t row = (size_t)wrap_near(y0 - 1 + r, ny) * nx;
+        float* slot = raw[r % kRingD];
+#pragma unroll
+        for (int j = 0; j < kRingPer; ++j)
+            if (off[j] >= 0) ring_cp16(slot + off[j], src[j] + row);
+    };
+#pragma unroll
+    for (int r = 0; r < kRingD; ++r) {
+        if (r < R) issue(r);
+        ring_commit();  // one group a row, empty past the end, so the count stays uniform
+    }
+    const int xo = xa + t;  // the column this thread writes (threads 4 .. kRingT - 5)
+    const bool writer = t >= 4 && t < kRingT - 4 && xo < nx;
+    bool ok = true;
+    for (int r = 0; r < R; ++r) {
+        if (r >= 1) {
+            // slot (r - 1) % kRingD was read by every thread before the last barrier
+            if (r - 1 + kRingD < R) issue(r - 1 + kRingD);
+            ring_commit();
+        }
+        ring_wait_groups<kRingD - 1>();  // this thread's pieces of row r have landed
+        __syncthreads();                 // and everyone's
+        {
+            float f[9];
+            const float* w = raw[r % kRingD];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) f[i] = w[i * kRingT + t];
+            const float fx = w[9 * kRingT + t], fy = w[10 * kRingT + t];
+            if constexpr (MRT)
+                ok &= collide_mrt<float>(f, fx, fy, a.omega, FLT_MAX, a.se, a.seps, a.sq);
+            else
+                ok &= collide_pairs<float>(f, fx, fy, a.omega, FLT_MAX);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) post[r % 3][i][t] = f[i];
+        }
+        __syncthreads();
+        if (r >= 2 && writer) {
+            // row y = y0 + r - 2 from rows y - 1 (A), y (B), y + 1 (C); e = (ex, ey)
+            // comes from row y - ey, column x - ex
+            const int A = (r - 2) % 3, B = (r - 1) % 3, C = r % 3;
+            float g[9];
+            g[0] = post[B][0][t];
+            g[1] = post[B][1][t - 1];
+            g[2] = post[A][2][t];
+            g[3] = post[B][3][t + 1];
+            g[4] = post[C][4][t];
+            g[5] = post[A][5][t - 1];
+            g[6] = post[A][6][t + 1];
+            g[7] = post[C][7][t + 1];
+            g[8] = post[C][8][t - 1];
+            const size_t n = (size_t)(y0 + r - 2) * nx + xo;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) a.fout[i * plane + n] = g[i];
+            const df rr = sum9_exact(g);
+            a.rh[n] = rr.hi;
+            a.rl[n] = rr.lo;
+        }
+    }
+    ring_wait_groups<0>();
+    if (!ok) raise_flag(a.st, FLAG_RHO, a.st->t);
+}
+
 // Batched: block b belongs to instance map[b]; its warps continue that
 // instance's warp numbering from the instance's first block.  Held to 48
 // registers like the lone kernel (reading the instance's arguments took it to
@@ -357,6 +480,28 @@ CsArgs cs_mixed_args(const float* fin, float* fout, const float* Fx, const float
     return a;
 }
 
+// Below this many nodes the sliding window is faster (1024^2: 20.5 us against
+// 22.5; 2048^2: 65.5 against 67.5; its 40 warps an SM hide latency better than
+// the ring's 20 when the grid is a wave or two of blocks); at and above it the
+// ring is (4096^2: 240 us against 263).
+constexpr long long kRingMinNodes = 1ll << 23;
+
+bool cs_ring_fits(const CsArgs& a) {
+    auto al16 = [](const void* p) { return ((uintptr_t)p & 15u) == 0; };
+    return !a.walls && a.nx % 4 == 0 && a.nx >= kRingT && a.plane % 4 == 0 && al16(a.fin) &&
+           al16(a.Fx) && al16(a.Fy);
+}
+
+// Row-ring arguments: strips of kRingW columns; `rows` rows a block (0: 8, the
+// fastest of 8, 16 and 32 at 1024^2 and 4096^2)
+CsArgs cs_ring_args(CsArgs a, int rows) {
+    a.nstrips = (a.nx + kRingW - 1) / kRingW;
+    if (rows <= 0) rows = 8;
+    a.rows = rows;
+    a.nseg = (a.ny + rows - 1) / rows;
+    return a;
+}
+
 int cs_mixed_blocks(const CsArgs& a) {
     const long long warps = (long long)a.nstrips * a.nseg;
     return (int)((warps + kSwWarps - 1) / kSwWarps);
@@ -378,9 +523,32 @@ cudaError_t launch_cs_mixed_args(const CsArgs& a, cudaStream_t s) {
 cudaError_t launch_cs_mixed(const float* fin, float* fout, const float* Fx, const float* Fy,
                             float* rh, float* rl, int nx, int ny, size_t plane, double omega,
                             const MrtRates* mrt, DevState* st, cudaStream_t s,
-                            const Walls& walls) {
-    return launch_cs_mixed_args(
-        cs_mixed_args(fin, fout, Fx, Fy, rh, rl, nx, ny, plane, omega, mrt, st, 0, walls), s);
+                            const Walls& walls, int ring_rows) {
+    const CsArgs a =
+        cs_mixed_args(fin, fout, Fx, Fy, rh, rl, nx, ny, plane, omega, mrt, st, 0, walls);
+    if (!cs_ring_used(nx, ny, plane, fin, Fx, Fy, walls.on, ring_rows))
+        return launch_cs_mixed_args(a, s);
+    const CsArgs r = cs_ring_args(a, ring_rows);
+    const unsigned nb = (unsigned)(r.nstrips * r.nseg);
+    if (r.mrt)
+        k_cs_mixed_ring<true><<<nb, kRingT, 0, s>>>(r);
+    else
+        k_cs_mixed_ring<false><<<nb, kRingT, 0, s>>>(r);
+    return cudaGetLastError();
+}
+
+bool cs_ring_used(int nx, int ny, size_t plane, const void* fin, const void* Fx,
+                  const void* Fy, bool walls, int ring_rows) {
+    if (ring_rows < 0 || (ring_rows == 0 && (long long)nx * ny < kRingMinNodes)) return false;
+    CsArgs a{};
+    a.fin = (const float*)fin;
+    a.Fx = (const float*)Fx;
+    a.Fy = (const float*)Fy;
+    a.nx = nx;
+    a.ny = ny;
+    a.plane = plane;
+    a.walls = walls ? 1 : 0;
+    return cs_ring_fits(a);
 }
 
 cudaError_t launch_cs_mixed_batch(const CsBatchInst* d, const int* map, int nblocks, int from,
