@@ -8,7 +8,39 @@
 
 #include "../../include/cplbm.h"
 
+#include <utility>
+
 namespace cplbm {
+
+// ---- programmatic dependent launch (the single-instance mixed step) --------
+// The kernels of a mixed step are each about one wave at small grids, so the gap
+// between one kernel's last blocks and the next kernel's first is a visible part
+// of the step.  Launched with the programmatic-serialization attribute, a kernel
+// lets the next one be scheduled once all of its own blocks have started
+// (launch_dependents), and waits, before touching memory, until the previous
+// kernel has completed and its writes are visible (wait).  The next kernel's
+// blocks thus become resident during this one's tail instead of after it.  Both
+// instructions are no-ops for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_prologue() {
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t s, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 
 // Device-resident state block (one per context, inside the workspace).
 struct DevState {

@@ -986,6 +986,7 @@ __global__ void __launch_bounds__(NL * 32, (xy_min_blocks<NL, SECOND, P1>()))
     k_lines_xy(InX inx, LineGeo gx, EpiX ex, InY iny, LineGeo gy, EpiY ey, LineConst<P1> k1,
                LineConst<PolF> k1f, LineConst<P2> k2, DevState* st, int bump, int nbx,
                const __grid_constant__ CUtensorMap tmy, int use_tma) {
+    pdl_prologue();
     if (bump && blockIdx.x == 0 && threadIdx.x == 0) st->t += 1;
     if ((int)blockIdx.x < nbx) {
         ex.init(st);
@@ -1317,10 +1318,9 @@ cudaError_t launch_xy_t(InX inx, EpiX ex, InY iny, EpiY ey, int nx, int ny, int 
     int use_tma = 0;
     if (std::is_same<P1, PolF>::value && std::is_same<P2, PolF>::value && st)
         use_tma = y_tensor_map(y_field(iny), nx, ny, NL, &tmy) ? 1 : 0;
-    kern<<<blocks, NL * 32, smem, s>>>(inx, gx, ex, iny, gy, ey, make_const<P1>(order),
-                                       make_const<PolF>(order), make_const<P2>(order), st, bump,
-                                       nbx, tmy, use_tma);
-    return cudaGetLastError();
+    return launch_pdl(kern, blocks, NL * 32, smem, s, inx, gx, ex, iny, gy, ey,
+                      make_const<P1>(order), make_const<PolF>(order), make_const<P2>(order), st,
+                      bump, nbx, tmy, use_tma);
 }
 
 template <class P1, class P2, bool SECOND, class InX, class EpiX, class InY, class EpiY>

@@ -164,6 +164,7 @@ __device__ __forceinline__ void cs_mixed_body(const CsArgs& a, int wid) {
 
 template <bool MRT>
 __global__ void __launch_bounds__(kSwWarps * 32) k_cs_mixed_sw(CsArgs a) {
+    pdl_prologue();
     cs_mixed_body<MRT, false>(a, blockIdx.x * kSwWarps + (threadIdx.x >> 5));
 }
 
@@ -172,6 +173,7 @@ __global__ void __launch_bounds__(kSwWarps * 32) k_cs_mixed_sw(CsArgs a) {
 // a tenth of the occupancy.
 template <bool MRT>
 __global__ void __launch_bounds__(kSwWarps * 32, 10) k_cs_mixed_sw_walls(CsArgs a) {
+    pdl_prologue();
     cs_mixed_body<MRT, true>(a, blockIdx.x * kSwWarps + (threadIdx.x >> 5));
 }
 
@@ -212,6 +214,7 @@ __device__ __forceinline__ void ring_wait_groups() {
 
 template <bool MRT>
 __global__ void __launch_bounds__(kRingT) k_cs_mixed_ring(CsArgs a) {
+    pdl_prologue();
     __shared__ __align__(16) float raw[kRingD][11 * kRingT];
     // three post-collision rows: row r overwrites row r - 3, whose last reader
     // (the gather of row r - 2) finished before the barrier that precedes it
@@ -403,6 +406,7 @@ __device__ __forceinline__ void mu_mixed_body(const float* __restrict__ rh, floa
 __global__ void k_mu_mixed(const float* __restrict__ rh, float* dxx_mu,
                            const float* __restrict__ dyy, size_t N, MuConstF p,
                            DevState* __restrict__ st) {
+    pdl_prologue();
     mu_mixed_body(rh, dxx_mu, dyy, N, p, st, blockIdx.x * (size_t)blockDim.x + threadIdx.x,
                   (size_t)gridDim.x * blockDim.x);
 }
@@ -509,15 +513,10 @@ int cs_mixed_blocks(const CsArgs& a) {
 
 cudaError_t launch_cs_mixed_args(const CsArgs& a, cudaStream_t s) {
     const int nb = cs_mixed_blocks(a);
-    if (a.mrt && a.walls)
-        k_cs_mixed_sw_walls<true><<<nb, kSwWarps * 32, 0, s>>>(a);
-    else if (a.mrt)
-        k_cs_mixed_sw<true><<<nb, kSwWarps * 32, 0, s>>>(a);
-    else if (a.walls)
-        k_cs_mixed_sw_walls<false><<<nb, kSwWarps * 32, 0, s>>>(a);
-    else
-        k_cs_mixed_sw<false><<<nb, kSwWarps * 32, 0, s>>>(a);
-    return cudaGetLastError();
+    if (a.mrt && a.walls) return launch_pdl(k_cs_mixed_sw_walls<true>, nb, kSwWarps * 32, 0, s, a);
+    if (a.mrt) return launch_pdl(k_cs_mixed_sw<true>, nb, kSwWarps * 32, 0, s, a);
+    if (a.walls) return launch_pdl(k_cs_mixed_sw_walls<false>, nb, kSwWarps * 32, 0, s, a);
+    return launch_pdl(k_cs_mixed_sw<false>, nb, kSwWarps * 32, 0, s, a);
 }
 
 cudaError_t launch_cs_mixed(const float* fin, float* fout, const float* Fx, const float* Fy,
@@ -530,11 +529,8 @@ cudaError_t launch_cs_mixed(const float* fin, float* fout, const float* Fx, cons
         return launch_cs_mixed_args(a, s);
     const CsArgs r = cs_ring_args(a, ring_rows);
     const unsigned nb = (unsigned)(r.nstrips * r.nseg);
-    if (r.mrt)
-        k_cs_mixed_ring<true><<<nb, kRingT, 0, s>>>(r);
-    else
-        k_cs_mixed_ring<false><<<nb, kRingT, 0, s>>>(r);
-    return cudaGetLastError();
+    return r.mrt ? launch_pdl(k_cs_mixed_ring<true>, nb, kRingT, 0, s, r)
+                 : launch_pdl(k_cs_mixed_ring<false>, nb, kRingT, 0, s, r);
 }
 
 bool cs_ring_used(int nx, int ny, size_t plane, const void* fin, const void* Fx,
@@ -592,9 +588,8 @@ MuConstF mu_mixed_const(const PhysParams& p) {
 cudaError_t launch_mu_mixed(const float* rh, float* dxx_mu, const float* dyy, int nx, int ny,
                             const PhysParams& p, DevState* st, cudaStream_t s) {
     const size_t N = (size_t)nx * ny;
-    k_mu_mixed<<<grid_for((N + 3) / 4, 256), 256, 0, s>>>(rh, dxx_mu, dyy, N, mu_mixed_const(p),
-                                                           st);
-    return cudaGetLastError();
+    return launch_pdl(k_mu_mixed, grid_for((N + 3) / 4, 256), 256, 0, s, rh, dxx_mu, dyy, N,
+                      mu_mixed_const(p), st);
 }
 
 cudaError_t launch_mu_mixed_batch(const MuBatchInst* d, const int* map, int nblocks,
