@@ -713,6 +713,53 @@ def collide_forms(sizes=(1024, 2048, 4096), reps=50):
     return out
 
 
+def launch_overlap(steps=300, graph_steps=2000):
+    """Programmatic dependent launch between the mixed step's kernels, on and off,
+    on the bench drop at 1024^2, in the same process: (a) single steps launched
+    directly, each bracketed by an event pair, the L2 flushed between them as in
+    the main timing; (b) back-to-back steps replayed from the CUDA graphs,
+    without flushing."""
+    import numpy as np
+    import torch
+    import paper_1906_09530_gb300 as P
+    from paper_1906_09530_gb300 import workloads as W
+    w = dict(WORKLOAD)
+    rg, rl = P.lbm_maxwell(w["T_r"])
+    sim = P.Simulation(w["nx"], w["ny"], w["T_r"], w["kappa"], w["tau"], w["k"],
+                       fd_order=w["order"], precision="mixed")
+    sim.set_fields(W.drop(w["nx"], w["ny"], rg, rl, w["radius"], w["width"]))
+    N = w["nx"] * w["ny"]
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    clean = torch.zeros(128 << 20, dtype=torch.float32, device="cuda")
+    out = {"workload": workload_name(w, "mixed")}
+    for on in (False, True, False, True):
+        sim.set_launch_overlap(on, on)
+        sim.step(10)
+        ea = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        eb = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        for i in range(steps):
+            flush.zero_()
+            clean.amax()
+            ea[i].record()
+            sim.step_async(1)
+            eb[i].record()
+        sim.check()
+        us = float(np.mean([a.elapsed_time(b) for a, b in zip(ea, eb)])) * 1e3
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        sim.step_async(graph_steps)
+        e1.record()
+        sim.check()
+        g = N * graph_steps / (e0.elapsed_time(e1) / 1e3) / 1e6
+        key = "on" if on else "off"
+        out.setdefault(key, []).append({"direct_us_per_step": round(us, 2),
+                                        "direct_mlups": round(N / us, 1),
+                                        "graph_mlups": round(g, 1)})
+    sim.close()
+    return out
+
+
 def mlp_products(batches=(256, 4096, 32768), reps=50):
     """The surrogate network's kernels alone: forward pass and Adam training
     step at several batch sizes, with the forward and input-gradient products
@@ -1165,6 +1212,7 @@ def main():
         line["splash_paper"] = splash_paper_config()
     if rank == 0 and not args.no_forms and args.precision == "mixed":
         line["collide_forms"] = collide_forms()
+        line["launch_overlap"] = launch_overlap()
     if rank == 0 and not args.no_mlp:
         line["mlp"] = mlp_products(tuple(int(b) for b in args.mlp_batches.split(",")),
                                    args.mlp_reps)

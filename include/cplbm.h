@@ -189,6 +189,16 @@ int32_t lbm_path_flags(const lbm_ctx *ctx);
  * which one runs.  LBM_EINVAL for other values. */
 lbm_status lbm_set_collide_form(lbm_ctx *ctx, int32_t ring_rows);
 
+/* Programmatic dependent launch between the kernels of a mixed step: each
+ * kernel lets the next be scheduled once all of its blocks have started, and
+ * waits in hardware for the previous one to complete before touching memory,
+ * so the next pass's blocks are resident during this one's tail.  Chosen
+ * separately (1 on, 0 off) for the passes launched directly (lbm_step_async of
+ * one step, lbm_step_timed) and for those captured in the CUDA graphs that run
+ * longer lbm_step / lbm_step_async calls.  Defaults: direct 1, graphs 0.
+ * Results are the same either way.  LBM_EINVAL for other values. */
+lbm_status lbm_set_launch_overlap(lbm_ctx *ctx, int32_t direct, int32_t graphs);
+
 /* Outputs of the current state to host FP64 [ny][nx] arrays, any may be NULL:
  * rho (Eq. 3), the velocity v = u + F/(2 rho) (Sec. 2, after Eq. 5) and the
  * mesh-space chemical potential mu-hat (Eq. 33).  Returns when copied. */

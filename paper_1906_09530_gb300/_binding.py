@@ -100,6 +100,7 @@ def lib():
             "lbm_time": (C.c_int64, [_vp]),
             "lbm_path_flags": (C.c_int32, [_vp]),
             "lbm_set_collide_form": (C.c_int, [_vp, _i32]),
+            "lbm_set_launch_overlap": (C.c_int, [_vp, _i32, _i32]),
             "lbm_failed_step": (C.c_int64, [_vp]),
             "lbm_set_timeout": (C.c_int, [_vp, C.c_double]),
             "lbm_set_wall_velocity": (C.c_int, [_vp, C.c_double, C.c_double]),
@@ -310,6 +311,12 @@ class Simulation:
         """Bit set: LBM_PATH_RHO_DF (2) for double-float density lines, LBM_PATH_CS_RING
         (4) for the row-ring collide-stream kernel; 0 for FP64."""
         return lib().lbm_path_flags(self.ctx)
+
+    def set_launch_overlap(self, direct, graphs):
+        """Programmatic dependent launch between the mixed step's kernels, for
+        direct launches and for graph-captured ones (lbm_set_launch_overlap)."""
+        _check(lib().lbm_set_launch_overlap(self.ctx, 1 if direct else 0, 1 if graphs else 0),
+               "lbm_set_launch_overlap")
 
     def set_collide_form(self, ring_rows):
         """Mixed collide-stream form: -1 sliding window, 0 by grid size (the

@@ -37,6 +37,10 @@ struct lbm_ctx {
     bool mrt;     // MRT collision (Eq. 4) with the rates below
     int ring_rows; // mixed collide-stream form: -1 sliding window, 0 by grid size,
                    // > 0 row ring with that many rows a block
+    // programmatic dependent launch between the mixed step's kernels, chosen
+    // separately for direct launches and for the launches captured in graphs;
+    // pdl_now is what the passes being enqueued use
+    bool pdl_direct, pdl_graph, pdl_now;
     MrtRates rates;
     double T, Tc, rhoc, kappa, tau, k;
     double mu_max;
@@ -124,6 +128,7 @@ lbm_status use_dev(lbm_ctx* c) {
 // Passes 2-5 on the current density.  `timed` records an event after each.
 lbm_status enqueue_force(lbm_ctx* c, cudaStream_t s, int bump, cudaEvent_t* ev = nullptr) {
     const int nx = c->nx, ny = c->ny, o = c->fd_order;
+    launch_pdl_on() = c->pdl_now;
     auto mark = [&](int i) { return ev ? cudaEventRecord(ev[i], s) : cudaSuccess; };
     if (!is_fp64(c)) {
         // x|y lines of rho together, mu-hat pointwise, x|y lines of mu-hat + force
@@ -157,6 +162,7 @@ lbm_status enqueue_force(lbm_ctx* c, cudaStream_t s, int bump, cudaEvent_t* ev =
 // Pass 1 from f[from] into f[1-from].
 lbm_status enqueue_collide(lbm_ctx* c, cudaStream_t s, int from) {
     const int to = 1 - from;
+    launch_pdl_on() = c->pdl_now;
     if (is_fp64(c))
         CK(launch_collide_stream<double>((const double*)c->f[from], (double*)c->f[to], c->Fx,
                                          c->Fy, c->rho, c->nx, c->ny, c->plane,
@@ -194,8 +200,10 @@ lbm_status build_graph(lbm_ctx* c, int from, int steps, cudaGraphExec_t* out) {
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
     lbm_status st = LBM_OK;
+    c->pdl_now = c->pdl_graph;
     for (int i = 0; i < steps && st == LBM_OK; ++i)
         st = enqueue_step(c, c->cap_stream, (from + i) & 1);
+    c->pdl_now = c->pdl_direct;
     cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
     if (st != LBM_OK) {
         if (g) cudaGraphDestroy(g);
@@ -326,6 +334,9 @@ lbm_status lbm_init(lbm_ctx** out, const lbm_grid* grid, const lbm_eos* eos, dou
     c->rho_df = opts->prec == LBM_PREC_MIXED_DF;
     c->mrt = opts->collision == LBM_COLLIDE_MRT;
     c->ring_rows = 0;
+    c->pdl_direct = true;
+    c->pdl_graph = false;
+    c->pdl_now = c->pdl_direct;
     c->walls_y = !grid->periodic_y;
     c->walls.on = c->walls_y;
     c->rates = MrtRates{opts->s_e, opts->s_eps, opts->s_q};
@@ -435,6 +446,15 @@ int32_t lbm_path_flags(const lbm_ctx* c) {
                      c->ring_rows))
         f |= LBM_PATH_CS_RING;
     return f;
+}
+
+lbm_status lbm_set_launch_overlap(lbm_ctx* c, int32_t direct, int32_t graphs) {
+    if (!c || (direct != 0 && direct != 1) || (graphs != 0 && graphs != 1)) return LBM_EINVAL;
+    c->pdl_direct = direct == 1;
+    c->pdl_graph = graphs == 1;
+    c->pdl_now = c->pdl_direct;
+    drop_graphs(c);  // the captured launches hold the old attribute
+    return LBM_OK;
 }
 
 lbm_status lbm_set_collide_form(lbm_ctx* c, int32_t ring_rows) {

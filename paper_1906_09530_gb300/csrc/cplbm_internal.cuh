@@ -26,6 +26,10 @@ __device__ __forceinline__ void pdl_prologue() {
     asm volatile("griddepcontrol.wait;\n" ::: "memory");
 }
 
+// Whether launch_pdl sets the attribute: chosen per context by whoever enqueues
+// (the host thread that enqueues a step sets it first; enqueueing is synchronous).
+bool& launch_pdl_on();
+
 template <typename... KArgs, typename... Args>
 cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
                        cudaStream_t s, Args&&... args) {
@@ -38,7 +42,7 @@ cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t sme
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = launch_pdl_on() ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 

@@ -467,6 +467,11 @@ inline unsigned grid_for(size_t n, int threads) {
 
 }  // namespace
 
+bool& launch_pdl_on() {
+    thread_local bool on = true;
+    return on;
+}
+
 CsArgs cs_mixed_args(const float* fin, float* fout, const float* Fx, const float* Fy,
                      float* rh, float* rl, int nx, int ny, size_t plane, double omega,
                      const MrtRates* mrt, DevState* st, int rows, const Walls& walls) {
