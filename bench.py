@@ -714,11 +714,12 @@ def collide_forms(sizes=(1024, 2048, 4096), reps=50):
 
 
 def launch_overlap(steps=300, graph_steps=2000):
-    """Programmatic dependent launch between the mixed step's kernels, on and off,
-    on the bench drop at 1024^2, in the same process: (a) single steps launched
-    directly, each bracketed by an event pair, the L2 flushed between them as in
-    the main timing; (b) back-to-back steps replayed from the CUDA graphs,
-    without flushing."""
+    """How a step's passes are launched, on the bench drop at 1024^2, in one
+    process: lone steps (lbm_step_async of one step) launched directly or from a
+    one-step graph, each with programmatic dependent launch off and on, each
+    step bracketed by an event pair with the L2 flushed between steps as in the
+    main timing; and back-to-back graph replays, without flushing, with it off
+    and on."""
     import numpy as np
     import torch
     import paper_1906_09530_gb300 as P
@@ -731,9 +732,10 @@ def launch_overlap(steps=300, graph_steps=2000):
     N = w["nx"] * w["ny"]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     clean = torch.zeros(128 << 20, dtype=torch.float32, device="cuda")
-    out = {"workload": workload_name(w, "mixed")}
-    for on in (False, True, False, True):
-        sim.set_launch_overlap(on, on)
+    out = {"workload": workload_name(w, "mixed"), "lone_step_us": {}, "graph_mlups": {}}
+
+    def lone(mode):
+        sim.set_launch_mode(*mode)
         sim.step(10)
         ea = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         eb = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
@@ -744,18 +746,23 @@ def launch_overlap(steps=300, graph_steps=2000):
             sim.step_async(1)
             eb[i].record()
         sim.check()
-        us = float(np.mean([a.elapsed_time(b) for a, b in zip(ea, eb)])) * 1e3
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record()
-        sim.step_async(graph_steps)
-        e1.record()
-        sim.check()
-        g = N * graph_steps / (e0.elapsed_time(e1) / 1e3) / 1e6
-        key = "on" if on else "off"
-        out.setdefault(key, []).append({"direct_us_per_step": round(us, 2),
-                                        "direct_mlups": round(N / us, 1),
-                                        "graph_mlups": round(g, 1)})
+        return float(np.mean([a.elapsed_time(b) for a, b in zip(ea, eb)])) * 1e3
+
+    for rep in range(2):
+        for name, mode in (("direct", (0, 0, 0)), ("direct_pdl", (0, 1, 0)),
+                           ("graph", (1, 0, 0)), ("graph_pdl", (1, 0, 1))):
+            out["lone_step_us"].setdefault(name, []).append(round(lone(mode), 2))
+        for name, mode in (("off", (0, 0, 0)), ("pdl", (0, 0, 1))):
+            sim.set_launch_mode(*mode)
+            sim.step(16)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            sim.step_async(graph_steps)
+            e1.record()
+            sim.check()
+            out["graph_mlups"].setdefault(name, []).append(
+                round(N * graph_steps / (e0.elapsed_time(e1) / 1e3) / 1e6, 1))
     sim.close()
     return out
 

@@ -189,15 +189,22 @@ int32_t lbm_path_flags(const lbm_ctx *ctx);
  * which one runs.  LBM_EINVAL for other values. */
 lbm_status lbm_set_collide_form(lbm_ctx *ctx, int32_t ring_rows);
 
-/* Programmatic dependent launch between the kernels of a mixed step: each
- * kernel lets the next be scheduled once all of its blocks have started, and
- * waits in hardware for the previous one to complete before touching memory,
- * so the next pass's blocks are resident during this one's tail.  Chosen
- * separately (1 on, 0 off) for the passes launched directly (lbm_step_async of
- * one step, lbm_step_timed) and for those captured in the CUDA graphs that run
- * longer lbm_step / lbm_step_async calls.  Defaults: direct 1, graphs 0.
- * Results are the same either way.  LBM_EINVAL for other values. */
-lbm_status lbm_set_launch_overlap(lbm_ctx *ctx, int32_t direct, int32_t graphs);
+/* How the passes of a step are launched (results are the same either way):
+ *   single_graph  1: a lone step (lbm_step_async of one step, or the odd last
+ *                 step of a longer call) replays a captured one-step CUDA graph;
+ *                 0: its passes are launched directly.  Longer calls always
+ *                 replay graphs of 2 and 16 steps.
+ *   pdl_direct, pdl_graphs  programmatic dependent launch between the kernels
+ *                 of a mixed step, for direct launches and for graph-captured
+ *                 ones: each kernel lets the next be scheduled once all of its
+ *                 blocks have started and waits in hardware for the previous
+ *                 one to complete before touching memory, so the next pass's
+ *                 blocks are resident during this one's tail.
+ * Defaults: single_graph 1, pdl_direct 1, pdl_graphs 0 (the fastest lone and
+ * back-to-back steps measured at 1024^2).  Each argument 0 or 1, else
+ * LBM_EINVAL. */
+lbm_status lbm_set_launch_mode(lbm_ctx *ctx, int32_t single_graph, int32_t pdl_direct,
+                               int32_t pdl_graphs);
 
 /* Outputs of the current state to host FP64 [ny][nx] arrays, any may be NULL:
  * rho (Eq. 3), the velocity v = u + F/(2 rho) (Sec. 2, after Eq. 5) and the

@@ -100,7 +100,7 @@ def lib():
             "lbm_time": (C.c_int64, [_vp]),
             "lbm_path_flags": (C.c_int32, [_vp]),
             "lbm_set_collide_form": (C.c_int, [_vp, _i32]),
-            "lbm_set_launch_overlap": (C.c_int, [_vp, _i32, _i32]),
+            "lbm_set_launch_mode": (C.c_int, [_vp, _i32, _i32, _i32]),
             "lbm_failed_step": (C.c_int64, [_vp]),
             "lbm_set_timeout": (C.c_int, [_vp, C.c_double]),
             "lbm_set_wall_velocity": (C.c_int, [_vp, C.c_double, C.c_double]),
@@ -312,11 +312,11 @@ class Simulation:
         (4) for the row-ring collide-stream kernel; 0 for FP64."""
         return lib().lbm_path_flags(self.ctx)
 
-    def set_launch_overlap(self, direct, graphs):
-        """Programmatic dependent launch between the mixed step's kernels, for
-        direct launches and for graph-captured ones (lbm_set_launch_overlap)."""
-        _check(lib().lbm_set_launch_overlap(self.ctx, 1 if direct else 0, 1 if graphs else 0),
-               "lbm_set_launch_overlap")
+    def set_launch_mode(self, single_graph, pdl_direct, pdl_graphs):
+        """Lone steps from a one-step graph or direct launches, and programmatic
+        dependent launch for direct and graph-captured passes (lbm_set_launch_mode)."""
+        _check(lib().lbm_set_launch_mode(self.ctx, int(bool(single_graph)), int(bool(pdl_direct)),
+                                         int(bool(pdl_graphs))), "lbm_set_launch_mode")
 
     def set_collide_form(self, ring_rows):
         """Mixed collide-stream form: -1 sliding window, 0 by grid size (the

@@ -41,6 +41,7 @@ struct lbm_ctx {
     // separately for direct launches and for the launches captured in graphs;
     // pdl_now is what the passes being enqueued use
     bool pdl_direct, pdl_graph, pdl_now;
+    bool single_graph;  // a lone step (lbm_step_async of 1, an odd last step) from a graph
     MrtRates rates;
     double T, Tc, rhoc, kappa, tau, k;
     double mu_max;
@@ -66,6 +67,7 @@ struct lbm_ctx {
     bool ready;      // fields set
     cudaGraphExec_t graph[2];    // two steps, starting from f[0] / f[1]
     cudaGraphExec_t graph16[2];  // kLongGraph steps, likewise (fewer graph launches)
+    cudaGraphExec_t graph1[2];   // one step, for single steps when single_graph is set
     double timeout_s;
 };
 
@@ -187,7 +189,7 @@ constexpr int kLongGraph = 16;
 
 void drop_graphs(lbm_ctx* c) {
     for (int i = 0; i < 2; ++i)
-        for (cudaGraphExec_t* gp : {&c->graph[i], &c->graph16[i]})
+        for (cudaGraphExec_t* gp : {&c->graph[i], &c->graph16[i], &c->graph1[i]})
             if (*gp) {
                 cudaGraphExecDestroy(*gp);
                 *gp = nullptr;
@@ -337,6 +339,7 @@ lbm_status lbm_init(lbm_ctx** out, const lbm_grid* grid, const lbm_eos* eos, dou
     c->pdl_direct = true;
     c->pdl_graph = false;
     c->pdl_now = c->pdl_direct;
+    c->single_graph = true;
     c->walls_y = !grid->periodic_y;
     c->walls.on = c->walls_y;
     c->rates = MrtRates{opts->s_e, opts->s_eps, opts->s_q};
@@ -448,10 +451,13 @@ int32_t lbm_path_flags(const lbm_ctx* c) {
     return f;
 }
 
-lbm_status lbm_set_launch_overlap(lbm_ctx* c, int32_t direct, int32_t graphs) {
-    if (!c || (direct != 0 && direct != 1) || (graphs != 0 && graphs != 1)) return LBM_EINVAL;
-    c->pdl_direct = direct == 1;
-    c->pdl_graph = graphs == 1;
+lbm_status lbm_set_launch_mode(lbm_ctx* c, int32_t single_graph, int32_t pdl_direct,
+                               int32_t pdl_graphs) {
+    auto bit = [](int32_t v) { return v == 0 || v == 1; };
+    if (!c || !bit(single_graph) || !bit(pdl_direct) || !bit(pdl_graphs)) return LBM_EINVAL;
+    c->single_graph = single_graph == 1;
+    c->pdl_direct = pdl_direct == 1;
+    c->pdl_graph = pdl_graphs == 1;
     c->pdl_now = c->pdl_direct;
     drop_graphs(c);  // the captured launches hold the old attribute
     return LBM_OK;
@@ -529,8 +535,14 @@ lbm_status lbm_step_async(lbm_ctx* c, int64_t n) {
         for (; left >= 2; left -= 2) CK(cudaGraphLaunch(c->graph[c->cur], c->stream));
     }
     if (left == 1) {
-        st = enqueue_step(c, c->stream, c->cur);
-        if (st) return st;
+        if (c->single_graph) {
+            st = build_graph(c, c->cur, 1, &c->graph1[c->cur]);
+            if (st) return st;
+            CK(cudaGraphLaunch(c->graph1[c->cur], c->stream));
+        } else {
+            st = enqueue_step(c, c->stream, c->cur);
+            if (st) return st;
+        }
         c->cur = 1 - c->cur;
     }
     c->t += n;

@@ -89,21 +89,21 @@ def test_ring_long_run_against_oracle_parity_size(cuda):
     assert np.array_equal(f_r, f_s)
 
 
-@pytest.mark.parametrize("direct,graphs", [(0, 0), (1, 1), (1, 0)])
-def test_launch_overlap_keeps_results(cuda, direct, graphs):
-    """Programmatic dependent launch changes when the kernels are scheduled,
-    not what they compute: single direct steps and graph replays, with it on
-    or off, give the populations of the default setting bit for bit."""
+@pytest.mark.parametrize("mode", [(0, 0, 0), (0, 1, 0), (0, 1, 1), (1, 0, 0), (1, 0, 1)])
+def test_launch_mode_keeps_results(cuda, mode):
+    """Graph or direct lone steps and programmatic dependent launch change when
+    the kernels are scheduled, not what they compute: single steps and graph
+    replays give the default setting's populations bit for bit."""
     rg, rl = lbm_maxwell(0.5)
     rho = W.drop(512, 384, rg, rl, 96.0, 8.0)
     out = []
-    for d, g in ((1, 0), (direct, graphs)):
+    for m in ((1, 1, 0), mode):
         s = Simulation(512, 384, 0.5, 0.1, 1.0, 0.5, fd_order=6, precision="mixed")
-        s.set_launch_overlap(d, g)
+        s.set_launch_mode(*m)
         s.set_fields(rho)
         for _ in range(3):
-            s.step_async(1)  # direct launches
-        s.step(20)           # graph replays
+            s.step_async(1)  # lone steps
+        s.step(21)           # graph replays and an odd last step
         out.append(s.get_populations()[0])
         s.close()
     assert np.array_equal(out[0], out[1])
