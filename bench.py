@@ -605,13 +605,13 @@ def surrogate_demo():
     loss = s.fit(T, K, k, G, L, P, epochs=3000, lr=2e-3, batch=128)
     fit_s = time.perf_counter() - t0
     # training-step throughput at batch 256 (algorithmic flops: forward
-    # 2 (3*256 + 3*256^2) per sample, backward twice that less the input layer's
+    # 2 (4*256 + 3*256^2) per sample, backward twice that less the input layer's
     # input gradient)
     # timed on a network of its own, so the trained one is left as it is
     from paper_1906_09530_gb300 import Mlp
     tnet = Mlp(256)
     tnet.set_params(SG.glorot_params(0))
-    x = torch.rand((256, 3), device="cuda") * 2 - 1
+    x = torch.rand((256, 4), device="cuda") * 2 - 1
     y = torch.rand((256, 256), device="cuda")
     for _ in range(10):
         tnet.train_step(x, y, 1e-3)
@@ -623,8 +623,8 @@ def surrogate_demo():
     torch.cuda.synchronize()
     step_ms = e0.elapsed_time(e1) / 200
     tnet.close()
-    fwd = 2 * (3 * 256 + 3 * 256 * 256)
-    flops = 256 * (fwd + 2 * fwd - 2 * 3 * 256)
+    fwd = 2 * (4 * 256 + 3 * 256 * 256)
+    flops = 256 * (fwd + 2 * fwd - 2 * 4 * 256)
     peak, _ = load_bf16_peak()
     tflops = flops / (step_ms / 1e3) / 1e12
     ny = 1536
@@ -771,19 +771,19 @@ def mlp_products(batches=(256, 4096, 32768), reps=50):
     """The surrogate network's kernels alone: forward pass and Adam training
     step at several batch sizes, with the forward and input-gradient products
     on tcgen05 (the default) and on the mma.sync comparison kernel.
-    Algorithmic flops per sample: forward 2 (3*256 + 3*256^2); training step
-    three times that less the input layer's input gradient (2*3*256)."""
+    Algorithmic flops per sample: forward 2 (4*256 + 3*256^2); training step
+    three times that less the input layer's input gradient (2*4*256)."""
     import torch
     from paper_1906_09530_gb300 import Mlp, surrogate as SG
     peak, how = load_bf16_peak()
-    fwd = 2 * (3 * 256 + 3 * 256 * 256)
-    train = 3 * fwd - 2 * 3 * 256
+    fwd = 2 * (4 * 256 + 3 * 256 * 256)
+    train = 3 * fwd - 2 * 4 * 256
     out = {"peak_tflops": peak, "peak_kind": how, "rows": []}
     for B in batches:
         net = Mlp(B)
         net.set_params(SG.glorot_params(0))
         g = torch.Generator(device="cuda").manual_seed(B)
-        x = torch.rand((B, 3), device="cuda", generator=g) * 2 - 1
+        x = torch.rand((B, 4), device="cuda", generator=g) * 2 - 1
         t = torch.rand((B, 256), device="cuda", generator=g)
         row = {"batch": B}
         for tc in (True, False):
@@ -951,6 +951,92 @@ def warm_drop_case(s, eq, t_r, n=4096, radius=1000.0, every=5000, max_steps=100_
     return row
 
 
+def drop_warm_start(train_T=(0.32, 0.33, 0.34, 0.36, 0.37, 0.38, 0.40),
+                    radii=(64.0, 125.0, 250.0), judge_T=0.35, judge_R=250.0,
+                    train_steps=300_000, run_steps=240_000, every=2000, window=10, kappa=0.1,
+                    k=0.2, epochs=4000):
+    """The learned warm start for drops (configs[4] scaled to a drop whose plain
+    run converges).  Training data: drops of the given radii (each at the centre
+    of a periodic grid 4 R wide) at the training temperatures, run as one batch
+    for train_steps; the surrogate takes (T_r, kappa-hat, k, 1/R).  Judge: a drop
+    of judge_R at judge_T (a temperature not trained on), from the tanh start
+    between the Maxwell densities (the plain run, whose settled bulks are the
+    target) and from the surrogate's prediction, its radius chosen so that the
+    warm field holds the plain field's mass (the same system: a drop's
+    equilibrium depends on its mass); each run samples the far-field
+    gas (outer n/16 of every side) and the liquid core (r < R/2) every `every`
+    steps, and its settling step is where the mean of the last `window` samples
+    stays within 1e-3 of the target."""
+    import numpy as np
+    import torch
+    from paper_1906_09530_gb300 import Simulation, lbm_maxwell, surrogate as SG
+    from paper_1906_09530_gb300 import workloads as W
+    T = np.repeat(np.asarray(train_T, dtype=np.float64), len(radii))
+    R = np.tile(np.asarray(radii, dtype=np.float64), len(train_T))
+    n = (4 * R).astype(int)
+    t0 = time.perf_counter()
+    G, L, P = SG.drop_profiles(T, np.full(T.size, kappa), np.full(T.size, k), R, n, train_steps)
+    data_s = time.perf_counter() - t0
+    s = SG.Surrogate(seed=7, ranges={"T_r": (min(train_T), max(train_T)),
+                                     "kappa": (kappa, kappa), "k": (k, k)},
+                     inv_r_range=(1.0 / max(radii), 1.0 / min(radii)), max_batch=256)
+    t0 = time.perf_counter()
+    loss = s.fit(T, np.full(T.size, kappa), np.full(T.size, k), G, L, P, epochs=epochs,
+                 lr=2e-3, batch=T.size, inv_r=1.0 / R)
+    fit_s = time.perf_counter() - t0
+    g, l, w = s.predict([judge_T], [kappa], [k], inv_r=[1.0 / judge_R])
+    s.close()
+    m = int(4 * judge_R)
+    rg, rl = lbm_maxwell(judge_T)
+    yy, xx = torch.meshgrid(torch.arange(m, device="cuda", dtype=torch.float64),
+                            torch.arange(m, device="cuda", dtype=torch.float64), indexing="ij")
+    r = torch.hypot(xx - m / 2, yy - m / 2)
+    liq = r < judge_R / 2
+    b = m // 16
+    gas = torch.zeros_like(liq)
+    gas[:b, :] = gas[-b:, :] = gas[:, :b] = gas[:, -b:] = True
+    runs = {}
+    plain = W.drop(m, m, rg, rl, judge_R, 4.0 / k)
+    # the warm start of the same system: its drop holds the plain start's mass
+    warm_R = SG.drop_radius_for_mass(m, m, plain.sum(), g[0], l[0], w[0], judge_R)
+    for name, field in (("plain", plain), ("warm", SG.drop_field(m, m, warm_R, g[0], l[0], w[0]))):
+        sim = Simulation(m, m, judge_T, kappa, 1.0, k, fd_order=6, precision="mixed")
+        sim.set_fields(field)
+        times, samples, step_s = [], [], 0.0
+        while True:
+            rho = sim.fields_device()[0]
+            times.append(sim.t)
+            samples.append((float(rho[gas].mean()), float(rho[liq].mean())))
+            if sim.t >= run_steps:
+                break
+            c0 = time.perf_counter()
+            sim.step(every)  # returns when the steps are done
+            step_s += time.perf_counter() - c0
+        runs[name] = {"times": times, "samples": samples, "step_s": step_s}
+        sim.close()
+    # wall time of the stepping alone, per step, the same for both starts
+    s_per_step = sum(rr["step_s"] for rr in runs.values()) / (2.0 * run_steps)
+    target = np.mean(np.array(runs["plain"]["samples"][-window:]), axis=0)
+    out = {"workload": f"drop-{m}x{m}-R{int(judge_R)}-Tr{judge_T}-k{k}-kappa{kappa}-mixed",
+           "training": {"T_r": list(train_T), "radii": list(radii), "steps": train_steps,
+                        "data_s": data_s, "fit_s": fit_s, "fit_loss": loss},
+           "target_rel_maxwell": {"gas": target[0] / rg - 1, "liquid": target[1] / rl - 1},
+           "predicted_rel_target": {"gas": g[0] / target[0] - 1, "liquid": l[0] / target[1] - 1},
+           "warm_radius_same_mass": warm_R,
+           "criterion": f"mean of the last {window} samples ({every} steps apart) within 1e-3 "
+                        "of the plain run's settled bulks, and staying there"}
+    for name, rr in runs.items():
+        st = SG.settle_step(rr["times"], rr["samples"], target, 1e-3, window)
+        v0 = np.array(rr["samples"][0])
+        out[name] = {"settle_step": st, "wall_s_to_settle": (None if st is None else
+                     s_per_step * st),
+                     "start_rel_target": {"gas": v0[0] / target[0] - 1,
+                                          "liquid": v0[1] / target[1] - 1},
+                     "series_gas_rel_target": [round(x[0] / target[0] - 1, 5)
+                                               for x in rr["samples"][::10]]}
+    return out
+
+
 def load_bf16_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -1040,6 +1126,8 @@ def main():
     ap.add_argument("--mlp-batches", default="256,4096,32768",
                     help="batch sizes of the network timings (comma-separated)")
     ap.add_argument("--mlp-reps", type=int, default=50)
+    ap.add_argument("--surrogate-drop", action="store_true",
+                    help="add the learned warm start for drops (a few minutes)")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched-instances line")
     ap.add_argument("--no-large", action="store_true",
@@ -1225,6 +1313,8 @@ def main():
                                    args.mlp_reps)
     if rank == 0 and args.surrogate:
         line["surrogate"] = surrogate_demo()
+    if rank == 0 and args.surrogate_drop:
+        line["surrogate_drop"] = drop_warm_start()
     if rank == 0 and not args.no_equilibrium:
         line["equilibrium"] = equilibrium_time(args.precision)
         # the same slab 1024 nodes wide (409 600 nodes, the grid scale of the

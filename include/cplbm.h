@@ -376,9 +376,10 @@ void lbm_batch_free(lbm_batch *b);
 
 /* ---- The surrogate network of the warm start ------------------------------
  *
- * A multilayer perceptron 3 -> 256 -> 256 -> 256 -> 256 (tanh on the three hidden
- * layers, linear output) that maps (T_r, kappa-hat, k), scaled by the caller, to
- * a 256-point equilibrium interface profile.  Every matrix product runs on the
+ * A multilayer perceptron 4 -> 256 -> 256 -> 256 -> 256 (tanh on the three hidden
+ * layers, linear output) that maps (T_r, kappa-hat, k, 1/R), scaled by the
+ * caller, to a 256-point equilibrium interface profile (R the radius of a drop;
+ * the caller's scaling of 1/R is constant for flat interfaces).  Every matrix product runs on the
  * tensor cores in BF16 with FP32 accumulation; master weights, Adam moments,
  * activations and the gradient are FP32.  The products are tcgen05 MMAs with
  * the accumulator in tensor memory (the weight gradient split over the batch
@@ -392,11 +393,11 @@ void lbm_batch_free(lbm_batch *b);
  *
  * Workspace: one caller-owned device buffer (256-byte aligned,
  * lbm_mlp_workspace_bytes(max_batch) long).  Inputs d_x are device FP32
- * [batch][3], targets and outputs device FP32 [batch][256], 1 <= batch <=
+ * [batch][4], targets and outputs device FP32 [batch][256], 1 <= batch <=
  * max_batch.  All work is enqueued on the stream given to lbm_mlp_init. */
 typedef struct lbm_mlp lbm_mlp; /* opaque, owned by the library */
 
-int64_t lbm_mlp_param_count(void); /* 198 400 */
+int64_t lbm_mlp_param_count(void); /* 198 656 */
 size_t lbm_mlp_workspace_bytes(int32_t max_batch); /* 0 if max_batch is out of range */
 lbm_status lbm_mlp_init(lbm_mlp **out, int32_t max_batch, void *d_workspace, size_t ws_bytes,
                         void *cuda_stream);

@@ -4,7 +4,7 @@ backward pass and Adam step, written out layer by layer.
 TEST INFRASTRUCTURE ONLY (part of the oracle): only the tests and the
 benchmark's CPU legs use it.  Shares no code with the CUDA library.
 
-Network (4 layers, width 256): x[3] -> tanh(x W1 + b1) -> tanh(. W2 + b2) ->
+Network (4 layers, width 256): x[4] -> tanh(x W1 + b1) -> tanh(. W2 + b2) ->
 tanh(. W3 + b3) -> . W4 + b4 = y[256].  Row vectors; W_l is [fan_in, fan_out].
 Loss: mean squared error over the batch and the 256 outputs,
 L = sum((y - t)^2) / (B * 256).  Adam (Kingma and Ba, 2015) with bias
@@ -23,7 +23,7 @@ arithmetic, so that such a network can be compared with it entry by entry.
 """
 import numpy as np
 
-SIZES = (3, 256, 256, 256, 256)
+SIZES = (4, 256, 256, 256, 256)
 N_LAYERS = len(SIZES) - 1
 
 

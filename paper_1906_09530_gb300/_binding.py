@@ -479,7 +479,7 @@ class Batch:
 
 class Mlp:
     """The surrogate network (lbm_mlp_* of the C ABI).  Inputs and targets are
-    CUDA float32 tensors [batch][3] and [batch][256]; parameters are numpy
+    CUDA float32 tensors [batch][4] and [batch][256]; parameters are numpy
     float32 vectors in the library's order."""
 
     def __init__(self, max_batch, device=None, stream=None):
@@ -517,7 +517,7 @@ class Mlp:
     def forward(self, x):
         import torch
         y = torch.empty((x.shape[0], 256), dtype=torch.float32, device=x.device)
-        _check(lib().lbm_mlp_forward(self.ctx, self._f32(x, 3), x.shape[0], y.data_ptr()),
+        _check(lib().lbm_mlp_forward(self.ctx, self._f32(x, 4), x.shape[0], y.data_ptr()),
                "lbm_mlp_forward")
         return y
 
@@ -525,13 +525,13 @@ class Mlp:
         import torch
         g = torch.empty(self.n_params, dtype=torch.float32, device=x.device)
         loss = C.c_double()
-        _check(lib().lbm_mlp_loss_grad(self.ctx, self._f32(x, 3), self._f32(t, 256), x.shape[0],
+        _check(lib().lbm_mlp_loss_grad(self.ctx, self._f32(x, 4), self._f32(t, 256), x.shape[0],
                                        C.byref(loss), g.data_ptr()), "lbm_mlp_loss_grad")
         return loss.value, g
 
     def train_step(self, x, t, lr, want_loss=False):
         loss = C.c_double()
-        _check(lib().lbm_mlp_train_step(self.ctx, self._f32(x, 3), self._f32(t, 256), x.shape[0],
+        _check(lib().lbm_mlp_train_step(self.ctx, self._f32(x, 4), self._f32(t, 256), x.shape[0],
                                         lr, C.byref(loss) if want_loss else None),
                "lbm_mlp_train_step")
         return loss.value if want_loss else None

@@ -1,7 +1,8 @@
 // mlp.cu -- the surrogate network of the warm start (lbm_mlp_* of
-// include/cplbm.h): a 3-256-256-256-256 multilayer perceptron with tanh hidden
-// layers that maps (T_r, kappa-hat, k) to a 256-point equilibrium interface
-// profile, trained and evaluated by the kernels of this file.
+// include/cplbm.h): a 4-256-256-256-256 multilayer perceptron with tanh hidden
+// layers that maps (T_r, kappa-hat, k, 1/R) to a 256-point equilibrium interface
+// profile (R the radius of a drop; 0 for flat interfaces), trained and evaluated
+// by the kernels of this file.
 //
 // Arithmetic: every matrix product runs on the tensor cores in BF16 with FP32
 // accumulation; master weights, Adam moments, biases, activations kept for the
@@ -30,7 +31,7 @@
 namespace cplbm {
 namespace {
 
-constexpr int kIn = 3, kW = 256, kOut = 256, kLayers = 4;
+constexpr int kIn = 4, kW = 256, kOut = 256, kLayers = 4;
 constexpr int kInPad = 16;  // the first product's K, padded to one mma k-step
 constexpr int kK0 = 64;     // row stride of the BF16 input and K of its tcgen05 product
                             // (zero-padded to one 128-byte swizzle row)
@@ -763,7 +764,7 @@ __global__ void __launch_bounds__(256) k_wgrad_reduce(const float* __restrict__ 
     }
 }
 
-// x [B][3] FP32 -> BF16 [B][kK0], zero-padded, and (x16t not null) its transpose
+// x [B][4] FP32 -> BF16 [B][kK0], zero-padded, and (x16t not null) its transpose
 // [16][ldt] with zeros for b in [B, rows_t)
 __global__ void k_input(const float* __restrict__ x, __nv_bfloat16* __restrict__ x16, int B,
                         __nv_bfloat16* __restrict__ x16t, int ldt, int rows_t) {

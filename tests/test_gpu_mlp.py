@@ -35,7 +35,7 @@ def _setup(cuda, B, seed=4):
     torch = cuda
     rng = np.random.default_rng(seed)
     p = O.init_params(seed).astype(np.float32)
-    x = rng.uniform(-1, 1, (B, 3)).astype(np.float32)
+    x = rng.uniform(-1, 1, (B, 4)).astype(np.float32)
     t = (0.5 + 0.4 * np.sin(np.outer(x[:, 0] + 0.5 * x[:, 1] - x[:, 2], np.linspace(0, 3, 256)))
          ).astype(np.float32)
     net = Mlp(max_batch=max(512, B))

@@ -83,8 +83,9 @@ def test_extract_recovers_a_window_laid_onto_a_slab():
 def test_drop_field_profile_is_radial():
     window = np.linspace(0.01, 0.4, S.WINDOW)
     rho = S.drop_field(64, 48, 10.0, 0.01, 0.4, window)
-    assert rho[24, 32] == pytest.approx(S.profile_at(0.01, 0.4, window, 10.0))
-    assert rho[24, 32 + 5] == pytest.approx(rho[24 + 5, 32])  # same distance, same value
+    assert rho[24, 32] == 0.4  # the core r < radius / 2 is the bulk liquid
+    assert rho[24, 32 + 7] == pytest.approx(S.profile_at(0.01, 0.4, window, 3.0))
+    assert rho[24, 32 + 7] == pytest.approx(rho[24 + 7, 32])  # same distance, same value
     assert rho.min() >= 0.01 and rho.max() <= 0.4
 
 
@@ -93,7 +94,10 @@ def test_input_scaling_and_sampling():
     lo = [v[0] for v in r.values()]
     hi = [v[1] for v in r.values()]
     x = S.scale_inputs([lo[0], hi[0]], [lo[1], hi[1]], [lo[2], hi[2]], r)
-    assert x.dtype == np.float32 and np.array_equal(x, [[-1, -1, -1], [1, 1, 1]])
+    assert x.dtype == np.float32 and np.array_equal(x, [[-1, -1, -1, 0], [1, 1, 1, 0]])
+    x = S.scale_inputs([lo[0], hi[0]], [lo[1], hi[1]], [lo[2], hi[2]], r,
+                       inv_r=[0.004, 0.016], inv_r_range=(0.004, 0.016))
+    assert np.array_equal(x[:, 3], [-1, 1])
     a = S.sample_inputs(500, 3)
     b = S.sample_inputs(500, 3)
     for col, (l0, h0), col_b in zip(a, r.values(), b):
@@ -128,3 +132,31 @@ def test_batch_instances_are_seeded_and_well_formed():
     assert trs[0] == pytest.approx(0.3) and trs[-1] == pytest.approx(0.9)
     assert all(d["k"] == (0.5 if d["T_r"] >= 0.45 else 0.3) for d in a)
     assert {d["kind"] for d in a} == {"drop", "flat"}
+
+
+def test_extract_drop_on_an_analytic_drop():
+    """A tanh drop of known radius and width: the bulks are the two densities
+    (the field's own values far from the interface) and the window is the
+    profile about the radius, where the midpoint crossing sits."""
+    n, R, w, g, l = 256, 64.0, 10.0, 0.02, 0.4
+    rho = W.drop(n, n, g, l, R, w)
+    eg, el, win = S.extract_drop(rho, R)
+    assert eg == pytest.approx(g, rel=2e-3) and el == pytest.approx(l, rel=1e-6)
+    exact = 0.5 * (g + l) + 0.5 * (g - l) * np.tanh(2.0 * (-S.S) / w)  # d = R - r
+    assert np.abs(win - exact).max() <= 5e-3 * l  # quarter-node bins on the steep flank
+
+
+def test_settle_step():
+    t = list(range(0, 10000, 100))
+    v = [(1.0 + np.exp(-ti / 800.0) * np.cos(ti / 50.0), 2.0) for ti in t]
+    s = S.settle_step(t, v, (1.0, 2.0), 1e-3, 4)
+    # the windowed mean settles once the decaying term is ~1e-3 (t ~ 800 ln 1000)
+    assert 4000 <= s <= 6000
+    assert S.settle_step(t, v, (1.1, 2.0), 1e-3, 4) is None
+
+
+def test_drop_radius_for_mass():
+    window = 0.2 + 0.18 * np.tanh(S.S / 5.0)
+    target = S.drop_field(96, 96, 20.0, 0.02, 0.38, window).sum()
+    r = S.drop_radius_for_mass(96, 96, target, 0.02, 0.38, window, 23.0)
+    assert r == pytest.approx(20.0, abs=1e-6)

@@ -8,7 +8,7 @@
   * a single linear layer's gradient matches the closed form x^T (2 (y - t)/(BN));
   * one Adam step from zero moments moves each parameter by lr sign(g) (up to
     eps), the known first-step behaviour;
-  * the parameter count of 3-256-256-256-256 is 198 400.
+  * the parameter count of 4-256-256-256-256 is 198 656.
 """
 import numpy as np
 import pytest
@@ -17,13 +17,13 @@ from oracle import mlp
 
 
 def test_parameter_count():
-    assert mlp.n_params() == 3 * 256 + 256 + 3 * (256 * 256 + 256) == 198400
+    assert mlp.n_params() == 4 * 256 + 256 + 3 * (256 * 256 + 256) == 198656
 
 
 def test_gradient_matches_finite_differences():
     rng = np.random.default_rng(3)
     p = mlp.init_params(11)
-    x = rng.uniform(-1, 1, (5, 3))
+    x = rng.uniform(-1, 1, (5, 4))
     t = rng.uniform(-1, 1, (5, 256))
     _, g = mlp.loss_and_grad(p, x, t)
     # sample parameters from every layer's weights and biases
@@ -46,7 +46,7 @@ def test_zero_weights_give_last_bias():
     p = np.zeros(mlp.n_params())
     b4 = np.linspace(-1, 1, 256)
     p[-256:] = b4
-    x = np.ones((4, 3))
+    x = np.ones((4, 4))
     y, _ = mlp.forward(p, x)
     assert np.array_equal(y, np.tile(b4, (4, 1)))
     t = np.random.default_rng(1).uniform(size=(4, 256))
@@ -59,7 +59,7 @@ def test_linear_layer_closed_form():
     gradient is a^T (2 (y - t) / (B N)) with a the last hidden activation."""
     rng = np.random.default_rng(5)
     p = mlp.init_params(2)
-    x = rng.uniform(-1, 1, (7, 3))
+    x = rng.uniform(-1, 1, (7, 4))
     t = rng.uniform(-1, 1, (7, 256))
     y, acts = mlp.forward(p, x)
     _, g = mlp.loss_and_grad(p, x, t)
@@ -94,7 +94,7 @@ def test_rounded_network_matches_torch_bfloat16_casts():
     torch = pytest.importorskip("torch")
     rng = np.random.default_rng(8)
     p = mlp.init_params(2).astype(np.float32).astype(np.float64)
-    x = rng.uniform(-1, 1, (7, 3)).astype(np.float32).astype(np.float64)
+    x = rng.uniform(-1, 1, (7, 4)).astype(np.float32).astype(np.float64)
     t = rng.uniform(-1, 1, (7, 256))
     loss, g = mlp.loss_and_grad_rounded(p, x, t)
 
