@@ -304,7 +304,8 @@ def fp64_path_summary(lg):
 def batch_config(steps, warmup, n=256):
     """The batched path on many independent instances (uneven sides 64-512, T_r
     log-spaced 0.3-0.9, drops and flat interfaces; workloads.batch_instances):
-    one launch per pass for all of them, strip heights autotuned.  Compared with
+    one launch per pass for all of them, strip heights and the FP32 line
+    launches' lines per block autotuned.  Compared with
     the same instances stepped one after another as lone contexts (each with its
     own two-step CUDA graph)."""
     import numpy as np
@@ -319,7 +320,17 @@ def batch_config(steps, warmup, n=256):
         fields.append(W.batch_field(d, *P.lbm_maxwell(d["T_r"])))
         b.set_fields(i, fields[-1])
     b.autotune(3)
+    chosen_nl = b.lines_per_block()
     b.step(warmup)
+    # the line launches' lines per block, each way (the autotuner keeps the faster)
+    names = pass_layout("mixed")[0]
+    nl_passes = {}
+    for nl in (8, 16):
+        b.set_lines_per_block(nl)
+        b.step(2)
+        m2 = np.array([b.step_timed() for _ in range(min(steps, 20))])
+        nl_passes[nl] = {nm: round(float(m2[:, i].mean()), 5) for i, nm in enumerate(names)}
+    b.set_lines_per_block(chosen_nl)
     ms = np.array([b.step_timed() for _ in range(steps)])
     N = sum(d["nx"] * d["ny"] for d in specs)
     step_ms = float(ms.sum(axis=1).mean())
@@ -369,6 +380,8 @@ def batch_config(steps, warmup, n=256):
                               "frac": pb * N / (step_ms / 1e3) / 1e9 / peak,
                               "peak": peak, "peak_kind": f"{peak_kind} copy bandwidth"},
             "launches_per_step": 4,
+            "lines_per_block": chosen_nl,
+            "passes_ms_by_lines_per_block": nl_passes,
             "l2": "working set above L2 (no flush)"}
 
 

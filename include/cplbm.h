@@ -361,6 +361,14 @@ lbm_status lbm_batch_autotune(lbm_batch *b, int32_t reps);
 /* The strip height in use for instance i (rows of the collide-stream warps). */
 int32_t lbm_batch_tile_rows(const lbm_batch *b, int32_t i);
 
+/* Lines per block (8 or 16) of the batch's FP32 line launches: the density
+ * lines of the instances below the double-float ratio, and every instance's
+ * force lines (lbm_batch_autotune times both and keeps the faster; the
+ * double-float density lines always take 8).  Results do not depend on it.
+ * The getter returns -1 for NULL; the setter LBM_EINVAL for other values. */
+int32_t lbm_batch_lines_per_block(const lbm_batch *b);
+lbm_status lbm_batch_set_lines_per_block(lbm_batch *b, int32_t nl);
+
 /* Time level of instance i (-1 if out of range). */
 int64_t lbm_batch_time(const lbm_batch *b, int32_t i);
 

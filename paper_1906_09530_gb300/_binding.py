@@ -116,6 +116,8 @@ def lib():
             "lbm_batch_diag": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
             "lbm_batch_autotune": (C.c_int, [_vp, _i32]),
             "lbm_batch_tile_rows": (_i32, [_vp, _i32]),
+            "lbm_batch_lines_per_block": (_i32, [_vp]),
+            "lbm_batch_set_lines_per_block": (C.c_int, [_vp, _i32]),
             "lbm_batch_time": (C.c_int64, [_vp, _i32]),
             "lbm_batch_failed": (C.c_int, [_vp, C.POINTER(_i32), C.POINTER(C.c_int64)]),
             "lbm_batch_set_timeout": (C.c_int, [_vp, C.c_double]),
@@ -453,6 +455,12 @@ class Batch:
 
     def tile_rows(self, i):
         return lib().lbm_batch_tile_rows(self.ctx, i)
+
+    def lines_per_block(self):
+        return lib().lbm_batch_lines_per_block(self.ctx)
+
+    def set_lines_per_block(self, nl):
+        _check(lib().lbm_batch_set_lines_per_block(self.ctx, nl), "lbm_batch_set_lines_per_block")
 
     def time(self, i):
         return lib().lbm_batch_time(self.ctx, i)

@@ -139,6 +139,7 @@ struct lbm_batch {
     DevState* dst;  // n state blocks, device
     DevState* hst;  // pinned host mirror
     int cur;
+    int line_nl;  // lines per block of the FP32 line launches (8 or 16)
     cudaGraphExec_t graph[2];
     double timeout_s;
     int failed_inst;
@@ -206,11 +207,12 @@ lbm_status upload_tables(lbm_batch* b) {
         const LineBatchKind rk = h.rho_df ? LineBatchKind::kRhoDF : LineBatchKind::kRhoF32;
         std::vector<int>& mr = h.rho_df ? mrdf : mrf;
         lines_batch_fill(rk, v, b->order, (int)mr.size(),
-                         h.rho_df ? rdf.data() + i * bdf : rf.data() + i * bf);
-        mr.insert(mr.end(), lines_batch_blocks(h.nx, h.ny, b->order, rk), i);
+                         h.rho_df ? rdf.data() + i * bdf : rf.data() + i * bf, b->line_nl);
+        mr.insert(mr.end(), lines_batch_blocks(h.nx, h.ny, b->order, rk, b->line_nl), i);
         lines_batch_fill(LineBatchKind::kForce, v, b->order, (int)mforce.size(),
-                         force.data() + i * bfo);
-        mforce.insert(mforce.end(), lines_batch_blocks(h.nx, h.ny, b->order, LineBatchKind::kForce),
+                         force.data() + i * bfo, b->line_nl);
+        mforce.insert(mforce.end(),
+                      lines_batch_blocks(h.nx, h.ny, b->order, LineBatchKind::kForce, b->line_nl),
                       i);
     }
     // the table region was sized for the largest counts
@@ -254,14 +256,14 @@ lbm_status enqueue_step(lbm_batch* b, cudaStream_t s, int from, cudaEvent_t* ev 
     CK(mark(1));
     // every instance is in exactly one of the two density launches
     CK(lines_batch_launch(LineBatchKind::kRhoF32, b->ws + t.rho_f32, at<int>(b, t.map_rho_f32),
-                          t.nb_rho_f32, b->order, 1, s));
+                          t.nb_rho_f32, b->order, 1, s, b->line_nl));
     CK(lines_batch_launch(LineBatchKind::kRhoDF, b->ws + t.rho_df, at<int>(b, t.map_rho_df),
                           t.nb_rho_df, b->order, 1, s));
     CK(mark(2));
     CK(launch_mu_mixed_batch(at<MuBatchInst>(b, t.mu), at<int>(b, t.map_mu), t.nb_mu, s));
     CK(mark(3));
     CK(lines_batch_launch(LineBatchKind::kForce, b->ws + t.force, at<int>(b, t.map_force),
-                          t.nb_force, b->order, 0, s));
+                          t.nb_force, b->order, 0, s, b->line_nl));
     CK(mark(4));
     return LBM_OK;
 }
@@ -393,6 +395,7 @@ lbm_status lbm_batch_init(lbm_batch** out, const lbm_instance* inst, int32_t n,
     if (!b) return LBM_ENOMEM;
     b->n = n;
     b->order = opts->fd_order;
+    b->line_nl = 8;
     b->mrt = opts->collision == LBM_COLLIDE_MRT;
     b->rates = MrtRates{opts->s_e, opts->s_eps, opts->s_q};
     b->stream = (cudaStream_t)cuda_stream;
@@ -664,10 +667,60 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int32_t reps) {
     // with the next time level: recompute the density of the current state
     for (const auto& h : b->inst)
         CK(launch_rho_from_f_mixed(h.f[b->cur], h.rh, h.rl, h.nx, h.ny, h.plane, s));
+    // lines per block of the FP32 line launches: the whole FP32 density launch
+    // and the force launch of the batch, timed at 8 and 16
+    {
+        float best = 0.0f;
+        int best_nl = 8;
+        for (int nl : {8, 16}) {
+            b->line_nl = nl;
+            st = upload_tables(b);
+            if (st) return st;
+            const Tables& t = b->tb;
+            auto pass = [&]() -> cudaError_t {
+                cudaError_t e = lines_batch_launch(LineBatchKind::kRhoF32, b->ws + t.rho_f32,
+                                                   at<int>(b, t.map_rho_f32), t.nb_rho_f32,
+                                                   b->order, 0, s, nl);
+                if (e != cudaSuccess) return e;
+                return lines_batch_launch(LineBatchKind::kForce, b->ws + t.force,
+                                          at<int>(b, t.map_force), t.nb_force, b->order, 0, s,
+                                          nl);
+            };
+            CK(pass());  // warm-up
+            CK(cudaEventRecord(b->tev[0], s));
+            for (int r = 0; r < reps; ++r) CK(pass());
+            CK(cudaEventRecord(b->tev[1], s));
+            st = wait_stream(b);
+            if (st) return st;
+            float ms = 0.0f;
+            CK(cudaEventElapsedTime(&ms, b->tev[0], b->tev[1]));
+            if (nl == 8 || ms < best) {
+                best = ms;
+                best_nl = nl;
+            }
+        }
+        b->line_nl = best_nl;
+    }
+    // the density lines overwrote mu-hat (it shares its plane with d_xx rho) and
+    // the force lines then read that: recompute the force stage of the state
+    for (int i = 0; i < b->n; ++i) {
+        st = instance_force(b, i);
+        if (st) return st;
+    }
     drop_graphs(b);
     st = upload_tables(b);
     if (st) return st;
     return read_states(b);
+}
+
+int32_t lbm_batch_lines_per_block(const lbm_batch* b) { return b ? b->line_nl : -1; }
+
+lbm_status lbm_batch_set_lines_per_block(lbm_batch* b, int32_t nl) {
+    if (!b || (nl != 8 && nl != 16)) return LBM_EINVAL;
+    CK(cudaSetDevice(b->dev));
+    b->line_nl = nl;
+    drop_graphs(b);
+    return upload_tables(b);
 }
 
 }  // extern "C"

@@ -242,11 +242,13 @@ enum class LineBatchKind {
     kForce,   // x|y lines of mu-hat with the force epilogue
 };
 size_t lines_batch_desc_bytes(LineBatchKind kind);
-int lines_batch_blocks(int nx, int ny, int order, LineBatchKind kind);
+// nl: lines per block, 8 or 16 (the FP32 kinds; the double-float density lines
+// always take 8).  Results do not depend on it.
+int lines_batch_blocks(int nx, int ny, int order, LineBatchKind kind, int nl = 8);
 void lines_batch_fill(LineBatchKind kind, const MixedLinesView& v, int order, int blk0,
-                      void* host_dst);
+                      void* host_dst, int nl = 8);
 cudaError_t lines_batch_launch(LineBatchKind kind, const void* d_desc, const int* map,
-                               int nblocks, int order, int bump, cudaStream_t s);
+                               int nblocks, int order, int bump, cudaStream_t s, int nl = 8);
 
 // Below this Maxwell density ratio the mixed path solves the density's lines in
 // FP32 (measured: coexistence densities within 2e-4 of the FP64 path); at and

@@ -1015,9 +1015,9 @@ struct LinesXYInst {
     DevState* st;
 };
 
-template <class P1, class P2, bool SIXTH, bool SECOND, class InX, class EpiX, class InY,
+template <class P1, class P2, bool SIXTH, bool SECOND, int NL, class InX, class EpiX, class InY,
           class EpiY>
-__global__ void __launch_bounds__(kNL * 32, 3)
+__global__ void __launch_bounds__(NL * 32, NL == 8 ? 3 : 2)
     k_lines_xy_batch(const LinesXYInst<InX, EpiX, InY, EpiY>* __restrict__ d,
                      const int* __restrict__ map, LineConst<P1> k1, LineConst<PolF> k1f,
                      LineConst<P2> k2, int bump) {
@@ -1031,14 +1031,14 @@ __global__ void __launch_bounds__(kNL * 32, 3)
         const LineGeo g = D.gx;
         epi.init(st);
         in.init(st);
-        lines_body<0, P1, P2, SIXTH, SECOND, kNL>(in, g, k1, k1f, k2, epi, st, local);
+        lines_body<0, P1, P2, SIXTH, SECOND, NL>(in, g, k1, k1f, k2, epi, st, local);
     } else {
         InY in = D.iny;
         EpiY epi = D.ey;
         const LineGeo g = D.gy;
         epi.init(st);
         in.init(st);
-        lines_body<1, P1, P2, SIXTH, SECOND, kNL>(in, g, k1, k1f, k2, epi, st, local - D.nbx);
+        lines_body<1, P1, P2, SIXTH, SECOND, NL>(in, g, k1, k1f, k2, epi, st, local - D.nbx);
     }
 }
 
@@ -1375,12 +1375,12 @@ int halo_of(LineBatchKind kind, int order) {
     }
 }
 
-template <class P1, class P2, bool SIXTH, bool SECOND, class Inst>
+template <class P1, class P2, bool SIXTH, bool SECOND, int NL, class Inst>
 cudaError_t launch_batch_t(const Inst* d, const int* map, int nblocks, int order, int bump,
                            cudaStream_t s) {
-    auto kern = k_lines_xy_batch<P1, P2, SIXTH, SECOND, decltype(Inst::inx), decltype(Inst::ex),
-                                 decltype(Inst::iny), decltype(Inst::ey)>;
-    const size_t smem = smem_bytes<P1, P2, SECOND>();
+    auto kern = k_lines_xy_batch<P1, P2, SIXTH, SECOND, NL, decltype(Inst::inx),
+                                 decltype(Inst::ex), decltype(Inst::iny), decltype(Inst::ey)>;
+    const size_t smem = smem_bytes<P1, P2, SECOND, NL>();
     static bool attr = false;  // one flag per kernel instantiation
     if (!attr) {
         cudaError_t e =
@@ -1388,8 +1388,8 @@ cudaError_t launch_batch_t(const Inst* d, const int* map, int nblocks, int order
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    kern<<<nblocks, kNL * 32, smem, s>>>(d, map, make_const<P1>(order), make_const<PolF>(order),
-                                         make_const<P2>(order), bump);
+    kern<<<nblocks, NL * 32, smem, s>>>(d, map, make_const<P1>(order), make_const<PolF>(order),
+                                        make_const<P2>(order), bump);
     return cudaGetLastError();
 }
 
@@ -1464,16 +1464,23 @@ size_t lines_batch_desc_bytes(LineBatchKind kind) {
     }
 }
 
-int lines_batch_blocks(int nx, int ny, int order, LineBatchKind kind) {
+// Lines per block of a batch launch: 8 or 16 for the FP32 kinds; the
+// double-float density lines always 8 (16 would spill).
+int batch_nl(LineBatchKind kind, int nl) { return kind == LineBatchKind::kRhoDF ? kNL : nl; }
+
+int lines_batch_blocks(int nx, int ny, int order, LineBatchKind kind, int nl) {
     const int H = halo_of(kind, order);
-    const LineGeo gx = make_geo(nx, ny, 0, H), gy = make_geo(nx, ny, 1, H);
+    nl = batch_nl(kind, nl);
+    const LineGeo gx = make_geo(nx, ny, 0, H, false, nl), gy = make_geo(nx, ny, 1, H, false, nl);
     return gx.ngroups * gx.nwin + gy.ngroups * gy.nwin;
 }
 
 void lines_batch_fill(LineBatchKind kind, const MixedLinesView& v, int order, int blk0,
-                      void* host_dst) {
+                      void* host_dst, int nl) {
     const int H = halo_of(kind, order);
-    const LineGeo gx = make_geo(v.nx, v.ny, 0, H), gy = make_geo(v.nx, v.ny, 1, H);
+    nl = batch_nl(kind, nl);
+    const LineGeo gx = make_geo(v.nx, v.ny, 0, H, false, nl),
+                  gy = make_geo(v.nx, v.ny, 1, H, false, nl);
     const int nbx = gx.ngroups * gx.nwin;
     if (kind == LineBatchKind::kRhoDF) {
         RhoInst d{InDF{v.rh, v.rl}, EpiStore<float, float>{v.dxr, v.dxx},
@@ -1491,22 +1498,29 @@ void lines_batch_fill(LineBatchKind kind, const MixedLinesView& v, int order, in
 }
 
 cudaError_t lines_batch_launch(LineBatchKind kind, const void* d_desc, const int* map,
-                               int nblocks, int order, int bump, cudaStream_t s) {
+                               int nblocks, int order, int bump, cudaStream_t s, int nl) {
     if (nblocks <= 0) return cudaSuccess;
     const bool six = order == 6;
     if (kind == LineBatchKind::kRhoDF) {
         const RhoInst* d = static_cast<const RhoInst*>(d_desc);
-        return six ? launch_batch_t<PolDF, PolF, true, true>(d, map, nblocks, order, bump, s)
-                   : launch_batch_t<PolDF, PolF, false, true>(d, map, nblocks, order, bump, s);
+        return six ? launch_batch_t<PolDF, PolF, true, true, kNL>(d, map, nblocks, order, bump, s)
+                   : launch_batch_t<PolDF, PolF, false, true, kNL>(d, map, nblocks, order, bump, s);
     }
     if (kind == LineBatchKind::kRhoF32) {
         const RhoF32Inst* d = static_cast<const RhoF32Inst*>(d_desc);
-        return six ? launch_batch_t<PolF, PolF, true, true>(d, map, nblocks, order, bump, s)
-                   : launch_batch_t<PolF, PolF, false, true>(d, map, nblocks, order, bump, s);
+        if (nl == 16)
+            return six ? launch_batch_t<PolF, PolF, true, true, 16>(d, map, nblocks, order, bump, s)
+                       : launch_batch_t<PolF, PolF, false, true, 16>(d, map, nblocks, order, bump,
+                                                                     s);
+        return six ? launch_batch_t<PolF, PolF, true, true, kNL>(d, map, nblocks, order, bump, s)
+                   : launch_batch_t<PolF, PolF, false, true, kNL>(d, map, nblocks, order, bump, s);
     }
     const ForceInst* d = static_cast<const ForceInst*>(d_desc);
-    return six ? launch_batch_t<PolF, PolF, true, false>(d, map, nblocks, order, 0, s)
-               : launch_batch_t<PolF, PolF, false, false>(d, map, nblocks, order, 0, s);
+    if (nl == 16)
+        return six ? launch_batch_t<PolF, PolF, true, false, 16>(d, map, nblocks, order, 0, s)
+                   : launch_batch_t<PolF, PolF, false, false, 16>(d, map, nblocks, order, 0, s);
+    return six ? launch_batch_t<PolF, PolF, true, false, kNL>(d, map, nblocks, order, 0, s)
+               : launch_batch_t<PolF, PolF, false, false, kNL>(d, map, nblocks, order, 0, s);
 }
 
 }  // namespace cplbm

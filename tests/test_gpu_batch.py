@@ -80,6 +80,29 @@ def test_batch_bitexact_vs_lone_contexts(cuda, fd_order, steps, precision):
     b.close()
 
 
+@pytest.mark.parametrize("nl", [8, 16])
+def test_batch_lines_per_block_bitexact(cuda, nl):
+    """The FP32 line launches with 8 or 16 lines a block give the lone contexts'
+    results bit for bit (set before the first step and switched mid-run)."""
+    from paper_1906_09530_gb300 import Batch
+    spec, rhos = _instances()
+    b = Batch(spec)
+    b.set_lines_per_block(nl)
+    assert b.lines_per_block() == nl
+    for i, r in enumerate(rhos):
+        b.set_fields(i, r)
+    b.step(4)
+    b.set_lines_per_block(24 - nl)
+    b.step(3)
+    for i, (d, r) in enumerate(zip(spec, rhos)):
+        s = _lone(d, r)
+        s.step(7)
+        for x, y in zip(b.fields(i), s.fields()):
+            assert np.array_equal(x, y), i
+        s.close()
+    b.close()
+
+
 def test_batch_member_close_to_oracle(cuda):
     """A batch member against the FP64 oracle, at the lone mixed path's tolerance."""
     from paper_1906_09530_gb300 import Batch
@@ -111,6 +134,7 @@ def test_batch_autotune_keeps_state_and_results(cuda):
     b.step(3)
     before = [b.fields(i) for i in range(len(spec))]
     b.autotune(reps=3)
+    assert b.lines_per_block() in (8, 16)
     for i in range(len(spec)):
         assert b.tile_rows(i) in (4, 8, 16, 32)
         for x, y in zip(b.fields(i), before[i]):
