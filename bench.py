@@ -968,8 +968,9 @@ def drop_warm_start(train_T=(0.32, 0.33, 0.34, 0.36, 0.37, 0.38, 0.40),
                     radii=(64.0, 125.0, 250.0), judge_T=0.35, judge_R=250.0,
                     train_steps=300_000, run_steps=240_000, every=2000, window=10, kappa=0.1,
                     k=0.2, epochs=4000):
-    """The learned warm start for drops (configs[4] scaled to a drop whose plain
-    run converges).  Training data: drops of the given radii (each at the centre
+    """The learned warm start for drops: the 4096^2 drop of radius 1000 at T_r 0.35
+    scaled down to a drop whose plain run converges (by default R 250 on 1000^2,
+    the same grid/radius ratio).  Training data: drops of the given radii (each at the centre
     of a periodic grid 4 R wide) at the training temperatures, run as one batch
     for train_steps; the surrogate takes (T_r, kappa-hat, k, 1/R).  Judge: a drop
     of judge_R at judge_T (a temperature not trained on), from the tanh start
