@@ -985,18 +985,25 @@ template <class P1, class P2, bool SIXTH, bool SECOND, int NL, class InX, class 
 __global__ void __launch_bounds__(NL * 32, (xy_min_blocks<NL, SECOND, P1>()))
     k_lines_xy(InX inx, LineGeo gx, EpiX ex, InY iny, LineGeo gy, EpiY ey, LineConst<P1> k1,
                LineConst<PolF> k1f, LineConst<P2> k2, DevState* st, int bump, int nbx,
-               const __grid_constant__ CUtensorMap tmy, int use_tma) {
+               const __grid_constant__ CUtensorMap tmy, int use_tma, int y_first) {
     pdl_prologue();
     if (bump && blockIdx.x == 0 && threadIdx.x == 0) st->t += 1;
-    if ((int)blockIdx.x < nbx) {
+    // y_first: the y-line blocks take the low block indices, so they are
+    // dispatched first (in a launch of about one wave the slower y-windows then
+    // do not form the tail); otherwise the x-line blocks do
+    const int nby = (int)gridDim.x - nbx;
+    const bool x = y_first ? (int)blockIdx.x >= nby : (int)blockIdx.x < nbx;
+    const int local = y_first ? (x ? (int)blockIdx.x - nby : (int)blockIdx.x)
+                              : (x ? (int)blockIdx.x : (int)blockIdx.x - nbx);
+    if (x) {
         ex.init(st);
         inx.init(st);
-        lines_body<0, P1, P2, SIXTH, SECOND, NL>(inx, gx, k1, k1f, k2, ex, st, (int)blockIdx.x);
+        lines_body<0, P1, P2, SIXTH, SECOND, NL>(inx, gx, k1, k1f, k2, ex, st, local);
     } else {
         ey.init(st);
         iny.init(st);
-        lines_body<1, P1, P2, SIXTH, SECOND, NL>(iny, gy, k1, k1f, k2, ey, st,
-                                             (int)blockIdx.x - nbx, use_tma ? &tmy : nullptr);
+        lines_body<1, P1, P2, SIXTH, SECOND, NL>(iny, gy, k1, k1f, k2, ey, st, local,
+                                             use_tma ? &tmy : nullptr);
     }
 }
 
@@ -1318,9 +1325,13 @@ cudaError_t launch_xy_t(InX inx, EpiX ex, InY iny, EpiY ey, int nx, int ny, int 
     int use_tma = 0;
     if (std::is_same<P1, PolF>::value && std::is_same<P2, PolF>::value && st)
         use_tma = y_tensor_map(y_field(iny), nx, ny, NL, &tmy) ? 1 : 0;
+    // y-line blocks first in the launches of 16 lines a block (grids up to 2^21
+    // nodes, about one wave): at 1024^2 the density lines 14.3 -> 12.7 us, the
+    // force lines 12.3 -> 12.0; at 4096^2 (8 lines a block, many waves) no gain
+    const int y_first = NL == 16 ? 1 : 0;
     return launch_pdl(kern, blocks, NL * 32, smem, s, inx, gx, ex, iny, gy, ey,
                       make_const<P1>(order), make_const<PolF>(order), make_const<P2>(order), st,
-                      bump, nbx, tmy, use_tma);
+                      bump, nbx, tmy, use_tma, y_first);
 }
 
 template <class P1, class P2, bool SECOND, class InX, class EpiX, class InY, class EpiY>
