@@ -197,20 +197,24 @@ def cpu_baseline(w, target_s=10.0):
 EQ_WORKLOAD = dict(nx=8, ny=400, T_r=0.8, k=0.1, kappa=0.1, tau=1.0, order=6)
 
 
-def equilibrium_time(precision, max_steps=600_000, nx=None):
+def equilibrium_time(precision, max_steps=600_000, nx=None, T_r=None):
     """Wall time from lbm_set_fields to Maxwell-accurate equilibrium of a flat
-    interface (periodic, height 400, k = 0.1, T_r = 0.8; Sec. 5.1), quasi-1-D
-    (8 wide) or nx wide.  Checked every 500 steps: done when the bulk gas and
-    liquid densities are both within 1e-3 of the Maxwell pair and moved by
-    < 1e-6 (relative) over the last 500 steps.  (At k = 0.1 the method's gas
-    settles within 1e-3 of Maxwell only above T_r ~ 0.65: below, the target is
-    out of its reach at this k.)"""
+    interface (periodic, height 400, k = 0.1, T_r = 0.8 unless given; Sec. 5.1),
+    quasi-1-D (8 wide) or nx wide.  Checked every 500 steps: done when the bulk
+    gas (at the node farthest from both interfaces, where the oracle's fixed
+    point reads it) and the bulk liquid (at the slab's centre) are both within
+    1e-3 of the Maxwell pair and moved by < 1e-6 (relative) over the last 500
+    steps.  (At k = 0.1 the method's own gas settles within 1e-3 of Maxwell only
+    above T_r ~ 0.67: +7.2e-4 at 0.7, +3.5e-3 at 0.6, out of its reach at this
+    k.)"""
     import numpy as np
     import paper_1906_09530_gb300 as P
     from paper_1906_09530_gb300 import workloads as W
     e = dict(EQ_WORKLOAD)
     if nx is not None:
         e["nx"] = nx
+    if T_r is not None:
+        e["T_r"] = T_r
     rg, rl = P.lbm_maxwell(e["T_r"])
     rho0 = W.flat(e["nx"], e["ny"], rg, rl, e["ny"] / 2, 4.0 / e["k"])
     sim = P.Simulation(e["nx"], e["ny"], e["T_r"], e["kappa"], e["tau"], e["k"],
@@ -223,8 +227,7 @@ def equilibrium_time(precision, max_steps=600_000, nx=None):
     while sim.t < max_steps:
         sim.step(500)
         r = sim.fields()[0][:, 0]
-        g = np.r_[r[: ny // 10], r[-ny // 10:]].mean()
-        l = r[ny // 2 - ny // 20: ny // 2 + ny // 20].mean()
+        g, l = r[0], r[ny // 2]
         cur = (g, l)
         if (prev is not None and abs(g / rg - 1) < 1e-3 and abs(l / rl - 1) < 1e-3
                 and abs(g / prev[0] - 1) < 1e-6 and abs(l / prev[1] - 1) < 1e-6):
@@ -236,8 +239,9 @@ def equilibrium_time(precision, max_steps=600_000, nx=None):
     return {"workload": f"flat-interface-{e['nx']}x{ny}-Tr{e['T_r']}-k{e['k']}-{precision}",
             "wall_s": done, "steps": steps, "reached": done is not None,
             "gas_rel_err": float(cur[0] / rg - 1), "liquid_rel_err": float(cur[1] / rl - 1),
-            "criterion": "both bulk densities within 1e-3 of Maxwell and steady to 1e-6 "
-                         "over 500 steps, checked every 500 steps"}
+            "criterion": "both bulk densities (gas at the node farthest from both "
+                         "interfaces, liquid at the slab centre) within 1e-3 of Maxwell and "
+                         "steady to 1e-6 over 500 steps, checked every 500 steps"}
 
 
 def large_grid(precision, steps, warmup, size=4096, collision="bgk", **over):
@@ -1334,6 +1338,9 @@ def main():
         # the same slab 1024 nodes wide (409 600 nodes, the grid scale of the
         # benchmark drop)
         line["equilibrium_1024"] = equilibrium_time(args.precision, nx=1024)
+        # the lowest temperature at which the method's gas comes within 1e-3 of
+        # Maxwell at k 0.1
+        line["equilibrium_0.7"] = equilibrium_time(args.precision, T_r=0.7)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     if rank == 0:
