@@ -132,6 +132,13 @@ def test_strerror_and_null_ctx():
     lib.lbm_free(None)
     assert lib.lbm_set_wall_velocity(None, 0.0, 0.0) == B.LBM_EINVAL
     assert lib.lbm_path_flags(None) == -1
+    # launch and kernel choices, and the batch's and the network's
+    assert lib.lbm_set_collide_form(None, 0) == B.LBM_EINVAL
+    assert lib.lbm_set_launch_mode(None, 1, 1, 0) == B.LBM_EINVAL
+    assert lib.lbm_batch_lines_per_block(None) == -1
+    assert lib.lbm_batch_set_lines_per_block(None, 16) == B.LBM_EINVAL
+    assert lib.lbm_mlp_set_tcgen05(None, 1) == B.LBM_EINVAL
+    assert lib.lbm_mlp_tcgen05(None) == -1
 
 
 def test_oracle_and_library_share_nothing():
