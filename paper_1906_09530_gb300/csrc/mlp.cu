@@ -32,7 +32,7 @@ namespace cplbm {
 namespace {
 
 constexpr int kIn = 4, kW = 256, kOut = 256, kLayers = 4;
-constexpr int kInPad = 16;  // the first product's K, padded to one mma k-step
+constexpr int kInPad = 16;  // the first product's K on mma.sync, padded to one k-step
 constexpr int kK0 = 64;     // row stride of the BF16 input and K of its tcgen05 product
                             // (zero-padded to one 128-byte swizzle row)
 constexpr int kFanIn[kLayers] = {kIn, kW, kW, kW};
@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(128) k_gemm(GemmArgs g) {
 // other roles see the flag and leave their loops, and the CTA waits (bounded)
 // for its copies and MMAs in flight before it frees its tensor memory.
 //
-// k_umma_rows: D[M x 256] = A[M x K] Bt[256 x K]^T, K = 16 or 256: the forward
+// k_umma_rows: D[M x 256] = A[M x K] Bt[256 x K]^T, K = 64 or 256: the forward
 // products (A = the layer input, Bt = the transposed weights) and the input
 // gradients (A = the backward signal, Bt = the weights as stored).  Persistent:
 // one CTA per SM walks 128-row tiles of A.  Warp 8 (one thread) streams the
@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(128) k_gemm(GemmArgs g) {
 // transposed BF16 copies At and Dt.  K is split into slices (grid.y) so that the
 // product fills the GPU; each CTA streams its slice through a four-stage ring
 // of 64-wide K chunks (warp 4 loads, warp 5 issues the MMAs) and writes an FP32
-// partial; k_wgrad_reduce adds the partials in slice order (deterministic).
+// partial; k_wgrad_reduce adds the partials in a fixed order (deterministic).
 // ---------------------------------------------------------------------------
 constexpr int UM = 128, UN = 256;
 constexpr unsigned kUmmaSpins = 1u << 22;
