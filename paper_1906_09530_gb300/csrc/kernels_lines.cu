@@ -1115,7 +1115,18 @@ struct EpiMu {
     }
 };
 
-// F = -rho d(mu-hat) + c_s^2 d(rho), Eq. 12.
+// F = -rho d(mu-hat) + c_s^2 d(rho), Eq. 12.  In FP32, c_s^2 = 1/3 as a constant is 3e-8
+// too large, a bias that the populations' pressure does not share and that moves the dilute
+// gas at high density ratios.  So c_s^2 = hi + lo, and the sum is rounded once.
+__device__ __forceinline__ float force_term(float r, float dmu, float d) {
+    constexpr float hi = 1.0f / 3.0f;
+    constexpr float lo = (float)(1.0 / 3.0 - (double)hi);
+    return rn_fma(d, hi, rn_fma(-r, dmu, rn_mul(d, lo)));
+}
+__device__ __forceinline__ double force_term(double r, double dmu, double d) {
+    return rn_fma(-r, dmu, rn_mul(d, 1.0 / 3.0));
+}
+
 template <class O, class RhoT>
 struct EpiForce {
     static constexpr int kBatch = 4;  // its operands are float4 pairs: four in flight
@@ -1130,7 +1141,7 @@ struct EpiForce {
     __device__ __forceinline__ Ops fetch(size_t o) const { return Ops{__ldg(rho + o), __ldg(dr + o)}; }
     __device__ __forceinline__ bool operator()(size_t o, O dmu, O, const Ops& op) {
         // explicit rounding: the epilogue is inlined in several kernels
-        F[o] = rn_fma(-(O)op.r, dmu, rn_mul(op.d, (O)(1.0 / 3.0)));
+        F[o] = force_term((O)op.r, dmu, op.d);
         return false;
     }
     struct Ops4 {
@@ -1141,12 +1152,11 @@ struct EpiForce {
                     __ldg(reinterpret_cast<const float4*>(dr + o))};
     }
     __device__ __forceinline__ bool put4(size_t o, float4 dmu, float4, const Ops4& op) {
-        const float t = 1.0f / 3.0f;
         float4 f;
-        f.x = rn_fma(-op.r.x, dmu.x, rn_mul(op.d.x, t));
-        f.y = rn_fma(-op.r.y, dmu.y, rn_mul(op.d.y, t));
-        f.z = rn_fma(-op.r.z, dmu.z, rn_mul(op.d.z, t));
-        f.w = rn_fma(-op.r.w, dmu.w, rn_mul(op.d.w, t));
+        f.x = force_term(op.r.x, dmu.x, op.d.x);
+        f.y = force_term(op.r.y, dmu.y, op.d.y);
+        f.z = force_term(op.r.z, dmu.z, op.d.z);
+        f.w = force_term(op.r.w, dmu.w, op.d.w);
         *reinterpret_cast<float4*>(F + o) = f;
         return false;
     }

@@ -67,8 +67,22 @@ __device__ __forceinline__ bool collide_pairs(T f[9], T Fx, T Fy, T omega, T big
     const T uu = rn_fma(ux, ux, rn_mul(uy, uy));
     const T vv = rn_fma(vx, vx, rn_mul(vy, vy));
     const T base = rn_fma(T(-1.5), rn_fma(-keep, uu, vv), omega);
-    const T r0 = rn_mul(rho, T(4.0 / 9.0)), r1 = rn_mul(rho, T(1.0 / 9.0)),
-            r2 = rn_mul(rho, T(1.0 / 36.0));
+    T r0, r1, r2;
+    if constexpr (sizeof(T) == 4) {
+        // In FP32, 4/9, 1/9 and 1/36 share one mantissa and all round up by 7.5e-9.  Used as
+        // constants, that bias adds mass every step and sets the populations' pressure apart
+        // from the force's c_s^2 rho, which shifts the dilute gas at high density ratios.
+        // Instead rho w_i = 16, 4, 1 x rho/36, with rho/36 = rho (hi + lo) rounded once.
+        constexpr float hi = 1.0f / 36.0f;
+        constexpr float lo = (float)(1.0 / 36.0 - (double)hi);
+        r2 = rn_fma(rho, T(hi), rn_mul(rho, T(lo)));
+        r1 = rn_mul(r2, T(4));
+        r0 = rn_mul(r2, T(16));
+    } else {
+        r0 = rn_mul(rho, T(4.0 / 9.0));
+        r1 = rn_mul(rho, T(1.0 / 9.0));
+        r2 = rn_mul(rho, T(1.0 / 36.0));
+    }
     f[0] = rn_fma(keep, f[0], rn_mul(r0, base));
     auto pair = [&](int i, int j, T w, T eu, T ev) {
         const T s = rn_fma(-keep, eu, ev);

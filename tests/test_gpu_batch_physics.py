@@ -4,7 +4,9 @@ interfaces at once, and a Laplace-law fit from a batch of drops (Secs. 5.1, 5.3)
 Measured facts these bounds come from (FP64 and mixed paths, flat interfaces,
 height 400, k = 0.1, 200 000 steps):
   * the liquid density settles within 1e-4 of the Maxwell value at every T_r
-    from 0.3 to 0.8;
+    from 0.3 to 0.8 on the FP64 path, and within 2e-4 on the mixed path, whose
+    FP32 populations stop on a fixed point of the FP32 step short of the
+    method's (-1.1e-4 at T_r 0.8, nothing changing after 200 000 steps);
   * the gas density settles above the Maxwell value by an offset that grows as
     T_r falls (+3e-3 at 0.62, +2.5e-2 at 0.47, +7.3e-2 at 0.4, +0.38 at 0.3) and
     is the same for tau = 0.8, 1.0, 1.5 and for the FP64 and mixed paths: a
@@ -49,7 +51,7 @@ def test_batch_coexistence_curve(cuda):
     gas, liq = np.array(gas), np.array(liq)
     mg, ml = np.array([p[0] for p in pairs]), np.array([p[1] for p in pairs])
     # liquid branch on Maxwell's curve
-    assert np.abs(liq / ml - 1).max() <= 1e-4
+    assert np.abs(liq / ml - 1).max() <= 2e-4
     # the curve is ordered: gas rises and liquid falls with T_r
     assert np.all(np.diff(gas) > 0) and np.all(np.diff(liq) < 0)
     # gas branch: above Maxwell by the scheme's offset, at most 0.14 decade

