@@ -235,8 +235,10 @@ lbm_status lbm_diag(lbm_ctx *ctx, double *mass, double *max_v, double *rho_min,
  * return LBM_EINVAL.  The paper has no counterpart; this is library plumbing.
  * The first call on a device looks up that array's device address; make it
  * before any stream capture.  Like lbm_diag, every call copies its results to
- * the host and waits for the context's stream before it returns.  Calls share
- * the array, so calls that overlap on the GPU race on it. */
+ * the host and waits for the context's stream before it returns, so no call can
+ * be captured into a CUDA graph: none may be made while the context's stream is
+ * capturing.  Calls share the array, so calls that overlap on the GPU race on
+ * it. */
 lbm_status lbm_diag_noalloc(lbm_ctx *ctx, double *mass, double *max_v, double *rho_min,
                             double *rho_max);
 

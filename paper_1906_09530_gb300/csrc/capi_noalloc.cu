@@ -8,7 +8,8 @@
 // the context (whose workspace they obtained from their own pool) and host
 // outputs, and nothing is allocated here.  Like lbm_diag, the call copies its
 // four results to the host and waits for the context's stream before it
-// returns.
+// returns.  So no call can be captured into a CUDA graph, and none may be made
+// while the context's stream is capturing.
 //
 // The array g_diag_partials is a file-scope __device__ variable: every GPU that
 // loads the library holds its 512 KB until the process exits.  In host code its
